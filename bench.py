@@ -1,0 +1,286 @@
+#!/usr/bin/env python
+"""Benchmark: walker-steps/s of the multideterminant hot path (Psi, grad Psi/Psi,
+Lap Psi/Psi and E_L for every walker) on the chlorine-like 750k-determinant
+workload, one JSON line on stdout.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                  [--workload NAME] [--precision mixed|fp64]
+
+A step evaluates the whole batch of walkers (8,192 per GPU) once. Walkers are
+independent, so with N GPUs each rank evaluates its own 8,192 walkers (weak
+scaling, no collective on the data path); the time is the max over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "walker-steps/s (Ψ,∇Ψ,∇²Ψ), 17e⁻, N_det=750k: mixed vs FP64 at 1e-5 rel err"
+UNIT = "walker-steps/s"
+FP64_PEAK_TFLOPS = 1.25     # nominal dense FP64 of one GB300 (recipe table); see the design doc
+CPU_SAMPLE_WALKERS = 96     # bounded oracle sample for the CPU baseline (~10-30 s of CPU work)
+
+
+def _env_int(k, d):
+    try:
+        return int(os.environ.get(k, d))
+    except ValueError:
+        return d
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms during the timed region."""
+    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.p = None
+
+    def __enter__(self):
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.Q,
+                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                      stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except (OSError, ValueError):
+            self.p = None
+        return self
+
+    def __exit__(self, *a):
+        self.lines = []
+        if self.p is not None:
+            time.sleep(0.25)
+            self.p.terminate()
+            try:
+                out, _ = self.p.communicate(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.p.kill()
+                out, _ = self.p.communicate()
+            self.lines = [l for l in out.splitlines() if l.strip()]
+
+    def summary(self):
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for l in getattr(self, "lines", []):
+            f = [x.strip() for x in l.split(",")]
+            if len(f) < 7:
+                continue
+            try:
+                sm.append(float(f[0]))
+                smax = float(f[1])
+            except ValueError:
+                continue
+            for n, v in zip(names, f[3:7]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": smax, "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def _gpu_index(local_rank):
+    vis = os.environ.get("CUDA_VISIBLE_DEVICES", "")
+    parts = [p for p in vis.split(",") if p.strip()]
+    if local_rank < len(parts) and parts[local_rank].strip().isdigit():
+        return int(parts[local_rank])
+    return local_rank
+
+
+def cpu_baseline(wl, n_sample, threads=None):
+    """The FP64 oracle as it stands, on a bounded sample of walkers, all host cores."""
+    import oracle
+    threads = threads or os.cpu_count() or 1
+    R = wl.R[:n_sample]
+    t0 = time.perf_counter()
+    ref = oracle.evaluate(wl, R=R, n_threads=threads)
+    dt = time.perf_counter() - t0
+    return ref, {"value": n_sample / dt, "unit": UNIT, "cores": threads, "kind": "oracle",
+                 "sample": "%d of the %d walkers of one step (same expansion), %.1f s wall" % (n_sample, wl.n_walk, dt)}
+
+
+def run_reference(args):
+    """Reference arm: the FP64 oracle on the host cores, same workload and metric."""
+    rank = _env_int("RANK", 0)
+    if rank != 0:
+        return
+    from paper_1510_00730_gb300 import synth
+    wl = synth.WORKLOADS[args.workload]()
+    n = max(1, min(args.ref_sample, wl.n_walk))
+    for _ in range(args.warmup):
+        cpu_baseline(wl, max(1, n // 4))
+    times = []
+    cores = os.cpu_count() or 1
+    for s in range(args.steps):
+        lo = (s * n) % max(1, wl.n_walk - n)
+        t0 = time.perf_counter()
+        import oracle
+        oracle.evaluate(wl, R=wl.R[lo:lo + n], n_threads=cores)
+        times.append(time.perf_counter() - t0)
+    per = statistics.mean(times)
+    val = n / per
+    line = {"impl": "reference", "metric": METRIC, "value": val, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": per * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": args.workload, "walkers_per_step": n, "n_det": wl.n_det},
+            "cpu_baseline": {"value": val, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": "%d walkers per step of the %d-walker workload" % (n, wl.n_walk)},
+            "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    import paper_1510_00730_gb300 as pkg
+    from paper_1510_00730_gb300 import synth
+
+    rank, world, local = _env_int("RANK", 0), _env_int("WORLD_SIZE", 1), _env_int("LOCAL_RANK", 0)
+    if world != args.gpus:
+        world = max(world, 1)
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+    prec = {"mixed": pkg.PRECISION_MIXED, "fp64": pkg.PRECISION_FP64}[args.precision]
+
+    wl = synth.WORKLOADS[args.workload]()
+    W = wl.n_walk
+    ctx = pkg.Context.from_workload(wl, device=local, precision=prec)
+    st = ctx.stats()
+    # distinct walker batches per rank (resident in HBM before timing)
+    rng = np.random.default_rng(1000 + rank)
+    batches = [wl.R if (b == 0 and rank == 0) else synth.make_walkers(rng, W, wl.n_elec) for b in range(4)]
+    Rdev = [torch.from_numpy(np.ascontiguousarray(b)).to(dev) for b in batches]
+    out = ctx.alloc_outputs(W)
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)  # 512 MB > 129 MB L2
+    stream = torch.cuda.current_stream(dev)
+
+    for s in range(args.warmup):
+        ctx.evaluate(Rdev[s % 4], out=out)
+    torch.cuda.synchronize()
+
+    ctx.set_profiling(True)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    stage_ms = []
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(_gpu_index(local)) as clk:
+        for s in range(args.steps):
+            flush.fill_(float(s))          # evict L2 between timed steps (outside the events)
+            ev[s][0].record(stream)
+            ctx.evaluate(Rdev[s % 4], out=out)
+            ev[s][1].record(stream)
+            stage_ms.append(ctx.profile())  # waits for this step's events
+        torch.cuda.synchronize()
+    if dist is not None:
+        dist.barrier()
+    ctx.set_profiling(False)
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    ms = statistics.mean(step_ms)
+    if dist is not None:
+        t = torch.tensor([ms], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    value = W * world / (ms / 1e3)
+
+    # end to end through the host-memory C-ABI call: H2D of R and D2H of all outputs per step
+    N = wl.n_elec
+    hR = torch.empty((W, N, 3), dtype=torch.float64, pin_memory=True)
+    hR.numpy()[:] = batches[0]
+    hout = dict(log_abs_psi=torch.empty(W, dtype=torch.float64, pin_memory=True).numpy(),
+                sign=torch.empty(W, dtype=torch.int8, pin_memory=True).numpy(),
+                grad=torch.empty((W, N, 3), dtype=torch.float64, pin_memory=True).numpy(),
+                lap=torch.empty((W, N), dtype=torch.float64, pin_memory=True).numpy(),
+                e_local=torch.empty(W, dtype=torch.float64, pin_memory=True).numpy(),
+                status=torch.empty(W, dtype=torch.int32, pin_memory=True).numpy().view(np.uint32))
+    for _ in range(2):
+        ctx.evaluate_host(hR.numpy(), out=hout)
+    e2e_t = []
+    for s in range(args.steps):
+        flush.fill_(float(s))
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        ctx.evaluate_host(hR.numpy(), out=hout)
+        e2e_t.append(time.perf_counter() - t0)
+    e2e_ms = statistics.mean(e2e_t) * 1e3
+    if dist is not None:
+        t = torch.tensor([e2e_ms], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_ms = float(t.item())
+    h2d = W * N * 3 * 8
+    d2h = W * (8 + 1 + 3 * N * 8 + N * 8 + 8 + 4)
+
+    # roofline of the dominant kernel: the FP64 sparse contraction (2 products, 2 FLOP per nonzero per walker)
+    kern = {k: statistics.mean(d[k] for d in stage_ms) for k in stage_ms[0]}
+    flops = 4.0 * st["n_det"] * W
+    achieved = flops / (kern["contract"] / 1e3) / 1e12
+    roofline = {"kernel": "k_spmm_f64 (v = C r_dn, u = C^T r_up)", "bound": "alu", "achieved": achieved,
+                "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS,
+                "traffic": args.traffic, "peak_source": "nominal FP64 of the recipe table (no measured FP64 peak)",
+                "flops_per_launch": flops}
+
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64" if prec == pkg.PRECISION_FP64 else "f32+f64",
+            "data": "synthetic",
+            "config": {"workload": args.workload, "precision": args.precision, "walkers_per_gpu": W,
+                       "n_det": st["n_det"], "n_det_up": st["n_det_up"], "n_det_dn": st["n_det_dn"],
+                       "n_elec": N, "n_ao": st["n_ao"], "n_mo": st["n_mo"],
+                       "l2": "flushed between timed steps (512 MB write outside the events)",
+                       "parallelism": "dp%d (walkers)" % world},
+            "clocks": clk.summary(),
+            "e2e": {"value": W * world / (e2e_ms / 1e3), "unit": UNIT, "h2d_bytes_per_step": h2d,
+                    "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms},
+            "gpu_launches": 6 * args.steps,
+            "kernels_ms": kern,
+            "roofline": roofline}
+
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        from tests.parity import walker_quantiles
+        host = ctx.evaluate_host(batches[0])
+        ref, cb = cpu_baseline(wl, CPU_SAMPLE_WALKERS)
+        line["cpu_baseline"] = cb
+        line["accuracy_vs_oracle"] = dict(walkers=CPU_SAMPLE_WALKERS,
+                                          **walker_quantiles({k: v[:CPU_SAMPLE_WALKERS] for k, v in host.items()},
+                                                             ref))
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+def main():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=10)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--workload", default="chlorine_like_750k")
+    p.add_argument("--precision", default="fp64", choices=["mixed", "fp64"])
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--ref-sample", type=int, default=32)
+    p.add_argument("--traffic", type=float, default=None, help="DRAM bytes per launch of the dominant kernel (ncu)")
+    args = p.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,228 @@
+/*
+ * mdet.h -- C ABI of the GB300 multideterminant wavefunction library.
+ *
+ * The library evaluates a large multideterminant trial wavefunction
+ *   Psi(R) = sum_k c_k D^up_k(R_up) D^dn_k(R_dn) = D_up^T C D_dn      (Eqs. 1-2)
+ * together with grad_i Psi / Psi and Lap_i Psi / Psi for every electron and
+ * the local energy, for a batch of walkers per call (Sec. 2 and Sec. 4: one
+ * Monte Carlo step computes Psi, the drift vector and the local energy).
+ *
+ * Conventions shared by every entry point:
+ *  - Electrons 0 .. n_up-1 are spin up, n_up .. n_up+n_dn-1 spin down, and
+ *    n_up >= n_dn >= 1 (the convention of Sec. 2.4).
+ *  - A determinant of one spin is a bit string of n_int = ceil(n_mo / 64)
+ *    64-bit words; bit (m mod 64) of word (m div 64) is set when MO m
+ *    (0-based) is occupied (Sec. 2.1, "Encoding"). Its Slater matrix lists the
+ *    occupied MOs in ascending order: [S]_{i a} = phi_{o_a}(r_i), o_1 < o_2 < ...
+ *  - Positions and all floating-point outputs are double precision.
+ *  - "device pointer": memory the caller allocated on the context's device
+ *    (for instance a torch CUDA tensor); "host pointer": ordinary host memory.
+ *  - Every set_* call deep-copies its inputs; the caller keeps ownership of
+ *    every buffer it passes. The context owns its device copies and scratch.
+ *  - Functions return an mdet_status; no exception or abort crosses the ABI.
+ *    On error mdet_last_error() describes the failure.
+ *  - A context is not re-entrant: one thread and one stream at a time.
+ */
+#ifndef MDET_H
+#define MDET_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct mdet_ctx mdet_ctx;
+
+typedef enum {
+  MDET_OK = 0,
+  MDET_E_ARG = 1,      /* bad argument (null pointer, negative size, size beyond a limit) */
+  MDET_E_STATE = 2,    /* call order violated (e.g. evaluate before set_ci_expansion) */
+  MDET_E_OOM = 3,      /* host or device allocation failed */
+  MDET_E_CUDA = 4,     /* a CUDA runtime call or kernel launch failed */
+  MDET_E_INPUT = 5,    /* malformed expansion: wrong popcount, bits beyond n_mo, duplicate product */
+  MDET_E_TIMEOUT = 6,  /* a bounded device-side wait gave up */
+  MDET_E_NODEVICE = 7  /* the context has no device (created with device = MDET_NO_DEVICE) */
+} mdet_status;
+
+/* Arithmetic of the evaluation. */
+enum {
+  MDET_PRECISION_FP64 = 0,  /* every step in FP64 */
+  MDET_PRECISION_MIXED = 1  /* FP32 orbitals/tables/ratios; FP64 reference LU, log|D0| and CI contraction */
+};
+
+/* Device number meaning "no GPU": host preprocessing and introspection only. */
+#define MDET_NO_DEVICE (-1)
+
+/* Limits of this implementation. */
+#define MDET_MAX_SPIN_ELEC 32   /* n_up, n_dn <= 32 */
+#define MDET_MAX_MO 255         /* n_mo <= 255 */
+#define MDET_MAX_L 3            /* s, p, d, f shells */
+#define MDET_MAX_EXC 4          /* excitation degree of a spin determinant relative to the reference */
+
+/* Per-walker status bits written by mdet_evaluate. */
+#define MDET_WS_REF_SINGULAR 0x1u   /* a reference Slater matrix had a zero pivot: outputs are NaN */
+#define MDET_WS_REF_ILLCOND 0x2u    /* reference pivot ratio below 1e-13: results may lose accuracy */
+#define MDET_WS_PSI_ZERO 0x4u       /* Psi == 0 (walker on the nodal surface): log = -inf, sign 0, ratios NaN */
+#define MDET_WS_NONFINITE 0x8u      /* an output is Inf or NaN */
+
+typedef struct {
+  int32_t n_up, n_dn, n_ao, n_mo, n_int;
+  int64_t n_det;            /* products (nonzeros of C) */
+  int32_t n_det_up, n_det_dn;  /* distinct spin determinants (Sec. 1, N_det^sigma) */
+  int32_t max_degree[2];    /* largest excitation degree per spin */
+  int64_t degree_hist[2][MDET_MAX_EXC + 1];  /* spin determinants per excitation degree (cf. Table 4) */
+  int32_t precision;
+  int32_t device;
+} mdet_stats;
+
+/* Create a context on CUDA device `device` (or MDET_NO_DEVICE) with the given
+ * precision. *out receives the context; destroy it with mdet_destroy. */
+mdet_status mdet_create(mdet_ctx** out, int device, int precision);
+
+/* Release the context and every device buffer it owns. Null is ignored. */
+void mdet_destroy(mdet_ctx* ctx);
+
+/* Static description of a status code. */
+const char* mdet_status_string(mdet_status s);
+
+/* Detail of the last failure on this context (empty string if none). */
+const char* mdet_last_error(const mdet_ctx* ctx);
+
+/*
+ * The molecular system (Eq. 1: electron counts per spin; the nuclei enter the
+ * local energy's potential). Z: [n_nuc] charges, xyz: [n_nuc][3] positions,
+ * host pointers. Requires 1 <= n_dn <= n_up <= MDET_MAX_SPIN_ELEC.
+ * Invalidates any expansion already set (it fixes the determinant popcounts).
+ */
+mdet_status mdet_set_system(mdet_ctx* ctx, int n_up, int n_dn, int n_nuc,
+                            const double* Z, const double* xyz);
+
+/*
+ * Orbitals (Sec. 2, first paragraph: MOs and their gradients and Laplacian at
+ * every electron). Basis: n_shell contracted Cartesian Gaussian shells; shell s
+ * has angular momentum shell_l[s] in 0..3, is centred on nucleus
+ * shell_center[s] and has shell_nprim[s] primitives whose exponents and
+ * contraction coefficients are consecutive entries of alpha / coef (all
+ * shells concatenated). Its (l+1)(l+2)/2 AOs are x^a y^b z^c R(r), a+b+c = l,
+ * ordered a descending then b descending (xx, xy, xz, yy, yz, zz), with
+ * R(r) = sum_p coef_p exp(-alpha_p r^2) (normalisation is part of coef).
+ * mo_coef: [n_ao][n_mo] column-major (mo_coef[mu + n_ao*m]), phi_m = sum_mu
+ * mo_coef[mu, m] chi_mu. All host pointers. Requires set_system first and
+ * n_mo <= MDET_MAX_MO.
+ */
+mdet_status mdet_set_orbitals(mdet_ctx* ctx, int n_shell, const int32_t* shell_l,
+                              const int32_t* shell_center, const int32_t* shell_nprim,
+                              const double* alpha, const double* coef,
+                              int n_mo, const double* mo_coef);
+
+/*
+ * The CI expansion (Eq. 1) and its preprocessing (Sec. 2.1), on the host:
+ * the spin determinants of each spin are sorted by the key of Eq. 3 with a
+ * radix sort and deduplicated; C becomes a sparse matrix over the distinct
+ * determinants ordered column by column (key N_up*(j-1)+i); each distinct
+ * determinant is stored as its excitation (holes, particles, phase) relative
+ * to the reference determinant of its spin, the spin part of the largest |c_k|
+ * product, and the list is grouped by excitation degree.
+ * det_up, det_dn: [n_det][n_int] host bit strings; coef: [n_det] host.
+ * Fails with MDET_E_INPUT on a wrong popcount, a bit at or beyond n_mo, a
+ * duplicate (up, dn) product, or a degree above MDET_MAX_EXC. Requires
+ * set_system and set_orbitals (n_int must equal ceil(n_mo/64)).
+ */
+mdet_status mdet_set_ci_expansion(mdet_ctx* ctx, int64_t n_det, int n_int,
+                                  const uint64_t* det_up, const uint64_t* det_dn,
+                                  const double* coef);
+
+/*
+ * One evaluation of the hot path for n_walk walkers (Sec. 2.2-2.4): orbitals,
+ * reference LU per spin, ratio tables, per-determinant ratios and their
+ * derivative contributions, the sparse bilinear contraction, and the
+ * epilogue. Asynchronous on `stream` (a cudaStream_t, or null for the legacy
+ * default stream); all pointers are device pointers on the context's device:
+ *   R            [n_walk][n_up+n_dn][3]  positions (input)
+ *   log_abs_psi  [n_walk]   log|Psi|
+ *   sign         [n_walk]   sign of Psi (-1, 0, +1)
+ *   grad         [n_walk][n_up+n_dn][3]  grad_i Psi / Psi
+ *   lap          [n_walk][n_up+n_dn]     Lap_i Psi / Psi
+ *   e_local      [n_walk]   local energy (may be null)
+ *   status       [n_walk]   MDET_WS_* bits (may be null)
+ * n_walk = 0 is a no-op. Scratch grows to the largest n_walk seen (a
+ * synchronous allocation on first use at a new size).
+ */
+mdet_status mdet_evaluate(mdet_ctx* ctx, int64_t n_walk, const double* R,
+                          double* log_abs_psi, int8_t* sign, double* grad, double* lap,
+                          double* e_local, uint32_t* status, void* stream);
+
+/*
+ * The same evaluation from and to HOST memory: copies R to the device, runs
+ * mdet_evaluate on the context's internal stream, copies every output back
+ * and synchronises. Output pointers may be null to skip that copy (except
+ * log_abs_psi). Pinned host memory makes the copies faster but is not required.
+ */
+mdet_status mdet_evaluate_host(mdet_ctx* ctx, int64_t n_walk, const double* R,
+                               double* log_abs_psi, int8_t* sign, double* grad, double* lap,
+                               double* e_local, uint32_t* status);
+
+/*
+ * Intermediate values of the last mdet_evaluate on this context, copied to
+ * host memory for inspection: r_up [n_walk][n_det_up] and r_dn
+ * [n_walk][n_det_dn] are the ratios D_I / D_ref of every distinct spin
+ * determinant (in the context's order, see mdet_get_spin_dets), log_d0
+ * [n_walk][2] and sign_d0 [n_walk][2] the reference determinants. Any pointer
+ * may be null. Synchronises the stream of the last evaluation.
+ */
+mdet_status mdet_get_ratios(mdet_ctx* ctx, int64_t n_walk, double* r_up, double* r_dn,
+                            double* log_d0, int8_t* sign_d0);
+
+/*
+ * Stage timing. With profiling on, every mdet_evaluate records CUDA events on
+ * its stream around each stage; mdet_get_profile waits for the last one and
+ * writes the durations in milliseconds of the last evaluation, in the order
+ * MDET_STAGE_* below (ms: [MDET_N_STAGES]). Off by default.
+ */
+enum {
+  MDET_STAGE_ORBITALS = 0,  /* AO values and AO->MO product (Sec. 2) */
+  MDET_STAGE_REFERENCE = 1, /* reference LU, inverse, tables (Sec. 2.2, Sec. 5) */
+  MDET_STAGE_RATIOS = 2,    /* determinant ratios (Sec. 2.2) */
+  MDET_STAGE_ZERO = 3,      /* clearing of the contraction accumulators */
+  MDET_STAGE_CONTRACT = 4,  /* sparse bilinear contraction (Sec. 2.4) */
+  MDET_STAGE_FINAL = 5,     /* derivative aggregation and epilogue (Sec. 2.3) */
+  MDET_N_STAGES = 6
+};
+mdet_status mdet_set_profiling(mdet_ctx* ctx, int enable);
+mdet_status mdet_get_profile(mdet_ctx* ctx, float* ms);
+
+/* Sizes and excitation statistics (host only; works without a device). */
+mdet_status mdet_get_stats(const mdet_ctx* ctx, mdet_stats* out);
+
+/*
+ * The distinct determinants of one spin (0 up, 1 down) in the context's
+ * order (reference first, then by excitation degree, then by the key of
+ * Eq. 3): dets [n][n_int] bit strings, degree [n], phase [n] (the sign that
+ * turns the reference-ordered substituted matrix into the ascending one).
+ * Any pointer may be null. Host only.
+ */
+mdet_status mdet_get_spin_dets(const mdet_ctx* ctx, int spin, uint64_t* dets, int32_t* degree,
+                               int8_t* phase);
+
+/*
+ * The sparse C matrix over the distinct determinants in the paper's column-
+ * major order (Sec. 2.1): row[k] (up index), col[k] (down index), val[k],
+ * k < n_det. Host only.
+ */
+mdet_status mdet_get_ci_matrix(const mdet_ctx* ctx, int32_t* row, int32_t* col, double* val);
+
+/*
+ * The sort of Sec. 2.1 on its own: order[] receives the permutation that
+ * sorts n bit-string determinants [n][n_int] by the key of Eq. 3
+ * (omega = i_1 xor ... xor i_{n_int}, compared as unsigned 64-bit; ties broken
+ * by the words from the last to the first, unsigned), computed with an LSD
+ * radix sort. Host only.
+ */
+mdet_status mdet_omega_sort(int64_t n, int n_int, const uint64_t* dets, int64_t* order);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MDET_H */

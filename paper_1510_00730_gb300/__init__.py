@@ -1,0 +1,12 @@
+"""GB300-native evaluation of large multideterminant QMC wavefunctions.
+
+The compute path lives in the CUDA library libmdet.so (C ABI in
+include/mdet.h); this package only marshals arguments to it. Importing the
+package does not need a GPU; evaluating does, and fails loudly when the
+library or the device is missing.
+"""
+from .binding import (Context, MdetError, PRECISION_FP64, PRECISION_MIXED, WS_NONFINITE, WS_PSI_ZERO,
+                      WS_REF_ILLCOND, WS_REF_SINGULAR, library_path, load_library, omega_sort)
+
+__all__ = ["Context", "MdetError", "PRECISION_FP64", "PRECISION_MIXED", "WS_REF_SINGULAR", "WS_REF_ILLCOND",
+           "WS_PSI_ZERO", "WS_NONFINITE", "library_path", "load_library", "omega_sort"]

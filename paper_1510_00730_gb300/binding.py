@@ -1,0 +1,256 @@
+"""Thin ctypes binding of libmdet.so: argument marshalling only.
+
+Names follow the C ABI (include/mdet.h). Device buffers are torch CUDA
+tensors; torch provides memory and the current stream, every step of the
+evaluation runs in the library's kernels.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+from . import build as _build
+
+PRECISION_FP64 = 0
+PRECISION_MIXED = 1
+NO_DEVICE = -1
+WS_REF_SINGULAR = 0x1
+WS_REF_ILLCOND = 0x2
+WS_PSI_ZERO = 0x4
+WS_NONFINITE = 0x8
+MAX_EXC = 4
+
+_lib = None
+
+
+class MdetError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(msg)
+        self.status = status
+
+
+class _Stats(C.Structure):
+    _fields_ = [("n_up", C.c_int32), ("n_dn", C.c_int32), ("n_ao", C.c_int32), ("n_mo", C.c_int32),
+                ("n_int", C.c_int32), ("n_det", C.c_int64), ("n_det_up", C.c_int32), ("n_det_dn", C.c_int32),
+                ("max_degree", C.c_int32 * 2), ("degree_hist", (C.c_int64 * (MAX_EXC + 1)) * 2),
+                ("precision", C.c_int32), ("device", C.c_int32)]
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load_library(build_if_missing: bool = True):
+    """Load libmdet.so (building it first if allowed). Raises if it cannot be loaded."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(_build.LIB):
+        if not build_if_missing:
+            raise RuntimeError("libmdet.so is not built (run __graft_entry__.build())")
+        _build.build()
+    L = C.CDLL(_build.LIB)
+    vp, i64, i32 = C.c_void_p, C.c_int64, C.c_int
+    L.mdet_create.argtypes = [C.POINTER(vp), i32, i32]
+    L.mdet_destroy.argtypes = [vp]
+    L.mdet_destroy.restype = None
+    L.mdet_status_string.argtypes = [i32]
+    L.mdet_status_string.restype = C.c_char_p
+    L.mdet_last_error.argtypes = [vp]
+    L.mdet_last_error.restype = C.c_char_p
+    L.mdet_set_system.argtypes = [vp, i32, i32, i32, vp, vp]
+    L.mdet_set_orbitals.argtypes = [vp, i32, vp, vp, vp, vp, vp, i32, vp]
+    L.mdet_set_ci_expansion.argtypes = [vp, i64, i32, vp, vp, vp]
+    L.mdet_evaluate.argtypes = [vp, i64, vp, vp, vp, vp, vp, vp, vp, vp]
+    L.mdet_evaluate_host.argtypes = [vp, i64, vp, vp, vp, vp, vp, vp, vp]
+    L.mdet_get_ratios.argtypes = [vp, i64, vp, vp, vp, vp]
+    L.mdet_get_stats.argtypes = [vp, C.POINTER(_Stats)]
+    L.mdet_get_spin_dets.argtypes = [vp, i32, vp, vp, vp]
+    L.mdet_get_ci_matrix.argtypes = [vp, vp, vp, vp]
+    L.mdet_omega_sort.argtypes = [i64, i32, vp, vp]
+    L.mdet_set_profiling.argtypes = [vp, i32]
+    L.mdet_get_profile.argtypes = [vp, vp]
+    for name in ("mdet_create", "mdet_set_system", "mdet_set_orbitals", "mdet_set_ci_expansion", "mdet_evaluate",
+                 "mdet_evaluate_host", "mdet_get_ratios", "mdet_get_stats", "mdet_get_spin_dets",
+                 "mdet_get_ci_matrix", "mdet_omega_sort", "mdet_set_profiling", "mdet_get_profile"):
+        getattr(L, name).restype = i32
+    _lib = L
+    return L
+
+
+def _ptr(a) -> int:
+    return a.ctypes.data if a is not None else None
+
+
+def _c(a, dt):
+    return np.ascontiguousarray(a, dtype=dt)
+
+
+def omega_sort(dets) -> np.ndarray:
+    """Permutation sorting bit-string determinants [n][n_int] by the key of Eq. 3."""
+    L = load_library()
+    d = _c(dets, np.uint64)
+    if d.ndim == 1:
+        d = d[:, None]
+    order = np.empty(d.shape[0], np.int64)
+    st = L.mdet_omega_sort(d.shape[0], d.shape[1], _ptr(d), _ptr(order))
+    if st:
+        raise MdetError(st, "mdet_omega_sort failed")
+    return order
+
+
+class Context:
+    """One expansion resident on one device (or host-only with device=-1)."""
+
+    def __init__(self, device: int = 0, precision: int | str = PRECISION_FP64):
+        if isinstance(precision, str):
+            precision = {"fp64": PRECISION_FP64, "mixed": PRECISION_MIXED}[precision]
+        self._L = load_library()
+        h = C.c_void_p()
+        st = self._L.mdet_create(C.byref(h), int(device), int(precision))
+        if st:
+            raise MdetError(st, "mdet_create(device=%d) failed: %s" % (device, self._L.mdet_status_string(st).decode()))
+        self._h = h
+        self.device = int(device)
+        self.precision = int(precision)
+        self.n_up = self.n_dn = 0
+        self._keep = []
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            self._L.mdet_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _check(self, st, what):
+        if st:
+            msg = self._L.mdet_last_error(self._h).decode()
+            raise MdetError(st, "%s: %s (%s)" % (what, self._L.mdet_status_string(st).decode(), msg))
+
+    # -- set-up -------------------------------------------------------------
+    def set_system(self, n_up, n_dn, Z, nuc_xyz):
+        Z = _c(Z, np.float64)
+        X = _c(nuc_xyz, np.float64)
+        self._check(self._L.mdet_set_system(self._h, int(n_up), int(n_dn), Z.shape[0], _ptr(Z), _ptr(X)),
+                    "mdet_set_system")
+        self.n_up, self.n_dn = int(n_up), int(n_dn)
+
+    def set_orbitals(self, shell_l, shell_center, shell_nprim, alpha, coef, mo_coef):
+        """mo_coef: [n_ao, n_mo] array (column m = MO m)."""
+        l_, c_, n_ = _c(shell_l, np.int32), _c(shell_center, np.int32), _c(shell_nprim, np.int32)
+        a_, k_ = _c(alpha, np.float64), _c(coef, np.float64)
+        mo = np.asarray(mo_coef, dtype=np.float64)
+        mo_cm = _c(mo.T, np.float64)  # column-major n_ao x n_mo
+        self._check(self._L.mdet_set_orbitals(self._h, l_.shape[0], _ptr(l_), _ptr(c_), _ptr(n_), _ptr(a_), _ptr(k_),
+                                              mo.shape[1], _ptr(mo_cm)), "mdet_set_orbitals")
+
+    def set_ci_expansion(self, det_up, det_dn, coef):
+        du, dd, cf = _c(det_up, np.uint64), _c(det_dn, np.uint64), _c(coef, np.float64)
+        self._check(self._L.mdet_set_ci_expansion(self._h, cf.shape[0], du.shape[1], _ptr(du), _ptr(dd), _ptr(cf)),
+                    "mdet_set_ci_expansion")
+
+    @classmethod
+    def from_workload(cls, wl, device=0, precision=PRECISION_FP64):
+        ctx = cls(device, precision)
+        ctx.set_system(wl.n_up, wl.n_dn, wl.Z, wl.nuc_xyz)
+        ctx.set_orbitals(wl.shell_l, wl.shell_center, wl.shell_nprim, wl.alpha, wl.coef, wl.mo_coef)
+        ctx.set_ci_expansion(wl.det_up, wl.det_dn, wl.ci_coef)
+        return ctx
+
+    # -- evaluation ---------------------------------------------------------
+    def alloc_outputs(self, n_walk):
+        import torch
+        dev = torch.device("cuda", self.device)
+        N = self.n_up + self.n_dn
+        return dict(log_abs_psi=torch.empty(n_walk, dtype=torch.float64, device=dev),
+                    sign=torch.empty(n_walk, dtype=torch.int8, device=dev),
+                    grad=torch.empty(n_walk, N, 3, dtype=torch.float64, device=dev),
+                    lap=torch.empty(n_walk, N, dtype=torch.float64, device=dev),
+                    e_local=torch.empty(n_walk, dtype=torch.float64, device=dev),
+                    status=torch.empty(n_walk, dtype=torch.int32, device=dev))
+
+    def evaluate(self, R, out=None, stream=None):
+        """R: CUDA float64 tensor [n_walk, n_up+n_dn, 3] on this context's device.
+        Returns (and fills) a dict of device tensors; asynchronous on `stream`
+        (default: torch's current stream)."""
+        import torch
+        if not (R.is_cuda and R.dtype == torch.float64 and R.is_contiguous()):
+            raise ValueError("R must be a contiguous CUDA float64 tensor")
+        n_walk = R.shape[0]
+        if out is None:
+            out = self.alloc_outputs(n_walk)
+        if stream is None:
+            stream = torch.cuda.current_stream(R.device)
+        sp = stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream)
+        self._check(self._L.mdet_evaluate(self._h, n_walk, R.data_ptr(), out["log_abs_psi"].data_ptr(),
+                                          out["sign"].data_ptr(), out["grad"].data_ptr(), out["lap"].data_ptr(),
+                                          out["e_local"].data_ptr(), out["status"].data_ptr(), sp), "mdet_evaluate")
+        return out
+
+    def evaluate_host(self, R, out=None):
+        """Host-memory evaluation (copies inside the call); returns numpy arrays."""
+        R = _c(R, np.float64)
+        n_walk = R.shape[0]
+        N = self.n_up + self.n_dn
+        if out is None:
+            out = dict(log_abs_psi=np.empty(n_walk), sign=np.empty(n_walk, np.int8), grad=np.empty((n_walk, N, 3)),
+                       lap=np.empty((n_walk, N)), e_local=np.empty(n_walk), status=np.empty(n_walk, np.uint32))
+        self._check(self._L.mdet_evaluate_host(self._h, n_walk, _ptr(R), _ptr(out["log_abs_psi"]), _ptr(out["sign"]),
+                                               _ptr(out["grad"]), _ptr(out["lap"]), _ptr(out["e_local"]),
+                                               _ptr(out["status"])), "mdet_evaluate_host")
+        return out
+
+    def ratios(self, n_walk):
+        s = self.stats()
+        r_up = np.empty((n_walk, s["n_det_up"]))
+        r_dn = np.empty((n_walk, s["n_det_dn"]))
+        ld0 = np.empty((n_walk, 2))
+        sg0 = np.empty((n_walk, 2), np.int8)
+        self._check(self._L.mdet_get_ratios(self._h, n_walk, _ptr(r_up), _ptr(r_dn), _ptr(ld0), _ptr(sg0)),
+                    "mdet_get_ratios")
+        return r_up, r_dn, ld0, sg0
+
+    STAGES = ("orbitals", "reference", "ratios", "zero", "contract", "final")
+
+    def set_profiling(self, enable=True):
+        self._check(self._L.mdet_set_profiling(self._h, int(bool(enable))), "mdet_set_profiling")
+
+    def profile(self):
+        """Stage durations (ms) of the last profiled evaluation."""
+        ms = (C.c_float * len(self.STAGES))()
+        self._check(self._L.mdet_get_profile(self._h, ms), "mdet_get_profile")
+        return dict(zip(self.STAGES, [float(x) for x in ms]))
+
+    # -- introspection (host only) -------------------------------------------
+    def stats(self):
+        s = _Stats()
+        self._check(self._L.mdet_get_stats(self._h, C.byref(s)), "mdet_get_stats")
+        return dict(n_up=s.n_up, n_dn=s.n_dn, n_ao=s.n_ao, n_mo=s.n_mo, n_int=s.n_int, n_det=s.n_det,
+                    n_det_up=s.n_det_up, n_det_dn=s.n_det_dn, max_degree=list(s.max_degree),
+                    degree_hist=[list(s.degree_hist[0]), list(s.degree_hist[1])],
+                    precision=s.precision, device=s.device)
+
+    def spin_dets(self, spin):
+        s = self.stats()
+        n = s["n_det_up"] if spin == 0 else s["n_det_dn"]
+        dets = np.empty((n, s["n_int"]), np.uint64)
+        deg = np.empty(n, np.int32)
+        ph = np.empty(n, np.int8)
+        self._check(self._L.mdet_get_spin_dets(self._h, int(spin), _ptr(dets), _ptr(deg), _ptr(ph)),
+                    "mdet_get_spin_dets")
+        return dets, deg, ph
+
+    def ci_matrix(self):
+        n = self.stats()["n_det"]
+        row = np.empty(n, np.int32)
+        col = np.empty(n, np.int32)
+        val = np.empty(n)
+        self._check(self._L.mdet_get_ci_matrix(self._h, _ptr(row), _ptr(col), _ptr(val)), "mdet_get_ci_matrix")
+        return row, col, val

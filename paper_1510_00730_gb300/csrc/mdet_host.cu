@@ -1,0 +1,709 @@
+// Host side of the C ABI: context, validation, the preprocessing of Sec. 2.1,
+// device residency and the launch sequence of one evaluation.
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "mdet_internal.h"
+
+using namespace mdet;
+
+struct mdet_ctx {
+  int device = MDET_NO_DEVICE;
+  int precision = MDET_PRECISION_FP64;
+  std::string err;
+  // system
+  bool has_system = false, has_orbitals = false, has_ci = false;
+  int n_up = 0, n_dn = 0, n_nuc = 0;
+  std::vector<double> Z, nuc_xyz;
+  // orbitals
+  int n_shell = 0, n_ao = 0, n_mo = 0, n_prim = 0;
+  std::vector<int> shell_l, shell_center, shell_nprim, shell_prim0, shell_ao0;
+  std::vector<double> alpha, coef, mo_colmajor;
+  // expansion after preprocessing
+  int64_t n_det = 0;
+  int n_int = 0;
+  std::vector<uint64_t> dets[2];   // distinct determinants in context order [n][n_int]
+  std::vector<int> degree[2];
+  std::vector<Exc> exc[2];
+  std::vector<int> ref_occ[2];
+  std::vector<int32_t> coo_row, coo_col;  // column-major order (Sec. 2.1)
+  std::vector<double> coo_val;
+  std::vector<int32_t> csr_row, csr_col;  // row-major order
+  std::vector<double> csr_val;
+  // device residency
+  std::vector<void*> dev_problem_allocs;
+  DevProblem P{};
+  DevScratch S{};
+  cudaStream_t own_stream = nullptr;
+  cudaStream_t last_stream = nullptr;
+  int64_t last_walk = 0;
+  // stage timing
+  bool profiling = false;
+  bool have_profile = false;
+  cudaEvent_t ev[MDET_N_STAGES + 1] = {};
+};
+
+namespace {
+
+mdet_status fail(mdet_ctx* c, mdet_status s, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  if (c) c->err = buf;
+  return s;
+}
+
+#define CUDA_TRY(ctx, call)                                                                \
+  do {                                                                                     \
+    cudaError_t e_ = (call);                                                               \
+    if (e_ != cudaSuccess)                                                                 \
+      return fail(ctx, MDET_E_CUDA, "%s failed: %s", #call, cudaGetErrorString(e_));       \
+  } while (0)
+
+int popcount_words(const uint64_t* w, int n_int) {
+  int c = 0;
+  for (int q = 0; q < n_int; q++) c += __builtin_popcountll(w[q]);
+  return c;
+}
+
+uint64_t omega_key(const uint64_t* w, int n_int) {
+  // Eq. 3: xor of the words. The -2^63 shift of the paper only emulates an
+  // unsigned comparison with signed integers; here the key is compared unsigned.
+  uint64_t k = 0;
+  for (int q = 0; q < n_int; q++) k ^= w[q];
+  return k;
+}
+
+// Compare two determinants by (omega, words from the last to the first), unsigned.
+int cmp_det(const uint64_t* a, const uint64_t* b, int n_int) {
+  uint64_t ka = omega_key(a, n_int), kb = omega_key(b, n_int);
+  if (ka != kb) return ka < kb ? -1 : 1;
+  for (int q = n_int - 1; q >= 0; q--)
+    if (a[q] != b[q]) return a[q] < b[q] ? -1 : 1;
+  return 0;
+}
+
+// LSD radix sort of indices by a 64-bit key, 8 bits per pass; stable.
+void radix_sort_u64(std::vector<int64_t>& idx, const std::vector<uint64_t>& key) {
+  const size_t n = idx.size();
+  std::vector<int64_t> tmp(n);
+  for (int pass = 0; pass < 8; pass++) {
+    const int sh = 8 * pass;
+    size_t cnt[257] = {0};
+    bool all_same = true;
+    uint64_t first = n ? (key[idx[0]] >> sh) & 0xff : 0;
+    for (size_t i = 0; i < n; i++) {
+      uint64_t d = (key[idx[i]] >> sh) & 0xff;
+      cnt[d + 1]++;
+      all_same &= (d == first);
+    }
+    if (all_same) continue;
+    for (int d = 0; d < 256; d++) cnt[d + 1] += cnt[d];
+    for (size_t i = 0; i < n; i++) tmp[cnt[(key[idx[i]] >> sh) & 0xff]++] = idx[i];
+    idx.swap(tmp);
+  }
+}
+
+// Permutation sorting determinants by the key of Eq. 3 (radix sort), ties
+// broken by the full words (only groups of equal keys are compared).
+std::vector<int64_t> omega_order(int64_t n, int n_int, const uint64_t* dets) {
+  std::vector<uint64_t> key(n);
+  for (int64_t k = 0; k < n; k++) key[k] = omega_key(dets + k * n_int, n_int);
+  std::vector<int64_t> idx(n);
+  for (int64_t k = 0; k < n; k++) idx[k] = k;
+  radix_sort_u64(idx, key);
+  if (n_int > 1) {
+    int64_t a = 0;
+    while (a < n) {
+      int64_t b = a + 1;
+      while (b < n && key[idx[b]] == key[idx[a]]) b++;
+      if (b - a > 1)
+        std::stable_sort(idx.begin() + a, idx.begin() + b, [&](int64_t x, int64_t y) {
+          return cmp_det(dets + x * n_int, dets + y * n_int, n_int) < 0;
+        });
+      a = b;
+    }
+  }
+  return idx;
+}
+
+std::vector<int> decode_occ(const uint64_t* w, int n_int) {
+  std::vector<int> occ;
+  for (int q = 0; q < n_int; q++)
+    for (int b = 0; b < 64; b++)
+      if ((w[q] >> b) & 1ULL) occ.push_back(64 * q + b);
+  return occ;
+}
+
+// Sign of the permutation that sorts `cols` ascending (inversion parity).
+int sort_parity(const std::vector<int>& cols) {
+  int inv = 0;
+  for (size_t i = 0; i < cols.size(); i++)
+    for (size_t j = i + 1; j < cols.size(); j++)
+      if (cols[i] > cols[j]) inv++;
+  return (inv & 1) ? -1 : 1;
+}
+
+template <class T>
+mdet_status upload(mdet_ctx* c, const std::vector<T>& v, const T** out) {
+  void* p = nullptr;
+  size_t bytes = std::max<size_t>(sizeof(T), v.size() * sizeof(T));
+  cudaError_t e = cudaMalloc(&p, bytes);
+  if (e != cudaSuccess) return fail(c, MDET_E_OOM, "cudaMalloc(%zu) failed: %s", bytes, cudaGetErrorString(e));
+  c->dev_problem_allocs.push_back(p);
+  if (!v.empty()) {
+    e = cudaMemcpy(p, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return fail(c, MDET_E_CUDA, "cudaMemcpy failed: %s", cudaGetErrorString(e));
+  }
+  *out = static_cast<const T*>(p);
+  return MDET_OK;
+}
+
+void free_problem(mdet_ctx* c) {
+  for (void* p : c->dev_problem_allocs) cudaFree(p);
+  c->dev_problem_allocs.clear();
+  c->P = DevProblem{};
+}
+
+void free_scratch(mdet_ctx* c) {
+  DevScratch& S = c->S;
+  void* ptrs[] = {S.phi, S.phi32, S.Ainv, S.ld0, S.sg0, S.g, S.T, S.T32, S.r, S.vu, S.psit, S.wstat,
+                  S.R_stage, S.out_stage};
+  for (void* p : ptrs)
+    if (p) cudaFree(p);
+  S = DevScratch{};
+}
+
+// Upload everything the kernels read (called once the expansion is complete).
+mdet_status upload_problem(mdet_ctx* c) {
+  if (c->device < 0) return MDET_OK;
+  CUDA_TRY(c, cudaSetDevice(c->device));
+  free_problem(c);
+  DevProblem& P = c->P;
+  P.n_up = c->n_up; P.n_dn = c->n_dn; P.n_elec = c->n_up + c->n_dn; P.n_nuc = c->n_nuc;
+  P.n_shell = c->n_shell; P.n_ao = c->n_ao; P.n_mo = c->n_mo; P.n_prim = c->n_prim;
+  P.n_det_sp[0] = (int)c->exc[0].size();
+  P.n_det_sp[1] = (int)c->exc[1].size();
+  P.nnz = c->n_det;
+  mdet_status s;
+#define UP(vec, dst) if ((s = upload(c, vec, &dst)) != MDET_OK) return s
+  UP(c->Z, P.Z);
+  UP(c->nuc_xyz, P.nuc_xyz);
+  UP(c->shell_l, P.shell_l);
+  UP(c->shell_center, P.shell_center);
+  UP(c->shell_nprim, P.shell_nprim);
+  UP(c->shell_prim0, P.shell_prim0);
+  UP(c->shell_ao0, P.shell_ao0);
+  UP(c->alpha, P.alpha);
+  UP(c->coef, P.coef);
+  std::vector<double> B((size_t)c->n_ao * c->n_mo);
+  std::vector<float> B32(B.size());
+  for (int mu = 0; mu < c->n_ao; mu++)
+    for (int m = 0; m < c->n_mo; m++) {
+      B[(size_t)mu * c->n_mo + m] = c->mo_colmajor[mu + (size_t)c->n_ao * m];
+      B32[(size_t)mu * c->n_mo + m] = (float)B[(size_t)mu * c->n_mo + m];
+    }
+  UP(B, P.B);
+  UP(B32, P.B32);
+  std::vector<int> occ(2 * kMaxSpin, 0);
+  for (int sp = 0; sp < 2; sp++)
+    for (size_t a = 0; a < c->ref_occ[sp].size(); a++) occ[sp * kMaxSpin + a] = c->ref_occ[sp][a];
+  UP(occ, P.ref_occ);
+  UP(c->exc[0], P.exc[0]);
+  UP(c->exc[1], P.exc[1]);
+  UP(c->csr_row, P.csr_row);
+  UP(c->csr_col, P.csr_col);
+  UP(c->csr_val, P.csr_val);
+  UP(c->coo_col, P.csc_col);
+  UP(c->coo_row, P.csc_row);
+  UP(c->coo_val, P.csc_val);
+#undef UP
+  free_scratch(c);  // sizes depend on the problem
+  return MDET_OK;
+}
+
+template <class T>
+mdet_status dalloc(mdet_ctx* c, T** p, size_t count) {
+  size_t bytes = std::max<size_t>(count, 1) * sizeof(T);
+  cudaError_t e = cudaMalloc((void**)p, bytes);
+  if (e != cudaSuccess) {
+    *p = nullptr;
+    return fail(c, MDET_E_OOM, "cudaMalloc(%zu bytes) for scratch failed: %s", bytes, cudaGetErrorString(e));
+  }
+  return MDET_OK;
+}
+
+mdet_status ensure_scratch(mdet_ctx* c, int64_t n_walk) {
+  DevScratch& S = c->S;
+  if (n_walk <= S.cap_walk) return MDET_OK;
+  free_scratch(c);
+  const DevProblem& P = c->P;
+  const int64_t W = n_walk;
+  const int64_t wp = (W + kWalkerPad - 1) / kWalkerPad * kWalkerPad;
+  const int64_t N = P.n_elec, M = P.n_mo;
+  const int64_t ndt = (int64_t)P.n_det_sp[0] + P.n_det_sp[1];
+  mdet_status s;
+  if ((s = dalloc(c, &S.phi, (size_t)W * 5 * N * M))) return s;
+  if ((s = dalloc(c, &S.Ainv, (size_t)W * (P.n_up * P.n_up + P.n_dn * P.n_dn)))) return s;
+  if ((s = dalloc(c, &S.ld0, (size_t)W * 2))) return s;
+  if ((s = dalloc(c, &S.sg0, (size_t)W * 2))) return s;
+  if ((s = dalloc(c, &S.g, (size_t)W * N * 4))) return s;
+  if ((s = dalloc(c, &S.T, (size_t)N * M * wp))) return s;
+  if ((s = dalloc(c, &S.r, (size_t)ndt * wp))) return s;
+  if ((s = dalloc(c, &S.vu, (size_t)ndt * wp))) return s;
+  if ((s = dalloc(c, &S.psit, (size_t)wp))) return s;
+  if ((s = dalloc(c, &S.wstat, (size_t)W))) return s;
+  // padded walker columns of the tables must hold finite values
+  CUDA_TRY(c, cudaMemset(S.T, 0, sizeof(double) * N * M * wp));
+  S.cap_walk = W;
+  S.wp = wp;
+  return MDET_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* mdet_status_string(mdet_status s) {
+  switch (s) {
+    case MDET_OK: return "ok";
+    case MDET_E_ARG: return "invalid argument";
+    case MDET_E_STATE: return "call order violated";
+    case MDET_E_OOM: return "out of memory";
+    case MDET_E_CUDA: return "CUDA error";
+    case MDET_E_INPUT: return "malformed expansion";
+    case MDET_E_TIMEOUT: return "device wait timed out";
+    case MDET_E_NODEVICE: return "context has no device";
+  }
+  return "unknown status";
+}
+
+const char* mdet_last_error(const mdet_ctx* ctx) { return ctx ? ctx->err.c_str() : "null context"; }
+
+mdet_status mdet_create(mdet_ctx** out, int device, int precision) {
+  if (!out) return MDET_E_ARG;
+  *out = nullptr;
+  if (precision != MDET_PRECISION_FP64 && precision != MDET_PRECISION_MIXED) return MDET_E_ARG;
+  if (device < MDET_NO_DEVICE) return MDET_E_ARG;
+  mdet_ctx* c = new (std::nothrow) mdet_ctx();
+  if (!c) return MDET_E_OOM;
+  c->device = device;
+  c->precision = precision;
+  if (device >= 0) {
+    int n = 0;
+    if (cudaGetDeviceCount(&n) != cudaSuccess || device >= n) {
+      delete c;
+      return MDET_E_CUDA;
+    }
+    if (cudaSetDevice(device) != cudaSuccess || cudaStreamCreateWithFlags(&c->own_stream, cudaStreamNonBlocking) != cudaSuccess) {
+      delete c;
+      return MDET_E_CUDA;
+    }
+  }
+  *out = c;
+  return MDET_OK;
+}
+
+void mdet_destroy(mdet_ctx* c) {
+  if (!c) return;
+  if (c->device >= 0) {
+    cudaSetDevice(c->device);
+    cudaDeviceSynchronize();
+    free_scratch(c);
+    free_problem(c);
+    for (int i = 0; i <= MDET_N_STAGES; i++)
+      if (c->ev[i]) cudaEventDestroy(c->ev[i]);
+    if (c->own_stream) cudaStreamDestroy(c->own_stream);
+  }
+  delete c;
+}
+
+mdet_status mdet_set_system(mdet_ctx* c, int n_up, int n_dn, int n_nuc, const double* Z, const double* xyz) {
+  if (!c) return MDET_E_ARG;
+  if (n_dn < 1 || n_up < n_dn || n_up > kMaxSpin)
+    return fail(c, MDET_E_ARG, "need 1 <= n_dn <= n_up <= %d (got %d, %d)", kMaxSpin, n_up, n_dn);
+  if (n_nuc < 0 || (n_nuc > 0 && (!Z || !xyz))) return fail(c, MDET_E_ARG, "bad nuclei");
+  c->n_up = n_up;
+  c->n_dn = n_dn;
+  c->n_nuc = n_nuc;
+  c->Z.assign(Z, Z + n_nuc);
+  c->nuc_xyz.assign(xyz, xyz + 3 * n_nuc);
+  c->has_system = true;
+  c->has_ci = false;
+  c->err.clear();
+  return MDET_OK;
+}
+
+mdet_status mdet_set_orbitals(mdet_ctx* c, int n_shell, const int32_t* shell_l, const int32_t* shell_center,
+                              const int32_t* shell_nprim, const double* alpha, const double* coef, int n_mo,
+                              const double* mo_coef) {
+  if (!c) return MDET_E_ARG;
+  if (!c->has_system) return fail(c, MDET_E_STATE, "set_system must come first");
+  if (n_shell < 1 || !shell_l || !shell_center || !shell_nprim || !alpha || !coef || !mo_coef)
+    return fail(c, MDET_E_ARG, "null or empty basis");
+  if (n_mo < 1 || n_mo > MDET_MAX_MO) return fail(c, MDET_E_ARG, "n_mo must be in 1..%d", MDET_MAX_MO);
+  if (n_mo < c->n_up) return fail(c, MDET_E_ARG, "n_mo < n_up");
+  c->shell_l.assign(shell_l, shell_l + n_shell);
+  c->shell_center.assign(shell_center, shell_center + n_shell);
+  c->shell_nprim.assign(shell_nprim, shell_nprim + n_shell);
+  c->shell_prim0.resize(n_shell);
+  c->shell_ao0.resize(n_shell);
+  int np = 0, nao = 0;
+  for (int s = 0; s < n_shell; s++) {
+    if (shell_l[s] < 0 || shell_l[s] > kMaxL) return fail(c, MDET_E_ARG, "shell %d: l=%d outside 0..3", s, shell_l[s]);
+    if (shell_center[s] < 0 || shell_center[s] >= c->n_nuc) return fail(c, MDET_E_ARG, "shell %d: bad centre", s);
+    if (shell_nprim[s] < 1) return fail(c, MDET_E_ARG, "shell %d: no primitive", s);
+    c->shell_prim0[s] = np;
+    c->shell_ao0[s] = nao;
+    np += shell_nprim[s];
+    nao += (shell_l[s] + 1) * (shell_l[s] + 2) / 2;
+  }
+  if (n_mo > nao) return fail(c, MDET_E_ARG, "n_mo (%d) > n_ao (%d)", n_mo, nao);
+  c->n_shell = n_shell;
+  c->n_prim = np;
+  c->n_ao = nao;
+  c->n_mo = n_mo;
+  c->alpha.assign(alpha, alpha + np);
+  c->coef.assign(coef, coef + np);
+  c->mo_colmajor.assign(mo_coef, mo_coef + (size_t)nao * n_mo);
+  c->has_orbitals = true;
+  c->has_ci = false;
+  c->err.clear();
+  return MDET_OK;
+}
+
+mdet_status mdet_omega_sort(int64_t n, int n_int, const uint64_t* dets, int64_t* order) {
+  if (n < 0 || n_int < 1 || (n > 0 && (!dets || !order))) return MDET_E_ARG;
+  std::vector<int64_t> idx = omega_order(n, n_int, dets);
+  std::copy(idx.begin(), idx.end(), order);
+  return MDET_OK;
+}
+
+mdet_status mdet_set_ci_expansion(mdet_ctx* c, int64_t n_det, int n_int, const uint64_t* det_up,
+                                  const uint64_t* det_dn, const double* coef) {
+  if (!c) return MDET_E_ARG;
+  if (!c->has_system || !c->has_orbitals) return fail(c, MDET_E_STATE, "set_system and set_orbitals must come first");
+  if (n_det < 1 || !det_up || !det_dn || !coef) return fail(c, MDET_E_ARG, "empty expansion or null pointer");
+  if (n_det >= (int64_t)1 << 31) return fail(c, MDET_E_ARG, "n_det must be below 2^31");
+  const int want_int = (c->n_mo + 63) / 64;
+  if (n_int != want_int) return fail(c, MDET_E_ARG, "n_int=%d but ceil(n_mo/64)=%d", n_int, want_int);
+  c->has_ci = false;
+  const uint64_t* in[2] = {det_up, det_dn};
+  const int nel[2] = {c->n_up, c->n_dn};
+  // validation: popcount and bits beyond n_mo
+  for (int sp = 0; sp < 2; sp++)
+    for (int64_t k = 0; k < n_det; k++) {
+      const uint64_t* w = in[sp] + k * n_int;
+      if (popcount_words(w, n_int) != nel[sp])
+        return fail(c, MDET_E_INPUT, "product %lld: spin %d determinant has %d electrons, expected %d",
+                    (long long)k, sp, popcount_words(w, n_int), nel[sp]);
+      const int top = c->n_mo - 64 * (n_int - 1);  // valid bits in the last word
+      if (top < 64 && (w[n_int - 1] >> top) != 0)
+        return fail(c, MDET_E_INPUT, "product %lld: spin %d determinant occupies an MO >= n_mo", (long long)k, sp);
+    }
+  // reference product: the largest |c_k| (first one on ties)
+  int64_t kref = 0;
+  for (int64_t k = 1; k < n_det; k++)
+    if (std::fabs(coef[k]) > std::fabs(coef[kref])) kref = k;
+
+  std::vector<int32_t> idx_of[2];  // product -> context index of its spin determinant
+  for (int sp = 0; sp < 2; sp++) {
+    const uint64_t* D = in[sp];
+    // Sec. 2.1: radix sort by the key of Eq. 3, then remove duplicates among equal keys
+    std::vector<int64_t> ord = omega_order(n_det, n_int, D);
+    std::vector<int64_t> uniq;  // product index of each distinct determinant, in omega order
+    for (int64_t q = 0; q < n_det; q++)
+      if (q == 0 || cmp_det(D + ord[q] * n_int, D + ord[q - 1] * n_int, n_int) != 0) uniq.push_back(ord[q]);
+    const int64_t nu = (int64_t)uniq.size();
+    // position of every product's determinant in the distinct list: binary search (Sec. 2.1)
+    std::vector<int32_t> pos(n_det);
+    for (int64_t k = 0; k < n_det; k++) {
+      int64_t lo = 0, hi = nu - 1;
+      while (lo < hi) {
+        int64_t mid = (lo + hi) / 2;
+        if (cmp_det(D + uniq[mid] * n_int, D + k * n_int, n_int) < 0) lo = mid + 1; else hi = mid;
+      }
+      pos[k] = (int32_t)lo;
+    }
+    // reference determinant and excitation degrees relative to it
+    const int64_t iref = pos[kref];
+    const uint64_t* ref = D + uniq[iref] * n_int;
+    std::vector<int> deg(nu);
+    for (int64_t i = 0; i < nu; i++) {
+      const uint64_t* w = D + uniq[i] * n_int;
+      int h = 0;
+      for (int q = 0; q < n_int; q++) h += __builtin_popcountll(ref[q] & ~w[q]);
+      deg[i] = h;
+      if (h > kMaxExc)
+        return fail(c, MDET_E_INPUT, "spin %d determinant is a degree-%d excitation of the reference (max %d)", sp,
+                    h, kMaxExc);
+    }
+    // context order: reference first, then by degree, omega order within a degree (stable counting sort)
+    std::vector<int64_t> order;
+    order.reserve(nu);
+    order.push_back(iref);
+    for (int d = 1; d <= kMaxExc; d++)
+      for (int64_t i = 0; i < nu; i++)
+        if (deg[i] == d && i != iref) order.push_back(i);
+    std::vector<int32_t> ctx_of(nu);
+    for (int64_t t = 0; t < nu; t++) ctx_of[order[t]] = (int32_t)t;
+    idx_of[sp].resize(n_det);
+    for (int64_t k = 0; k < n_det; k++) idx_of[sp][k] = ctx_of[pos[k]];
+    // excitation records
+    std::vector<int> rocc = decode_occ(ref, n_int);
+    c->ref_occ[sp] = rocc;
+    c->dets[sp].assign((size_t)nu * n_int, 0);
+    c->degree[sp].assign(nu, 0);
+    c->exc[sp].assign(nu, Exc{});
+    for (int64_t t = 0; t < nu; t++) {
+      const uint64_t* w = D + uniq[order[t]] * n_int;
+      std::copy(w, w + n_int, c->dets[sp].begin() + t * n_int);
+      Exc e{};
+      std::vector<int> cols = rocc;  // reference columns with holes replaced by particles
+      int k = 0, kp = 0;
+      for (size_t a = 0; a < rocc.size(); a++) {
+        int m = rocc[a];
+        if (!((w[m / 64] >> (m % 64)) & 1ULL)) e.h[k++] = (uint8_t)a;
+      }
+      for (int q = 0; q < n_int; q++) {
+        uint64_t part = w[q] & ~ref[q];
+        while (part) {
+          int b = __builtin_ctzll(part);
+          part &= part - 1;
+          e.p[kp++] = (uint8_t)(64 * q + b);
+        }
+      }
+      if (k != kp) return fail(c, MDET_E_INPUT, "internal: hole/particle count mismatch");
+      for (int a = 0; a < k; a++) cols[e.h[a]] = e.p[a];
+      e.k = (uint8_t)k;
+      e.eps = (int8_t)sort_parity(cols);
+      c->exc[sp][t] = e;
+      c->degree[sp][t] = k;
+    }
+  }
+  // C in the paper's column-major order: radix sort of N_up * j + i
+  const int64_t nup = (int64_t)c->exc[0].size(), ndn = (int64_t)c->exc[1].size();
+  std::vector<uint64_t> key(n_det);
+  std::vector<int64_t> ord(n_det);
+  for (int64_t k = 0; k < n_det; k++) {
+    key[k] = (uint64_t)idx_of[1][k] * (uint64_t)nup + (uint64_t)idx_of[0][k];
+    ord[k] = k;
+  }
+  radix_sort_u64(ord, key);
+  for (int64_t q = 1; q < n_det; q++)
+    if (key[ord[q]] == key[ord[q - 1]])
+      return fail(c, MDET_E_INPUT, "products %lld and %lld repeat the same (up, down) pair", (long long)ord[q - 1],
+                  (long long)ord[q]);
+  c->coo_row.resize(n_det);
+  c->coo_col.resize(n_det);
+  c->coo_val.resize(n_det);
+  for (int64_t q = 0; q < n_det; q++) {
+    c->coo_row[q] = idx_of[0][ord[q]];
+    c->coo_col[q] = idx_of[1][ord[q]];
+    c->coo_val[q] = coef[ord[q]];
+  }
+  // row-major copy for the v = C D_dn product (Sec. 2.4)
+  for (int64_t k = 0; k < n_det; k++) {
+    key[k] = (uint64_t)idx_of[0][k] * (uint64_t)ndn + (uint64_t)idx_of[1][k];
+    ord[k] = k;
+  }
+  radix_sort_u64(ord, key);
+  c->csr_row.resize(n_det);
+  c->csr_col.resize(n_det);
+  c->csr_val.resize(n_det);
+  for (int64_t q = 0; q < n_det; q++) {
+    c->csr_row[q] = idx_of[0][ord[q]];
+    c->csr_col[q] = idx_of[1][ord[q]];
+    c->csr_val[q] = coef[ord[q]];
+  }
+  c->n_det = n_det;
+  c->n_int = n_int;
+  mdet_status s = upload_problem(c);
+  if (s != MDET_OK) return s;
+  c->has_ci = true;
+  c->err.clear();
+  return MDET_OK;
+}
+
+mdet_status mdet_evaluate(mdet_ctx* c, int64_t n_walk, const double* R, double* log_abs_psi, int8_t* sign,
+                          double* grad, double* lap, double* e_local, uint32_t* status, void* stream) {
+  if (!c) return MDET_E_ARG;
+  if (c->device < 0) return fail(c, MDET_E_NODEVICE, "context has no device");
+  if (!c->has_ci) return fail(c, MDET_E_STATE, "set_ci_expansion must come first");
+  if (n_walk < 0) return fail(c, MDET_E_ARG, "n_walk < 0");
+  if (n_walk == 0) return MDET_OK;
+  if (n_walk > (int64_t)1 << 30) return fail(c, MDET_E_ARG, "n_walk above 2^30");
+  if (!R || !log_abs_psi || !sign || !grad || !lap) return fail(c, MDET_E_ARG, "null device pointer");
+  if (c->precision != MDET_PRECISION_FP64) return fail(c, MDET_E_STATE, "mixed-precision kernels are not built yet");
+  CUDA_TRY(c, cudaSetDevice(c->device));
+  mdet_status s = ensure_scratch(c, n_walk);
+  if (s != MDET_OK) return s;
+  cudaStream_t st = (cudaStream_t)stream;
+  const DevProblem& P = c->P;
+  const DevScratch& S = c->S;
+  const bool prof = c->profiling;
+#define STAGE_EVENT(i) \
+  if (prof) CUDA_TRY(c, cudaEventRecord(c->ev[i], st))
+  STAGE_EVENT(0);
+  CUDA_TRY(c, launch_mo_f64(P, S, n_walk, R, st));
+  STAGE_EVENT(1);
+  CUDA_TRY(c, launch_ref_tables_f64(P, S, n_walk, st));
+  STAGE_EVENT(2);
+  CUDA_TRY(c, launch_ratios_f64(P, S, n_walk, st));
+  STAGE_EVENT(3);
+  CUDA_TRY(c, launch_zero_f64(P, S, n_walk, st));
+  STAGE_EVENT(4);
+  CUDA_TRY(c, launch_contract_f64(P, S, n_walk, st));
+  STAGE_EVENT(5);
+  CUDA_TRY(c, launch_final_f64(P, S, n_walk, R, log_abs_psi, sign, grad, lap, e_local, status, st));
+  STAGE_EVENT(6);
+#undef STAGE_EVENT
+  c->have_profile = prof;
+  c->last_stream = st;
+  c->last_walk = n_walk;
+  return MDET_OK;
+}
+
+mdet_status mdet_evaluate_host(mdet_ctx* c, int64_t n_walk, const double* R, double* log_abs_psi, int8_t* sign,
+                               double* grad, double* lap, double* e_local, uint32_t* status) {
+  if (!c) return MDET_E_ARG;
+  if (c->device < 0) return fail(c, MDET_E_NODEVICE, "context has no device");
+  if (!c->has_ci) return fail(c, MDET_E_STATE, "set_ci_expansion must come first");
+  if (n_walk < 0) return fail(c, MDET_E_ARG, "n_walk < 0");
+  if (n_walk == 0) return MDET_OK;
+  if (!R || !log_abs_psi) return fail(c, MDET_E_ARG, "null host pointer");
+  CUDA_TRY(c, cudaSetDevice(c->device));
+  mdet_status s = ensure_scratch(c, n_walk);
+  if (s != MDET_OK) return s;
+  DevScratch& S = c->S;
+  const int64_t N = c->n_up + c->n_dn;
+  const size_t nR = (size_t)n_walk * N * 3;
+  // staging: R, then outputs [log | sign(8 B slots) | grad | lap | e_local | status(8 B slots)]
+  const size_t nout = (size_t)n_walk * (1 + 1 + 3 * N + N + 1 + 1);
+  if (!S.R_stage) {
+    if ((s = dalloc(c, &S.R_stage, (size_t)S.cap_walk * N * 3))) return s;
+    if ((s = dalloc(c, &S.out_stage, (size_t)S.cap_walk * (4 + 4 * N)))) return s;
+  }
+  cudaStream_t st = c->own_stream;
+  double* d_log = S.out_stage;
+  int8_t* d_sign = (int8_t*)(d_log + n_walk);
+  double* d_grad = d_log + 2 * n_walk;
+  double* d_lap = d_grad + 3 * N * n_walk;
+  double* d_el = d_lap + N * n_walk;
+  uint32_t* d_st = (uint32_t*)(d_el + n_walk);
+  (void)nout;
+  CUDA_TRY(c, cudaMemcpyAsync(S.R_stage, R, nR * sizeof(double), cudaMemcpyHostToDevice, st));
+  s = mdet_evaluate(c, n_walk, S.R_stage, d_log, d_sign, d_grad, d_lap, d_el, d_st, st);
+  if (s != MDET_OK) return s;
+  CUDA_TRY(c, cudaMemcpyAsync(log_abs_psi, d_log, n_walk * sizeof(double), cudaMemcpyDeviceToHost, st));
+  if (sign) CUDA_TRY(c, cudaMemcpyAsync(sign, d_sign, n_walk * sizeof(int8_t), cudaMemcpyDeviceToHost, st));
+  if (grad) CUDA_TRY(c, cudaMemcpyAsync(grad, d_grad, 3 * N * n_walk * sizeof(double), cudaMemcpyDeviceToHost, st));
+  if (lap) CUDA_TRY(c, cudaMemcpyAsync(lap, d_lap, N * n_walk * sizeof(double), cudaMemcpyDeviceToHost, st));
+  if (e_local) CUDA_TRY(c, cudaMemcpyAsync(e_local, d_el, n_walk * sizeof(double), cudaMemcpyDeviceToHost, st));
+  if (status) CUDA_TRY(c, cudaMemcpyAsync(status, d_st, n_walk * sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
+  CUDA_TRY(c, cudaStreamSynchronize(st));
+  return MDET_OK;
+}
+
+mdet_status mdet_get_ratios(mdet_ctx* c, int64_t n_walk, double* r_up, double* r_dn, double* log_d0,
+                            int8_t* sign_d0) {
+  if (!c) return MDET_E_ARG;
+  if (c->device < 0) return fail(c, MDET_E_NODEVICE, "context has no device");
+  if (!c->has_ci || c->last_walk == 0) return fail(c, MDET_E_STATE, "no evaluation yet");
+  if (n_walk < 0 || n_walk > c->last_walk) return fail(c, MDET_E_ARG, "n_walk beyond the last evaluation");
+  CUDA_TRY(c, cudaSetDevice(c->device));
+  CUDA_TRY(c, cudaStreamSynchronize(c->last_stream));
+  const DevScratch& S = c->S;
+  const int64_t nu = c->exc[0].size(), nd = c->exc[1].size();
+  if (r_up || r_dn) {
+    std::vector<double> h((size_t)(nu + nd) * S.wp);
+    CUDA_TRY(c, cudaMemcpy(h.data(), S.r, h.size() * sizeof(double), cudaMemcpyDeviceToHost));
+    for (int64_t w = 0; w < n_walk; w++) {
+      if (r_up)
+        for (int64_t i = 0; i < nu; i++) r_up[w * nu + i] = h[(size_t)i * S.wp + w];
+      if (r_dn)
+        for (int64_t j = 0; j < nd; j++) r_dn[w * nd + j] = h[(size_t)(nu + j) * S.wp + w];
+    }
+  }
+  if (log_d0) CUDA_TRY(c, cudaMemcpy(log_d0, S.ld0, n_walk * 2 * sizeof(double), cudaMemcpyDeviceToHost));
+  if (sign_d0) {
+    std::vector<double> h(n_walk * 2);
+    CUDA_TRY(c, cudaMemcpy(h.data(), S.sg0, h.size() * sizeof(double), cudaMemcpyDeviceToHost));
+    for (size_t q = 0; q < h.size(); q++) sign_d0[q] = (int8_t)(h[q] > 0 ? 1 : (h[q] < 0 ? -1 : 0));
+  }
+  return MDET_OK;
+}
+
+mdet_status mdet_set_profiling(mdet_ctx* c, int enable) {
+  if (!c) return MDET_E_ARG;
+  if (c->device < 0) return fail(c, MDET_E_NODEVICE, "context has no device");
+  CUDA_TRY(c, cudaSetDevice(c->device));
+  if (enable && !c->ev[0])
+    for (int i = 0; i <= MDET_N_STAGES; i++) CUDA_TRY(c, cudaEventCreate(&c->ev[i]));
+  c->profiling = enable != 0;
+  c->have_profile = false;
+  return MDET_OK;
+}
+
+mdet_status mdet_get_profile(mdet_ctx* c, float* ms) {
+  if (!c || !ms) return MDET_E_ARG;
+  if (!c->have_profile) return fail(c, MDET_E_STATE, "no profiled evaluation yet");
+  CUDA_TRY(c, cudaSetDevice(c->device));
+  CUDA_TRY(c, cudaEventSynchronize(c->ev[MDET_N_STAGES]));
+  for (int i = 0; i < MDET_N_STAGES; i++) CUDA_TRY(c, cudaEventElapsedTime(&ms[i], c->ev[i], c->ev[i + 1]));
+  return MDET_OK;
+}
+
+mdet_status mdet_get_stats(const mdet_ctx* c, mdet_stats* out) {
+  if (!c || !out) return MDET_E_ARG;
+  std::memset(out, 0, sizeof *out);
+  out->n_up = c->n_up;
+  out->n_dn = c->n_dn;
+  out->n_ao = c->n_ao;
+  out->n_mo = c->n_mo;
+  out->n_int = c->n_int;
+  out->n_det = c->has_ci ? c->n_det : 0;
+  out->precision = c->precision;
+  out->device = c->device;
+  if (c->has_ci) {
+    out->n_det_up = (int32_t)c->exc[0].size();
+    out->n_det_dn = (int32_t)c->exc[1].size();
+    for (int sp = 0; sp < 2; sp++)
+      for (int d : c->degree[sp]) {
+        out->degree_hist[sp][d]++;
+        out->max_degree[sp] = std::max(out->max_degree[sp], d);
+      }
+  }
+  return MDET_OK;
+}
+
+mdet_status mdet_get_spin_dets(const mdet_ctx* c, int spin, uint64_t* dets, int32_t* degree, int8_t* phase) {
+  if (!c || (spin != 0 && spin != 1)) return MDET_E_ARG;
+  if (!c->has_ci) return MDET_E_STATE;
+  const size_t n = c->exc[spin].size();
+  if (dets) std::copy(c->dets[spin].begin(), c->dets[spin].end(), dets);
+  for (size_t t = 0; t < n; t++) {
+    if (degree) degree[t] = c->degree[spin][t];
+    if (phase) phase[t] = c->exc[spin][t].eps;
+  }
+  return MDET_OK;
+}
+
+mdet_status mdet_get_ci_matrix(const mdet_ctx* c, int32_t* row, int32_t* col, double* val) {
+  if (!c) return MDET_E_ARG;
+  if (!c->has_ci) return MDET_E_STATE;
+  if (row) std::copy(c->coo_row.begin(), c->coo_row.end(), row);
+  if (col) std::copy(c->coo_col.begin(), c->coo_col.end(), col);
+  if (val) std::copy(c->coo_val.begin(), c->coo_val.end(), val);
+  return MDET_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,93 @@
+// Internal data layout shared by the host side (mdet_host.cu) and the kernels.
+// Not part of the public ABI.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "../../include/mdet.h"
+
+namespace mdet {
+
+constexpr int kMaxSpin = MDET_MAX_SPIN_ELEC;
+constexpr int kMaxExc = MDET_MAX_EXC;
+constexpr int kMaxL = MDET_MAX_L;
+constexpr int kWalkerPad = 128;  // walker-minor arrays are padded to a multiple of this
+
+// Excitation of one distinct spin determinant relative to the reference of its
+// spin: columns h[0..k) of the reference Slater matrix (hole positions, in the
+// reference's ascending MO order) are replaced by MOs p[0..k) (particles);
+// eps is the sign that reorders the substituted columns ascending.
+struct __align__(16) Exc {
+  uint8_t k;
+  int8_t eps;
+  uint8_t pad0, pad1;
+  uint8_t h[kMaxExc];
+  uint8_t p[kMaxExc];
+  uint32_t pad2;
+};
+static_assert(sizeof(Exc) == 16, "Exc must be 16 bytes");
+
+// Read-only problem description resident on the device.
+struct DevProblem {
+  int n_up, n_dn, n_elec, n_nuc;
+  int n_shell, n_ao, n_mo, n_prim;
+  int n_det_sp[2];        // distinct determinants per spin
+  int64_t nnz;            // products
+  const double* Z;        // [n_nuc]
+  const double* nuc_xyz;  // [n_nuc][3]
+  const int* shell_l;     // [n_shell]
+  const int* shell_center;
+  const int* shell_nprim;
+  const int* shell_prim0;  // first primitive of each shell
+  const int* shell_ao0;    // first AO of each shell
+  const double* alpha;     // [n_prim]
+  const double* coef;      // [n_prim]
+  const double* B;         // [n_ao][n_mo] row-major (B[mu*n_mo + m])
+  const float* B32;        // same in FP32 (mixed path)
+  const int* ref_occ;      // [2][kMaxSpin] ascending occupied MOs of each reference
+  const Exc* exc[2];       // [n_det_sp[s]] excitation records
+  // C over the distinct determinants, two orderings (Sec. 2.1, Sec. 2.4)
+  const int* csr_row;      // [nnz] row (up index) of each entry, sorted by row then column
+  const int* csr_col;      // [nnz]
+  const double* csr_val;   // [nnz]
+  const int* csc_col;      // [nnz] column (down index), sorted by column then row
+  const int* csc_row;      // [nnz]
+  const double* csc_val;   // [nnz]
+};
+
+// Per-evaluation scratch (owned by the context, grown on demand).
+struct DevScratch {
+  int64_t cap_walk = 0;   // capacity in walkers
+  int64_t wp = 0;         // padded walker stride of walker-minor arrays
+  double* phi = nullptr;  // [W][5][n_elec][n_mo]  value, d/dx, d/dy, d/dz, Laplacian
+  float* phi32 = nullptr; // same in FP32 (mixed path)
+  double* Ainv = nullptr; // [W][n_up^2 + n_dn^2]  inverses of the reference Slater matrices, A[a][i]
+  double* ld0 = nullptr;  // [W][2] log|D_ref|
+  double* sg0 = nullptr;  // [W][2] sign(D_ref)
+  double* g = nullptr;    // [W][n_elec][4]  (d_{i mu} D_ref) / D_ref
+  double* T = nullptr;    // [n_up + n_dn][n_mo][wp] walker-minor ratio tables (up block then down block)
+  float* T32 = nullptr;   // same in FP32 (mixed path)
+  double* r = nullptr;    // [n_det_up + n_det_dn][wp] ratios D_I / D_ref, walker-minor
+  double* vu = nullptr;   // [n_det_up + n_det_dn][wp]: v = C r_dn (up rows) then u = C^T r_up
+  double* psit = nullptr; // [wp] Psi / (D_ref_up D_ref_dn)
+  uint32_t* wstat = nullptr;  // [W] status bits
+  double* R_stage = nullptr;  // host-API staging buffers
+  double* out_stage = nullptr;
+};
+
+// Kernel launchers (mdet_kernels.cu). Each returns the launch error.
+cudaError_t launch_mo_f64(const DevProblem& P, const DevScratch& S, int64_t n_walk,
+                          const double* R, cudaStream_t st);
+cudaError_t launch_ref_tables_f64(const DevProblem& P, const DevScratch& S, int64_t n_walk,
+                                  cudaStream_t st);
+cudaError_t launch_ratios_f64(const DevProblem& P, const DevScratch& S, int64_t n_walk,
+                              cudaStream_t st);
+cudaError_t launch_zero_f64(const DevProblem& P, const DevScratch& S, int64_t n_walk, cudaStream_t st);
+cudaError_t launch_contract_f64(const DevProblem& P, const DevScratch& S, int64_t n_walk,
+                                cudaStream_t st);
+cudaError_t launch_final_f64(const DevProblem& P, const DevScratch& S, int64_t n_walk,
+                             const double* R, double* log_abs_psi, int8_t* sign, double* grad,
+                             double* lap, double* e_local, uint32_t* status, cudaStream_t st);
+
+}  // namespace mdet

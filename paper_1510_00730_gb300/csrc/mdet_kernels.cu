@@ -1,0 +1,612 @@
+// FP64 kernels of one evaluation (Sec. 2.2-2.4), in launch order:
+//   k_mo_f64         orbitals and their derivatives at every electron (Sec. 2)
+//   k_ref_f64        LU with partial pivoting of each reference Slater matrix,
+//                    its inverse A, log|D_ref|, the table T = A Phi and the
+//                    single-determinant derivatives g (Sec. 2.2; Sec. 5 Table method)
+//   k_ratio_f64      D_I / D_ref = eps_I det T[h_I, p_I] for every distinct
+//                    spin determinant (k x k, k <= 4)
+//   k_spmm_f64       v = C r_dn (plus Psi~ = r_up . v) and u = C^T r_up (Sec. 2.4)
+//   k_final_f64      derivative aggregation and the per-walker epilogue (Eqs. 5-8)
+//
+// Notation. For spin s with n electrons (rows i) and reference occupied MOs
+// o_1 < ... < o_n (columns a): S_ref[i][a] = phi_{o_a}(r_i), A = S_ref^-1
+// (A[a][i]), T[a][m] = sum_i A[a][i] phi_m(r_i). A determinant I that replaces
+// reference columns h_1..h_k by MOs p_1..p_k has
+//   D_I / D_ref = eps_I det M_I,    M_I[alpha][beta] = T[h_alpha][p_beta]
+// (generalised matrix-determinant lemma; eps_I reorders the columns ascending).
+// Since row i of every Slater matrix depends on r_i only, the derivative
+// d_{i mu} D_I / D_ref (mu = x, y, z, Laplacian) is the same ratio for the
+// matrices with row i replaced by d_mu phi(r_i), which gives
+//   d_{i mu} D_I / D_ref = eps_I [ g_{i mu} det M_I + sum_{alpha beta}
+//                          cof(M_I)[alpha][beta] Y_{i mu}[p_beta] A[h_alpha][i] ]
+//   g_{i mu} = sum_a A[a][i] d_mu phi_{o_a}(r_i),
+//   Y_{i mu}[m] = d_mu phi_m(r_i) - sum_b d_mu phi_{o_b}(r_i) T[b][m].
+// Summed against the contraction weights w_I (v for up, u for down) this is
+//   sum_I w_I d_{i mu} D_I / D_ref = g_{i mu} Psi~ + sum_{a,m} A[a][i] Y_{i mu}[m] W[a][m],
+//   W[a][m] = sum_I w_I eps_I cof(M_I)[alpha][beta] over (h_alpha, p_beta) = (a, m),
+// so the per-determinant derivative vectors are never stored.
+#include <cfloat>
+#include <cmath>
+
+#include "mdet_internal.h"
+
+namespace mdet {
+
+namespace {
+
+constexpr int kEC = 6;  // electrons per CTA in the orbital kernel
+
+__device__ __forceinline__ double ipow_d(double x, int n) {
+  double r = 1.0;
+  for (int i = 0; i < n; i++) r *= x;
+  return r;
+}
+
+// Determinant of a k x k matrix (k <= 4), row-major in m[4][4].
+template <class F>
+__device__ __forceinline__ F small_det(int k, const F (&m)[4][4]) {
+  if (k == 0) return F(1);
+  if (k == 1) return m[0][0];
+  if (k == 2) return m[0][0] * m[1][1] - m[0][1] * m[1][0];
+  if (k == 3)
+    return m[0][0] * (m[1][1] * m[2][2] - m[1][2] * m[2][1]) - m[0][1] * (m[1][0] * m[2][2] - m[1][2] * m[2][0]) +
+           m[0][2] * (m[1][0] * m[2][1] - m[1][1] * m[2][0]);
+  // Laplace expansion along rows 0 and 1: 2 x 2 minors of rows (0,1) and (2,3)
+  F s01 = m[0][0] * m[1][1] - m[0][1] * m[1][0];
+  F s02 = m[0][0] * m[1][2] - m[0][2] * m[1][0];
+  F s03 = m[0][0] * m[1][3] - m[0][3] * m[1][0];
+  F s12 = m[0][1] * m[1][2] - m[0][2] * m[1][1];
+  F s13 = m[0][1] * m[1][3] - m[0][3] * m[1][1];
+  F s23 = m[0][2] * m[1][3] - m[0][3] * m[1][2];
+  F c01 = m[2][0] * m[3][1] - m[2][1] * m[3][0];
+  F c02 = m[2][0] * m[3][2] - m[2][2] * m[3][0];
+  F c03 = m[2][0] * m[3][3] - m[2][3] * m[3][0];
+  F c12 = m[2][1] * m[3][2] - m[2][2] * m[3][1];
+  F c13 = m[2][1] * m[3][3] - m[2][3] * m[3][1];
+  F c23 = m[2][2] * m[3][3] - m[2][3] * m[3][2];
+  return s01 * c23 - s02 * c13 + s03 * c12 + s12 * c03 - s13 * c02 + s23 * c01;
+}
+
+// Cofactors cof[alpha][beta] = (-1)^(alpha+beta) det(minor without row alpha, column beta), k <= 4.
+template <class F>
+__device__ __forceinline__ void small_cof(int k, const F (&m)[4][4], F (&cof)[4][4]) {
+  if (k == 1) {
+    cof[0][0] = F(1);
+    return;
+  }
+  if (k == 2) {
+    cof[0][0] = m[1][1];
+    cof[0][1] = -m[1][0];
+    cof[1][0] = -m[0][1];
+    cof[1][1] = m[0][0];
+    return;
+  }
+  if (k == 3) {
+#pragma unroll
+    for (int a = 0; a < 3; a++)
+#pragma unroll
+      for (int b = 0; b < 3; b++) {
+        const int r0 = a == 0 ? 1 : 0, r1 = a == 2 ? 1 : 2;
+        const int c0 = b == 0 ? 1 : 0, c1 = b == 2 ? 1 : 2;
+        F d = m[r0][c0] * m[r1][c1] - m[r0][c1] * m[r1][c0];
+        cof[a][b] = ((a + b) & 1) ? -d : d;
+      }
+    return;
+  }
+  // k == 4: each 3 x 3 minor is expanded along the row that shares its pair
+  // ({0,1} or {2,3}) with the removed row, using precomputed 2 x 2 minors of the other pair.
+  F top[4][4], bot[4][4];  // 2 x 2 minors of rows (0,1) and (2,3) for column pairs (x < y)
+#pragma unroll
+  for (int x = 0; x < 4; x++)
+#pragma unroll
+    for (int y = x + 1; y < 4; y++) {
+      top[x][y] = m[0][x] * m[1][y] - m[0][y] * m[1][x];
+      bot[x][y] = m[2][x] * m[3][y] - m[2][y] * m[3][x];
+    }
+#pragma unroll
+  for (int a = 0; a < 4; a++) {
+    const int rho = a < 2 ? 1 - a : 5 - a;  // the remaining row of the removed row's pair
+#pragma unroll
+    for (int b = 0; b < 4; b++) {
+      int cols[3];
+      int q = 0;
+#pragma unroll
+      for (int x = 0; x < 4; x++)
+        if (x != b) cols[q++] = x;
+      // det of the 3 x 3 minor = sum_t (-1)^t m[rho][cols[t]] * D2(other two columns)
+      F d = F(0);
+#pragma unroll
+      for (int t = 0; t < 3; t++) {
+        const int x = t == 0 ? cols[1] : cols[0];
+        const int y = t == 2 ? cols[1] : cols[2];
+        const F d2 = a < 2 ? bot[x][y] : top[x][y];
+        const F term = m[rho][cols[t]] * d2;
+        d = (t & 1) ? d - term : d + term;
+      }
+      cof[a][b] = ((a + b) & 1) ? -d : d;
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// K1: orbitals. grid (n_walk, ceil(n_elec / kEC)); smem X[5][kEC][n_ao].
+// AO chi = P(x, y, z) f(r^2), P = x^a y^b z^c (degree l), f(s) = sum_p c_p e^{-alpha_p s}:
+//   d_x chi = P_x f + 2 x P f',   Lap chi = (Lap P) f + P ((4 l + 6) f' + 4 s f'')
+// (Euler: x P_x + y P_y + z P_z = l P). Then Phi[c][e][m] = sum_mu X[c][e][mu] B[mu][m].
+__global__ void __launch_bounds__(128) k_mo_f64(DevProblem P, double* __restrict__ phi,
+                                                const double* __restrict__ R) {
+  extern __shared__ double smem[];
+  const int K = P.n_ao, M = P.n_mo, N = P.n_elec;
+  const int64_t w = blockIdx.x;
+  const int e_begin = blockIdx.y * kEC;
+  const int ne = min(kEC, N - e_begin);
+  double* X = smem;  // X[(c * kEC + e) * K + mu]
+  for (int t = threadIdx.x; t < kEC * P.n_shell; t += blockDim.x) {
+    const int e = t / P.n_shell, s = t - e * P.n_shell;
+    const int l = P.shell_l[s], ao0 = P.shell_ao0[s], nc = (l + 1) * (l + 2) / 2;
+    if (e >= ne) {
+      for (int c = 0; c < 5; c++)
+        for (int q = 0; q < nc; q++) X[(c * kEC + e) * K + ao0 + q] = 0.0;
+      continue;
+    }
+    const double* r = R + (w * N + e_begin + e) * 3;
+    const double* C = P.nuc_xyz + 3 * P.shell_center[s];
+    const double x = r[0] - C[0], y = r[1] - C[1], z = r[2] - C[2];
+    const double s2 = x * x + y * y + z * z;
+    double f0 = 0, f1 = 0, f2 = 0;
+    const int p0 = P.shell_prim0[s], np = P.shell_nprim[s];
+    for (int p = 0; p < np; p++) {
+      const double al = P.alpha[p0 + p], cf = P.coef[p0 + p];
+      const double ex = cf * exp(-al * s2);
+      f0 += ex;
+      f1 -= al * ex;
+      f2 += al * al * ex;
+    }
+    const double lapf = (4.0 * l + 6.0) * f1 + 4.0 * s2 * f2;
+    int q = 0;
+    for (int a = l; a >= 0; a--)
+      for (int b = l - a; b >= 0; b--, q++) {
+        const int cc = l - a - b;
+        const double xa = ipow_d(x, a), yb = ipow_d(y, b), zc = ipow_d(z, cc);
+        const double P0 = xa * yb * zc;
+        const double Px = a ? a * ipow_d(x, a - 1) * yb * zc : 0.0;
+        const double Py = b ? b * xa * ipow_d(y, b - 1) * zc : 0.0;
+        const double Pz = cc ? cc * xa * yb * ipow_d(z, cc - 1) : 0.0;
+        double lapP = 0.0;
+        if (a >= 2) lapP += a * (a - 1) * ipow_d(x, a - 2) * yb * zc;
+        if (b >= 2) lapP += b * (b - 1) * xa * ipow_d(y, b - 2) * zc;
+        if (cc >= 2) lapP += cc * (cc - 1) * xa * yb * ipow_d(z, cc - 2);
+        const int mu = ao0 + q;
+        X[(0 * kEC + e) * K + mu] = P0 * f0;
+        X[(1 * kEC + e) * K + mu] = Px * f0 + 2.0 * x * P0 * f1;
+        X[(2 * kEC + e) * K + mu] = Py * f0 + 2.0 * y * P0 * f1;
+        X[(3 * kEC + e) * K + mu] = Pz * f0 + 2.0 * z * P0 * f1;
+        X[(4 * kEC + e) * K + mu] = lapP * f0 + P0 * lapf;
+      }
+  }
+  __syncthreads();
+  for (int m = threadIdx.x; m < M; m += blockDim.x) {
+    double acc[5 * kEC];
+#pragma unroll
+    for (int q = 0; q < 5 * kEC; q++) acc[q] = 0.0;
+    for (int mu = 0; mu < K; mu++) {
+      const double b = __ldg(P.B + (size_t)mu * M + m);
+#pragma unroll
+      for (int q = 0; q < 5 * kEC; q++) acc[q] = fma(X[q * K + mu], b, acc[q]);
+    }
+#pragma unroll
+    for (int c = 0; c < 5; c++)
+#pragma unroll
+      for (int e = 0; e < kEC; e++)
+        if (e < ne) phi[((w * 5 + c) * N + e_begin + e) * M + m] = acc[c * kEC + e];
+  }
+}
+
+// ---------------------------------------------------------------------------
+// K2+K3: reference inverse and tables. grid n_walk, block 64: warp s factorises
+// spin s by Gauss-Jordan elimination with partial pivoting on [S | I] (rows
+// stay in their lanes; the pivot order is a permutation whose parity enters
+// the sign of the determinant). Then every thread computes T and g.
+// smem: aug[2][kMaxSpin][2*kMaxSpin] + A[2][kMaxSpin][kMaxSpin]
+__global__ void __launch_bounds__(64) k_ref_f64(DevProblem P, DevScratch S) {
+  __shared__ double aug[2][kMaxSpin][2 * kMaxSpin];
+  __shared__ int rowof[2][kMaxSpin];  // lane whose right half holds row a of A
+  __shared__ int bad[2];
+  __shared__ uint32_t stf[2];
+  const int64_t w = blockIdx.x;
+  const int N = P.n_elec, M = P.n_mo;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  {
+    const int sp = warp;
+    const int n = sp ? P.n_dn : P.n_up, e0 = sp ? P.n_up : 0;
+    const int* occ = P.ref_occ + sp * kMaxSpin;
+    if (lane < n) {
+      for (int a = 0; a < n; a++) {
+        aug[sp][lane][a] = S.phi[((w * 5 + 0) * N + e0 + lane) * M + occ[a]];
+        aug[sp][lane][n + a] = (a == lane) ? 1.0 : 0.0;
+      }
+    }
+    __syncwarp();
+    bool used = false;
+    int step = -1;
+    double logd = 0.0, sgn = 1.0, pmax = 0.0, pmin = DBL_MAX;
+    int singular = 0;
+    for (int j = 0; j < n; j++) {
+      double v = (lane < n && !used) ? fabs(aug[sp][lane][j]) : -1.0;
+      int idx = lane;
+#pragma unroll
+      for (int off = 16; off; off >>= 1) {
+        const double ov = __shfl_xor_sync(0xffffffffu, v, off);
+        const int oi = __shfl_xor_sync(0xffffffffu, idx, off);
+        if (ov > v || (ov == v && oi < idx)) {
+          v = ov;
+          idx = oi;
+        }
+      }
+      if (!(v > 0.0)) {  // zero pivot (or NaN input): singular reference
+        singular = 1;
+        break;
+      }
+      const int p = idx;
+      const double piv = aug[sp][p][j];
+      logd += log(fabs(piv));
+      if (piv < 0) sgn = -sgn;
+      pmax = fmax(pmax, fabs(piv));
+      pmin = fmin(pmin, fabs(piv));
+      __syncwarp();
+      if (lane == p) {
+        used = true;
+        step = j;
+        const double inv = 1.0 / piv;
+        for (int c = 0; c < 2 * n; c++) aug[sp][p][c] *= inv;
+      }
+      __syncwarp();
+      if (lane < n && lane != p) {
+        const double f = aug[sp][lane][j];
+        if (f != 0.0)
+          for (int c = 0; c < 2 * n; c++) aug[sp][lane][c] = fma(-f, aug[sp][p][c], aug[sp][lane][c]);
+      }
+      __syncwarp();
+    }
+    // parity of the pivot order: lane i was the pivot of step step(i)
+    int inv_cnt = 0;
+    for (int q = 0; q < 32; q++) {
+      const int sq = __shfl_sync(0xffffffffu, step, q);
+      if (lane < n && q > lane && q < n && sq < step) inv_cnt++;
+    }
+#pragma unroll
+    for (int off = 16; off; off >>= 1) inv_cnt += __shfl_xor_sync(0xffffffffu, inv_cnt, off);
+    if (inv_cnt & 1) sgn = -sgn;
+    if (lane < n && !singular) rowof[sp][step] = lane;
+    if (lane == 0) {
+      bad[sp] = singular;
+      S.ld0[w * 2 + sp] = singular ? -INFINITY : logd;
+      S.sg0[w * 2 + sp] = singular ? 0.0 : sgn;
+      uint32_t st = singular ? MDET_WS_REF_SINGULAR : 0u;
+      if (!singular && pmin < 1e-13 * pmax) st |= MDET_WS_REF_ILLCOND;
+      stf[sp] = st;
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) S.wstat[w] = stf[0] | stf[1];
+  // A to global, T = A Phi (walker-minor), g
+  const int nu = P.n_up, nd = P.n_dn;
+  // A[a][i] of spin sp
+  auto Aat = [&](int sp, int a, int i) { return aug[sp][rowof[sp][a]][(sp ? nd : nu) + i]; };
+  double* Ag = S.Ainv + w * (nu * nu + nd * nd);
+  for (int t = threadIdx.x; t < nu * nu + nd * nd; t += blockDim.x) {
+    const int sp = t < nu * nu ? 0 : 1;
+    const int n = sp ? nd : nu;
+    const int tt = sp ? t - nu * nu : t;
+    Ag[t] = bad[sp] ? NAN : Aat(sp, tt / n, tt % n);
+  }
+  for (int t = threadIdx.x; t < N * M; t += blockDim.x) {
+    const int row = t / M, m = t - row * M;  // row indexes the table rows of both spins
+    const int sp = row < nu ? 0 : 1;
+    const int n = sp ? nd : nu, e0 = sp ? nu : 0, a = row - e0;
+    double acc = 0.0;
+    if (!bad[sp])
+      for (int i = 0; i < n; i++) acc = fma(Aat(sp, a, i), S.phi[((w * 5 + 0) * N + e0 + i) * M + m], acc);
+    S.T[(size_t)t * S.wp + w] = bad[sp] ? NAN : acc;
+  }
+  for (int t = threadIdx.x; t < N * 4; t += blockDim.x) {
+    const int e = t >> 2, mu = t & 3;
+    const int sp = e < nu ? 0 : 1;
+    const int n = sp ? nd : nu, e0 = sp ? nu : 0, i = e - e0;
+    const int* occ = P.ref_occ + sp * kMaxSpin;
+    double acc = 0.0;
+    if (!bad[sp])
+      for (int a = 0; a < n; a++) acc = fma(Aat(sp, a, i), S.phi[((w * 5 + 1 + mu) * N + e) * M + occ[a]], acc);
+    S.g[(w * N + e) * 4 + mu] = bad[sp] ? NAN : acc;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// K4: ratios r_I = eps_I det M_I. grid (ceil(n_det_total / 32), wpad / 32),
+// block 128 = 4 warps; lanes are walkers, each warp takes 8 determinants.
+__global__ void __launch_bounds__(128) k_ratio_f64(DevProblem P, DevScratch S) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int64_t w = (int64_t)blockIdx.y * 32 + lane;
+  const int nu_det = P.n_det_sp[0], ntot = nu_det + P.n_det_sp[1];
+  const int M = P.n_mo;
+  const int64_t wp = S.wp;
+  for (int q = 0; q < 8; q++) {
+    const int t = blockIdx.x * 32 + warp * 8 + q;
+    if (t >= ntot) return;
+    const int sp = t < nu_det ? 0 : 1;
+    const Exc e = P.exc[sp][sp ? t - nu_det : t];
+    const double* T = S.T + (size_t)(sp ? P.n_up * M : 0) * wp;
+    double m[4][4];
+#pragma unroll
+    for (int a = 0; a < 4; a++)
+#pragma unroll
+      for (int b = 0; b < 4; b++)
+        m[a][b] = (a < e.k && b < e.k) ? T[((size_t)e.h[a] * M + e.p[b]) * wp + w] : 0.0;
+    const double d = small_det(e.k, m);
+    S.r[(size_t)t * wp + w] = e.eps < 0 ? -d : d;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// K5: y[seg][w] += sum_k val_k x[gidx_k][w] over one ordering of C. Each warp
+// owns `chunk` consecutive nonzeros and 4 walkers per lane (128 per warp);
+// partial sums are flushed with atomics whenever the segment changes. If rdot
+// is given, psit[w] += rdot[seg][w] * (partial sum) as well (Psi~ = r_up . v).
+__global__ void __launch_bounds__(256) k_spmm_f64(const int* __restrict__ seg, const int* __restrict__ gidx,
+                                                  const double* __restrict__ val, int64_t nnz, int chunk,
+                                                  const double* __restrict__ x, double* __restrict__ y,
+                                                  int64_t wp, const double* __restrict__ rdot,
+                                                  double* __restrict__ psit) {
+  const int lane = threadIdx.x & 31;
+  const int64_t gw = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  const int64_t k0 = gw * chunk;
+  if (k0 >= nnz) return;
+  const int64_t k1 = min(k0 + (int64_t)chunk, nnz);
+  const int64_t wb = (int64_t)blockIdx.y * 128 + lane * 4;
+  double a0 = 0, a1 = 0, a2 = 0, a3 = 0;
+  int cur = __ldg(seg + k0);
+  auto flush = [&](int s) {
+    double* yp = y + (size_t)s * wp + wb;
+    atomicAdd(yp + 0, a0);
+    atomicAdd(yp + 1, a1);
+    atomicAdd(yp + 2, a2);
+    atomicAdd(yp + 3, a3);
+    if (rdot) {
+      const double* rp = rdot + (size_t)s * wp + wb;
+      atomicAdd(psit + wb + 0, rp[0] * a0);
+      atomicAdd(psit + wb + 1, rp[1] * a1);
+      atomicAdd(psit + wb + 2, rp[2] * a2);
+      atomicAdd(psit + wb + 3, rp[3] * a3);
+    }
+  };
+  for (int64_t k = k0; k < k1; k++) {
+    const int s = __ldg(seg + k);
+    if (s != cur) {
+      flush(cur);
+      cur = s;
+      a0 = a1 = a2 = a3 = 0;
+    }
+    const double c = __ldg(val + k);
+    const double2* xp = reinterpret_cast<const double2*>(x + (size_t)__ldg(gidx + k) * wp + wb);
+    const double2 u = __ldg(xp), v = __ldg(xp + 1);
+    a0 = fma(c, u.x, a0);
+    a1 = fma(c, u.y, a1);
+    a2 = fma(c, v.x, a2);
+    a3 = fma(c, v.y, a3);
+  }
+  flush(cur);
+}
+
+// ---------------------------------------------------------------------------
+// K6: per walker: W scatter over every determinant, Q = A^T W, Pm = T Q^T,
+// G_{i mu} = g Psi~ + sum_m d_mu phi[i][m] Q[i][m] - sum_b d_mu phi[i][o_b] Pm[b][i],
+// then grad, Laplacian, log|Psi|, sign and E_L. grid n_walk, block 128.
+// smem: T[N][M], W[N][M], Q[N][M] (rows of both spins stacked), A blocks, Pm.
+__global__ void __launch_bounds__(128) k_final_f64(DevProblem P, DevScratch S, const double* __restrict__ R,
+                                                   double* __restrict__ log_abs_psi, int8_t* __restrict__ sign,
+                                                   double* __restrict__ grad, double* __restrict__ lap,
+                                                   double* __restrict__ e_local, uint32_t* __restrict__ status) {
+  extern __shared__ double sm[];
+  const int nu = P.n_up, nd = P.n_dn, N = nu + nd, M = P.n_mo;
+  const int64_t w = blockIdx.x, wp = S.wp;
+  double* Ts = sm;                 // [N][M]
+  double* Ws = Ts + N * M;         // [N][M]
+  double* Qs = Ws + N * M;         // [N][M]
+  double* As = Qs + N * M;         // [nu*nu + nd*nd]
+  double* Pm = As + nu * nu + nd * nd;  // [nu*nu + nd*nd]  Pm[b][i] per spin
+  __shared__ double red[4];
+  __shared__ double Gs[kMaxSpin * 2][4];
+  for (int t = threadIdx.x; t < N * M; t += blockDim.x) {
+    Ts[t] = S.T[(size_t)t * wp + w];
+    Ws[t] = 0.0;
+  }
+  for (int t = threadIdx.x; t < nu * nu + nd * nd; t += blockDim.x) As[t] = S.Ainv[w * (nu * nu + nd * nd) + t];
+  __syncthreads();
+  const int nu_det = P.n_det_sp[0], ntot = nu_det + P.n_det_sp[1];
+  for (int t = threadIdx.x; t < ntot; t += blockDim.x) {
+    const int sp = t < nu_det ? 0 : 1;
+    const Exc e = P.exc[sp][sp ? t - nu_det : t];
+    if (e.k == 0) continue;
+    const double wgt = (e.eps < 0 ? -1.0 : 1.0) * S.vu[(size_t)t * wp + w];
+    if (wgt == 0.0) continue;
+    const double* Tb = Ts + (sp ? nu * M : 0);
+    double* Wb = Ws + (sp ? nu * M : 0);
+    double m[4][4], cof[4][4];
+#pragma unroll
+    for (int a = 0; a < 4; a++)
+#pragma unroll
+      for (int b = 0; b < 4; b++) m[a][b] = (a < e.k && b < e.k) ? Tb[e.h[a] * M + e.p[b]] : 0.0;
+    small_cof(e.k, m, cof);
+#pragma unroll
+    for (int a = 0; a < 4; a++)
+#pragma unroll
+      for (int b = 0; b < 4; b++)
+        if (a < e.k && b < e.k) atomicAdd(Wb + e.h[a] * M + e.p[b], wgt * cof[a][b]);
+  }
+  __syncthreads();
+  // Q[i][m] = sum_a A[a][i] W[a][m] (per spin block)
+  for (int t = threadIdx.x; t < N * M; t += blockDim.x) {
+    const int row = t / M, m = t - row * M;
+    const int sp = row < nu ? 0 : 1;
+    const int n = sp ? nd : nu, e0 = sp ? nu : 0, i = row - e0;
+    const double* A = As + (sp ? nu * nu : 0);
+    const double* Wb = Ws + e0 * M;
+    double acc = 0.0;
+    for (int a = 0; a < n; a++) acc = fma(A[a * n + i], Wb[a * M + m], acc);
+    Qs[t] = acc;
+  }
+  __syncthreads();
+  // Pm[b][i] = sum_m T[b][m] Q[i][m]
+  for (int t = threadIdx.x; t < nu * nu + nd * nd; t += blockDim.x) {
+    const int sp = t < nu * nu ? 0 : 1;
+    const int n = sp ? nd : nu, e0 = sp ? nu : 0;
+    const int tt = sp ? t - nu * nu : t;
+    const int b = tt / n, i = tt - b * n;
+    const double* Tr = Ts + (e0 + b) * M;
+    const double* Qr = Qs + (e0 + i) * M;
+    double acc = 0.0;
+    for (int m = 0; m < M; m++) acc = fma(Tr[m], Qr[m], acc);
+    Pm[t] = acc;
+  }
+  __syncthreads();
+  const double psit = S.psit[w];
+  const double ld = S.ld0[w * 2] + S.ld0[w * 2 + 1];
+  const double sg = S.sg0[w * 2] * S.sg0[w * 2 + 1];
+  for (int t = threadIdx.x; t < N * 4; t += blockDim.x) {
+    const int e = t >> 2, mu = t & 3;
+    const int sp = e < nu ? 0 : 1;
+    const int n = sp ? nd : nu, e0 = sp ? nu : 0, i = e - e0;
+    const int* occ = P.ref_occ + sp * kMaxSpin;
+    const double* dphi = S.phi + ((w * 5 + 1 + mu) * N + e) * M;
+    const double* Qr = Qs + e * M;
+    double acc = S.g[(w * N + e) * 4 + mu] * psit;
+    for (int m = 0; m < M; m++) acc = fma(dphi[m], Qr[m], acc);
+    const double* Pb = Pm + (sp ? nu * nu : 0);
+    for (int b = 0; b < n; b++) acc = fma(-dphi[occ[b]], Pb[b * n + i], acc);
+    Gs[e][mu] = acc;
+  }
+  __syncthreads();
+  // potential energy: electron-nucleus, electron-electron, nucleus-nucleus
+  double v = 0.0;
+  const double* r = R + w * N * 3;
+  for (int t = threadIdx.x; t < N * P.n_nuc; t += blockDim.x) {
+    const int i = t / P.n_nuc, A = t - i * P.n_nuc;
+    const double dx = r[3 * i] - P.nuc_xyz[3 * A], dy = r[3 * i + 1] - P.nuc_xyz[3 * A + 1],
+                 dz = r[3 * i + 2] - P.nuc_xyz[3 * A + 2];
+    v -= P.Z[A] / sqrt(dx * dx + dy * dy + dz * dz);
+  }
+  for (int t = threadIdx.x; t < N * N; t += blockDim.x) {
+    const int i = t / N, j = t - i * N;
+    if (j <= i) continue;
+    const double dx = r[3 * i] - r[3 * j], dy = r[3 * i + 1] - r[3 * j + 1], dz = r[3 * i + 2] - r[3 * j + 2];
+    v += 1.0 / sqrt(dx * dx + dy * dy + dz * dz);
+  }
+  if (threadIdx.x == 0)
+    for (int A = 0; A < P.n_nuc; A++)
+      for (int B = A + 1; B < P.n_nuc; B++) {
+        const double dx = P.nuc_xyz[3 * A] - P.nuc_xyz[3 * B], dy = P.nuc_xyz[3 * A + 1] - P.nuc_xyz[3 * B + 1],
+                     dz = P.nuc_xyz[3 * A + 2] - P.nuc_xyz[3 * B + 2];
+        v += P.Z[A] * P.Z[B] / sqrt(dx * dx + dy * dy + dz * dz);
+      }
+#pragma unroll
+  for (int off = 16; off; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+  __syncthreads();
+  const double inv = 1.0 / psit;
+  bool finite = true;
+  for (int t = threadIdx.x; t < N; t += blockDim.x) {
+    const double gx = Gs[t][0] * inv, gy = Gs[t][1] * inv, gz = Gs[t][2] * inv, lp = Gs[t][3] * inv;
+    grad[(w * N + t) * 3 + 0] = gx;
+    grad[(w * N + t) * 3 + 1] = gy;
+    grad[(w * N + t) * 3 + 2] = gz;
+    lap[w * N + t] = lp;
+    finite &= isfinite(gx) && isfinite(gy) && isfinite(gz) && isfinite(lp);
+  }
+  const int all_finite = __syncthreads_and(finite);
+  if (threadIdx.x == 0) {
+    double tl = 0.0;
+    for (int i = 0; i < N; i++) tl += Gs[i][3];
+    const double vpot = red[0] + red[1] + red[2] + red[3];
+    const double el = -0.5 * tl * inv + vpot;
+    const double lg = ld + log(fabs(psit));
+    const int s = (psit > 0.0) - (psit < 0.0);
+    log_abs_psi[w] = lg;
+    sign[w] = (int8_t)(sg > 0 ? s : (sg < 0 ? -s : 0));
+    if (e_local) e_local[w] = el;
+    uint32_t st = S.wstat[w];
+    if (psit == 0.0) st |= MDET_WS_PSI_ZERO;
+    if (!all_finite || !isfinite(el) || !isfinite(lg)) st |= MDET_WS_NONFINITE;
+    S.wstat[w] = st;
+    if (status) status[w] = st;
+  }
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+cudaError_t launch_mo_f64(const DevProblem& P, const DevScratch& S, int64_t n_walk, const double* R,
+                          cudaStream_t st) {
+  const size_t smem = sizeof(double) * 5 * kEC * P.n_ao;
+  if (smem > 48 * 1024) {
+    cudaError_t e = cudaFuncSetAttribute(k_mo_f64, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+  }
+  dim3 grid((unsigned)n_walk, (P.n_elec + kEC - 1) / kEC);
+  k_mo_f64<<<grid, 128, smem, st>>>(P, S.phi, R);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_ref_tables_f64(const DevProblem& P, const DevScratch& S, int64_t n_walk, cudaStream_t st) {
+  k_ref_f64<<<(unsigned)n_walk, 64, 0, st>>>(P, S);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_ratios_f64(const DevProblem& P, const DevScratch& S, int64_t n_walk, cudaStream_t st) {
+  const int ntot = P.n_det_sp[0] + P.n_det_sp[1];
+  const int64_t wpad = (n_walk + 31) / 32 * 32;
+  dim3 grid((ntot + 31) / 32, (unsigned)(wpad / 32));
+  k_ratio_f64<<<grid, 128, 0, st>>>(P, S);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_zero_f64(const DevProblem& P, const DevScratch& S, int64_t n_walk, cudaStream_t st) {
+  (void)n_walk;
+  const int64_t ndt = (int64_t)P.n_det_sp[0] + P.n_det_sp[1];
+  cudaError_t e = cudaMemsetAsync(S.vu, 0, sizeof(double) * ndt * S.wp, st);
+  if (e != cudaSuccess) return e;
+  return cudaMemsetAsync(S.psit, 0, sizeof(double) * S.wp, st);
+}
+
+cudaError_t launch_contract_f64(const DevProblem& P, const DevScratch& S, int64_t n_walk, cudaStream_t st) {
+  cudaError_t e;
+  const int chunk = 512;
+  const int64_t nchunks = (P.nnz + chunk - 1) / chunk;
+  const int64_t wgroups = (n_walk + 127) / 128;
+  dim3 grid((unsigned)((nchunks + 7) / 8), (unsigned)wgroups);
+  const double* r_up = S.r;
+  const double* r_dn = S.r + (size_t)P.n_det_sp[0] * S.wp;
+  double* v = S.vu;
+  double* u = S.vu + (size_t)P.n_det_sp[0] * S.wp;
+  // v = C r_dn (rows = up determinants) and Psi~ = r_up . v
+  k_spmm_f64<<<grid, 256, 0, st>>>(P.csr_row, P.csr_col, P.csr_val, P.nnz, chunk, r_dn, v, S.wp, r_up, S.psit);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  // u = C^T r_up (columns = down determinants), in the paper's column-major order
+  k_spmm_f64<<<grid, 256, 0, st>>>(P.csc_col, P.csc_row, P.csc_val, P.nnz, chunk, r_up, u, S.wp, nullptr, nullptr);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_final_f64(const DevProblem& P, const DevScratch& S, int64_t n_walk, const double* R,
+                             double* log_abs_psi, int8_t* sign, double* grad, double* lap, double* e_local,
+                             uint32_t* status, cudaStream_t st) {
+  const int N = P.n_elec, M = P.n_mo;
+  const size_t smem = sizeof(double) * (3 * (size_t)N * M + 2 * (P.n_up * P.n_up + P.n_dn * P.n_dn));
+  if (smem > 48 * 1024) {
+    cudaError_t e = cudaFuncSetAttribute(k_final_f64, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+  }
+  k_final_f64<<<(unsigned)n_walk, 128, smem, st>>>(P, S, R, log_abs_psi, sign, grad, lap, e_local, status);
+  return cudaGetLastError();
+}
+
+}  // namespace mdet

@@ -1,0 +1,189 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle on the same
+seeded inputs. FP64 path: 1e-10 relative on Psi, 1e-8 on grad Psi / Psi and
+Lap Psi / Psi (scaled by the conditioning kappa of the determinant sum)."""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+import paper_1510_00730_gb300 as pkg
+from paper_1510_00730_gb300 import synth
+from tests.parity import compare
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+def _gpu_eval(ctx, R):
+    Rt = torch.from_numpy(np.ascontiguousarray(R)).to("cuda:0")
+    out = ctx.evaluate(Rt)
+    torch.cuda.synchronize()
+    return {k: v.cpu().numpy() for k, v in out.items()}
+
+
+@pytest.fixture(scope="module")
+def o1k():
+    wl = synth.oxygen_like_1k(n_walk=64)
+    return wl, oracle.evaluate(wl)
+
+
+def test_fp64_oxygen_like_1k_all_walkers(o1k):
+    wl, ref = o1k
+    ctx = pkg.Context.from_workload(wl, device=0, precision=pkg.PRECISION_FP64)
+    got = _gpu_eval(ctx, wl.R)
+    rep = compare(got, ref)
+    assert rep["ok"], rep
+    assert np.all(got["status"] & (pkg.WS_REF_SINGULAR | pkg.WS_NONFINITE) == 0)
+
+
+def test_fp64_per_determinant_ratios(o1k):
+    """Every distinct spin determinant: D_I / D_ref from the table method equals
+    the oracle's ratio of full LU determinants. The k x k determinant of table
+    entries cancels terms as large as the permanent of |T[h, p]|, and T itself
+    carries the conditioning of the reference Slater matrix, so the absolute
+    bound is 1e-14 (about 90 ulps) * cond(S_ref) * max(per|T[h,p]|, |r|, 1)."""
+    from itertools import permutations
+    wl, _ = o1k
+    ctx = pkg.Context.from_workload(wl, device=0, precision=pkg.PRECISION_FP64)
+    _gpu_eval(ctx, wl.R)
+    r_up, r_dn, ld0, sg0 = ctx.ratios(wl.n_walk)
+    for spin, r in ((0, r_up), (1, r_dn)):
+        dets, _, _ = ctx.spin_dets(spin)
+        lg, sg, _ = oracle.spin_dets(wl, spin, dets)
+        want = sg * sg[:, :1] * np.exp(lg - lg[:, :1])
+        n, e0 = (wl.n_up, 0) if spin == 0 else (wl.n_dn, wl.n_up)
+        ref_occ = [b for b in range(64) if (int(dets[0, 0]) >> b) & 1]
+        occs = [[b for b in range(64) if (int(d[0]) >> b) & 1] for d in dets]
+        holes = [[a for a, m in enumerate(ref_occ) if m not in o] for o in occs]
+        parts = [sorted(set(o) - set(ref_occ)) for o in occs]
+        for w in range(wl.n_walk):
+            phi = oracle.mo_eval(wl, wl.R[w])[e0:e0 + n, 0, :]
+            cond = np.linalg.cond(phi[:, ref_occ])
+            T = np.abs(np.linalg.solve(phi[:, ref_occ], phi))
+            for t in range(len(dets)):
+                M = T[np.ix_(holes[t], parts[t])]
+                k = M.shape[0]
+                per = sum(np.prod([M[i, q[i]] for i in range(k)]) for q in permutations(range(k))) if k else 1.0
+                bound = 1e-14 * max(cond, 1.0) * max(per, abs(want[w, t]), 1.0)
+                assert abs(r[w, t] - want[w, t]) <= bound, (spin, w, t, r[w, t], want[w, t], bound)
+        assert np.all(np.abs(ld0[:, spin] - lg[:, 0]) < 1e-11)
+        assert np.all(sg0[:, spin] == sg[:, 0])
+
+
+@pytest.mark.parametrize("n_walk", [1, 31, 77, 130, 257])
+def test_fp64_ragged_walker_counts(n_walk):
+    """Walker counts that are not multiples of the 32/128-walker tiles."""
+    wl = synth.oxygen_like_1k(n_walk=n_walk, seed=4242 + n_walk)
+    ref = oracle.evaluate(wl)
+    ctx = pkg.Context.from_workload(wl, device=0)
+    rep = compare(_gpu_eval(ctx, wl.R), ref)
+    assert rep["ok"], rep
+
+
+def test_fp64_grow_and_shrink_batch(o1k):
+    """One context, batches of varying size (scratch grows once, stale columns ignored)."""
+    wl, ref = o1k
+    ctx = pkg.Context.from_workload(wl, device=0)
+    for n in (8, 64, 5, 40):
+        rep = compare(_gpu_eval(ctx, wl.R[:n]), {k: v[:n] for k, v in ref.items()})
+        assert rep["ok"], (n, rep)
+
+
+def test_empty_batch_is_noop(o1k):
+    wl, _ = o1k
+    ctx = pkg.Context.from_workload(wl, device=0)
+    out = ctx.evaluate(torch.empty(0, wl.n_elec, 3, dtype=torch.float64, device="cuda:0"))
+    torch.cuda.synchronize()
+    assert out["log_abs_psi"].numel() == 0
+
+
+def test_single_determinant():
+    """N_det = 1: the plain Slater determinant product (Table 2, first row)."""
+    wl = synth.oxygen_like_1k(n_walk=32)
+    k = 11
+    wl.det_up, wl.det_dn, wl.ci_coef = wl.det_up[k:k + 1], wl.det_dn[k:k + 1], np.array([0.5])
+    ref = oracle.evaluate(wl)
+    ctx = pkg.Context.from_workload(wl, device=0)
+    rep = compare(_gpu_eval(ctx, wl.R), ref)
+    assert rep["ok"], rep
+
+
+def test_fci_expansion_all_degrees():
+    """Full CI of 4 up / 4 down electrons in 10 MOs (210 x 210 = 44,100 products,
+    excitation degrees 0..4 in both spins)."""
+    from itertools import combinations
+    wl = synth.oxygen_like_1k(n_walk=40)
+    wl.mo_coef = wl.mo_coef[:, :10].copy()
+    subsets = list(combinations(range(10), 4))
+    bits = np.array([[sum(1 << m for m in s)] for s in subsets], np.uint64)
+    rng = np.random.default_rng(9)
+    cu = rng.normal(size=len(subsets))
+    I, J = np.meshgrid(np.arange(210), np.arange(210), indexing="ij")
+    wl.det_up, wl.det_dn = bits[I.ravel()], bits[J.ravel()]
+    wl.ci_coef = cu[I.ravel()] * cu[J.ravel()] + 0.1 * rng.normal(size=I.size)
+    ref = oracle.evaluate(wl)
+    ctx = pkg.Context.from_workload(wl, device=0)
+    assert ctx.stats()["max_degree"] == [4, 4]
+    rep = compare(_gpu_eval(ctx, wl.R), ref)
+    assert rep["ok"], rep
+
+
+def test_host_api_matches_device_api(o1k):
+    wl, _ = o1k
+    ctx = pkg.Context.from_workload(wl, device=0)
+    dev = _gpu_eval(ctx, wl.R)
+    host = ctx.evaluate_host(wl.R)
+    # the contraction accumulates with atomics, so two runs agree to rounding, not bitwise
+    for k in ("log_abs_psi", "grad", "lap", "e_local"):
+        np.testing.assert_allclose(host[k], dev[k], rtol=1e-9, atol=1e-9)
+    assert np.array_equal(host["sign"], dev["sign"])
+
+
+def test_coincident_same_spin_electrons_flagged():
+    """Two up electrons at the same point: every up Slater matrix is singular
+    (Psi = 0 on this node). Rounding may leave a tiny nonzero pivot, so the
+    walker is flagged singular or ill-conditioned; its neighbours are unaffected."""
+    wl = synth.oxygen_like_1k(n_walk=8)
+    R = wl.R.copy()
+    R[3, 1] = R[3, 0]
+    ref = oracle.evaluate(wl, R=R)
+    assert ref["sign"][3] == 0
+    ctx = pkg.Context.from_workload(wl, device=0)
+    got = _gpu_eval(ctx, R)
+    assert got["status"][3] & (pkg.WS_REF_SINGULAR | pkg.WS_REF_ILLCOND)
+    assert not np.any(got["status"][[0, 1, 2, 4, 5, 6, 7]] & (pkg.WS_REF_SINGULAR | pkg.WS_REF_ILLCOND))
+    keep = [i for i in range(8) if i != 3]
+    rep = compare({k: v[keep] for k, v in got.items()}, {k: v[keep] for k, v in ref.items()})
+    assert rep["ok"], rep
+
+
+@pytest.mark.slow
+def test_fp64_chlorine_like_100k_sampled():
+    """10^5 determinants, 4,096 walkers on the GPU; 32 sampled walkers checked."""
+    wl = synth.chlorine_like_100k()
+    ctx = pkg.Context.from_workload(wl, device=0)
+    got = _gpu_eval(ctx, wl.R)
+    idx = np.random.default_rng(1).choice(wl.n_walk, 32, replace=False)
+    ref = oracle.evaluate(wl, R=wl.R[idx])
+    rep = compare({k: v[idx] for k, v in got.items()}, ref)
+    assert rep["ok"], rep
+    assert np.all(np.isfinite(got["log_abs_psi"]))
+
+
+@pytest.mark.slow
+def test_fp64_chlorine_like_750k_full_size_sampled():
+    """The full 750k-determinant, 8,192-walker workload in one launch sequence;
+    16 sampled walkers checked against the oracle, every walker finite."""
+    wl = synth.chlorine_like_750k()
+    ctx = pkg.Context.from_workload(wl, device=0)
+    got = _gpu_eval(ctx, wl.R)
+    assert np.all(np.isfinite(got["log_abs_psi"]))
+    assert np.all(got["status"] & (pkg.WS_REF_SINGULAR | pkg.WS_NONFINITE) == 0)
+    idx = np.random.default_rng(2).choice(wl.n_walk, 16, replace=False)
+    ref = oracle.evaluate(wl, R=wl.R[idx])
+    rep = compare({k: v[idx] for k, v in got.items()}, ref)
+    assert rep["ok"], rep
