@@ -137,6 +137,48 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def _time_steps(ctx, Rdev, out, flush, stream, steps, warmup, dist, clock_index=None):
+    """Warm up, then time `steps` evaluations with CUDA events (L2 flushed between
+    steps outside the events). Returns per-step ms, per-stage ms and clocks."""
+    import torch
+    for s in range(warmup):
+        ctx.evaluate(Rdev[s % len(Rdev)], out=out)
+    torch.cuda.synchronize()
+    ctx.set_profiling(True)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    stage_ms = []
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clk = ClockSampler(clock_index) if clock_index is not None else None
+    if clk:
+        clk.__enter__()
+    for s in range(steps):
+        flush.fill_(float(s))          # evict L2 between timed steps (outside the events)
+        ev[s][0].record(stream)
+        ctx.evaluate(Rdev[s % len(Rdev)], out=out)
+        ev[s][1].record(stream)
+        stage_ms.append(ctx.profile())  # waits for this step's events
+    torch.cuda.synchronize()
+    if clk:
+        clk.__exit__(None, None, None)
+    if dist is not None:
+        dist.barrier()
+    ctx.set_profiling(False)
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    kern = {k: statistics.mean(d[k] for d in stage_ms) for k in stage_ms[0]}
+    return step_ms, kern, (clk.summary() if clk else None)
+
+
+def _max_over_ranks(x, dist, dev):
+    if dist is None:
+        return x
+    import torch
+    t = torch.tensor([x], device=dev, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -145,59 +187,43 @@ def run_ours(args):
     from paper_1510_00730_gb300 import synth
 
     rank, world, local = _env_int("RANK", 0), _env_int("WORLD_SIZE", 1), _env_int("LOCAL_RANK", 0)
-    if world != args.gpus:
-        world = max(world, 1)
+    world = max(world, 1)
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     dist = None
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=dev)
-    prec = {"mixed": pkg.PRECISION_MIXED, "fp64": pkg.PRECISION_FP64}[args.precision]
+    prec_of = {"mixed": pkg.PRECISION_MIXED, "fp64": pkg.PRECISION_FP64}
+    primary = args.precision
+    others = [p for p in ("mixed", "fp64") if p != primary] if args.compare else []
 
     wl = synth.WORKLOADS[args.workload]()
     W = wl.n_walk
-    ctx = pkg.Context.from_workload(wl, device=local, precision=prec)
-    st = ctx.stats()
-    # distinct walker batches per rank (resident in HBM before timing)
+    N = wl.n_elec
+    # distinct walker batches per rank, resident in HBM before timing
     rng = np.random.default_rng(1000 + rank)
-    batches = [wl.R if (b == 0 and rank == 0) else synth.make_walkers(rng, W, wl.n_elec) for b in range(4)]
+    batches = [wl.R if (b == 0 and rank == 0) else synth.make_walkers(rng, W, N) for b in range(4)]
     Rdev = [torch.from_numpy(np.ascontiguousarray(b)).to(dev) for b in batches]
-    out = ctx.alloc_outputs(W)
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)  # 512 MB > 129 MB L2
     stream = torch.cuda.current_stream(dev)
 
-    for s in range(args.warmup):
-        ctx.evaluate(Rdev[s % 4], out=out)
-    torch.cuda.synchronize()
-
-    ctx.set_profiling(True)
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
-    stage_ms = []
-    if dist is not None:
-        dist.barrier()
-    torch.cuda.synchronize()
-    with ClockSampler(_gpu_index(local)) as clk:
-        for s in range(args.steps):
-            flush.fill_(float(s))          # evict L2 between timed steps (outside the events)
-            ev[s][0].record(stream)
-            ctx.evaluate(Rdev[s % 4], out=out)
-            ev[s][1].record(stream)
-            stage_ms.append(ctx.profile())  # waits for this step's events
-        torch.cuda.synchronize()
-    if dist is not None:
-        dist.barrier()
-    ctx.set_profiling(False)
-    step_ms = [a.elapsed_time(b) for a, b in ev]
-    ms = statistics.mean(step_ms)
-    if dist is not None:
-        t = torch.tensor([ms], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-    value = W * world / (ms / 1e3)
+    results = {}
+    ctxs = {}
+    for pname in [primary] + others:
+        ctx = pkg.Context.from_workload(wl, device=local, precision=prec_of[pname])
+        ctxs[pname] = ctx
+        out = ctx.alloc_outputs(W)
+        step_ms, kern, clocks = _time_steps(ctx, Rdev, out, flush, stream, args.steps, args.warmup, dist,
+                                            _gpu_index(local) if pname == primary else None)
+        ms = _max_over_ranks(statistics.mean(step_ms), dist, dev)
+        results[pname] = dict(ms=ms, value=W * world / (ms / 1e3), kern=kern, clocks=clocks)
+        del out
+    st = ctxs[primary].stats()
+    main = results[primary]
 
     # end to end through the host-memory C-ABI call: H2D of R and D2H of all outputs per step
-    N = wl.n_elec
+    ctx = ctxs[primary]
     hR = torch.empty((W, N, 3), dtype=torch.float64, pin_memory=True)
     hR.numpy()[:] = batches[0]
     hout = dict(log_abs_psi=torch.empty(W, dtype=torch.float64, pin_memory=True).numpy(),
@@ -215,47 +241,49 @@ def run_ours(args):
         t0 = time.perf_counter()
         ctx.evaluate_host(hR.numpy(), out=hout)
         e2e_t.append(time.perf_counter() - t0)
-    e2e_ms = statistics.mean(e2e_t) * 1e3
-    if dist is not None:
-        t = torch.tensor([e2e_ms], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_ms = float(t.item())
+    e2e_ms = _max_over_ranks(statistics.mean(e2e_t) * 1e3, dist, dev)
     h2d = W * N * 3 * 8
     d2h = W * (8 + 1 + 3 * N * 8 + N * 8 + 8 + 4)
 
-    # roofline of the dominant kernel: the FP64 sparse contraction (2 products, 2 FLOP per nonzero per walker)
-    kern = {k: statistics.mean(d[k] for d in stage_ms) for k in stage_ms[0]}
-    flops = 4.0 * st["n_det"] * W
-    achieved = flops / (kern["contract"] / 1e3) / 1e12
-    roofline = {"kernel": "k_spmm_f64 (v = C r_dn, u = C^T r_up)", "bound": "alu", "achieved": achieved,
-                "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS,
-                "traffic": args.traffic, "peak_source": "nominal FP64 of the recipe table (no measured FP64 peak)",
-                "flops_per_launch": flops}
+    # roofline of the dominant kernel: the FP64 sparse contraction, 2 launches per step
+    # (v = C r_dn, u = C^T r_up), each 2 FLOP per nonzero per walker
+    kern = main["kern"]
+    flops_launch = 2.0 * st["n_det"] * W
+    launch_ms = kern["contract"] / 2
+    achieved = flops_launch / (launch_ms / 1e3) / 1e12
+    roofline = {"kernel": "k_spmm_f64", "bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS,
+                "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS, "traffic": args.traffic,
+                "peak_source": "nominal FP64 of the recipe table (no measured FP64 peak)",
+                "flops_per_launch": flops_launch, "launch_ms": launch_ms}
 
-    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f64" if prec == pkg.PRECISION_FP64 else "f32+f64",
+    line = {"metric": METRIC, "value": main["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": main["ms"], "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64" if primary == "fp64" else "f64+f32x2",
             "data": "synthetic",
-            "config": {"workload": args.workload, "precision": args.precision, "walkers_per_gpu": W,
+            "config": {"workload": args.workload, "precision": primary, "walkers_per_gpu": W,
                        "n_det": st["n_det"], "n_det_up": st["n_det_up"], "n_det_dn": st["n_det_dn"],
                        "n_elec": N, "n_ao": st["n_ao"], "n_mo": st["n_mo"],
                        "l2": "flushed between timed steps (512 MB write outside the events)",
                        "parallelism": "dp%d (walkers)" % world},
-            "clocks": clk.summary(),
+            "clocks": main["clocks"],
             "e2e": {"value": W * world / (e2e_ms / 1e3), "unit": UNIT, "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms},
             "gpu_launches": 6 * args.steps,
             "kernels_ms": kern,
             "roofline": roofline}
+    for pname in others:
+        line[pname] = {"value": results[pname]["value"], "ms_per_step": results[pname]["ms"],
+                       "kernels_ms": results[pname]["kern"]}
 
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         from tests.parity import walker_quantiles
-        host = ctx.evaluate_host(batches[0])
         ref, cb = cpu_baseline(wl, CPU_SAMPLE_WALKERS)
         line["cpu_baseline"] = cb
-        line["accuracy_vs_oracle"] = dict(walkers=CPU_SAMPLE_WALKERS,
-                                          **walker_quantiles({k: v[:CPU_SAMPLE_WALKERS] for k, v in host.items()},
-                                                             ref))
+        acc = {}
+        for pname, c in ctxs.items():
+            host = c.evaluate_host(batches[0][:CPU_SAMPLE_WALKERS])
+            acc[pname] = walker_quantiles(host, ref)
+        line["accuracy_vs_oracle"] = dict(walkers=CPU_SAMPLE_WALKERS, **acc)
     if rank == 0:
         print(json.dumps(line), flush=True)
     if dist is not None:
@@ -269,7 +297,9 @@ def main():
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--workload", default="chlorine_like_750k")
-    p.add_argument("--precision", default="fp64", choices=["mixed", "fp64"])
+    p.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
+    p.add_argument("--no-compare", dest="compare", action="store_false",
+                   help="skip timing the other precision in the same run")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--ref-sample", type=int, default=32)
     p.add_argument("--traffic", type=float, default=None, help="DRAM bytes per launch of the dominant kernel (ncu)")

@@ -1,0 +1,147 @@
+// Device helpers shared by the FP64 and mixed-precision kernels.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "mdet_internal.h"
+
+namespace mdet {
+
+static __device__ __forceinline__ double ipow_d(double x, int n) {
+  double r = 1.0;
+  for (int i = 0; i < n; i++) r *= x;
+  return r;
+}
+
+// Determinant of a k x k matrix (k <= 4), row-major in m[4][4].
+template <class F>
+static __device__ __forceinline__ F small_det(int k, const F (&m)[4][4]) {
+  if (k == 0) return F(1);
+  if (k == 1) return m[0][0];
+  if (k == 2) return m[0][0] * m[1][1] - m[0][1] * m[1][0];
+  if (k == 3)
+    return m[0][0] * (m[1][1] * m[2][2] - m[1][2] * m[2][1]) - m[0][1] * (m[1][0] * m[2][2] - m[1][2] * m[2][0]) +
+           m[0][2] * (m[1][0] * m[2][1] - m[1][1] * m[2][0]);
+  // Laplace expansion along rows 0 and 1: 2 x 2 minors of rows (0,1) and (2,3)
+  F s01 = m[0][0] * m[1][1] - m[0][1] * m[1][0];
+  F s02 = m[0][0] * m[1][2] - m[0][2] * m[1][0];
+  F s03 = m[0][0] * m[1][3] - m[0][3] * m[1][0];
+  F s12 = m[0][1] * m[1][2] - m[0][2] * m[1][1];
+  F s13 = m[0][1] * m[1][3] - m[0][3] * m[1][1];
+  F s23 = m[0][2] * m[1][3] - m[0][3] * m[1][2];
+  F c01 = m[2][0] * m[3][1] - m[2][1] * m[3][0];
+  F c02 = m[2][0] * m[3][2] - m[2][2] * m[3][0];
+  F c03 = m[2][0] * m[3][3] - m[2][3] * m[3][0];
+  F c12 = m[2][1] * m[3][2] - m[2][2] * m[3][1];
+  F c13 = m[2][1] * m[3][3] - m[2][3] * m[3][1];
+  F c23 = m[2][2] * m[3][3] - m[2][3] * m[3][2];
+  return s01 * c23 - s02 * c13 + s03 * c12 + s12 * c03 - s13 * c02 + s23 * c01;
+}
+
+// Cofactors cof[alpha][beta] = (-1)^(alpha+beta) det(minor without row alpha, column beta), k <= 4.
+template <class F>
+static __device__ __forceinline__ void small_cof(int k, const F (&m)[4][4], F (&cof)[4][4]) {
+  if (k == 1) {
+    cof[0][0] = F(1);
+    return;
+  }
+  if (k == 2) {
+    cof[0][0] = m[1][1];
+    cof[0][1] = -m[1][0];
+    cof[1][0] = -m[0][1];
+    cof[1][1] = m[0][0];
+    return;
+  }
+  if (k == 3) {
+#pragma unroll
+    for (int a = 0; a < 3; a++)
+#pragma unroll
+      for (int b = 0; b < 3; b++) {
+        const int r0 = a == 0 ? 1 : 0, r1 = a == 2 ? 1 : 2;
+        const int c0 = b == 0 ? 1 : 0, c1 = b == 2 ? 1 : 2;
+        F d = m[r0][c0] * m[r1][c1] - m[r0][c1] * m[r1][c0];
+        cof[a][b] = ((a + b) & 1) ? -d : d;
+      }
+    return;
+  }
+  // k == 4: each 3 x 3 minor is expanded along the row that shares its pair
+  // ({0,1} or {2,3}) with the removed row, using precomputed 2 x 2 minors of the other pair.
+  F top[4][4], bot[4][4];  // 2 x 2 minors of rows (0,1) and (2,3) for column pairs (x < y)
+#pragma unroll
+  for (int x = 0; x < 4; x++)
+#pragma unroll
+    for (int y = x + 1; y < 4; y++) {
+      top[x][y] = m[0][x] * m[1][y] - m[0][y] * m[1][x];
+      bot[x][y] = m[2][x] * m[3][y] - m[2][y] * m[3][x];
+    }
+#pragma unroll
+  for (int a = 0; a < 4; a++) {
+    const int rho = a < 2 ? 1 - a : 5 - a;  // the remaining row of the removed row's pair
+#pragma unroll
+    for (int b = 0; b < 4; b++) {
+      int cols[3];
+      int q = 0;
+#pragma unroll
+      for (int x = 0; x < 4; x++)
+        if (x != b) cols[q++] = x;
+      // det of the 3 x 3 minor = sum_t (-1)^t m[rho][cols[t]] * D2(other two columns)
+      F d = F(0);
+#pragma unroll
+      for (int t = 0; t < 3; t++) {
+        const int x = t == 0 ? cols[1] : cols[0];
+        const int y = t == 2 ? cols[1] : cols[2];
+        const F d2 = a < 2 ? bot[x][y] : top[x][y];
+        const F term = m[rho][cols[t]] * d2;
+        d = (t & 1) ? d - term : d + term;
+      }
+      cof[a][b] = ((a + b) & 1) ? -d : d;
+    }
+  }
+}
+
+
+// Values, gradient and Laplacian of the (l+1)(l+2)/2 Cartesian AOs of one shell
+// at one point (FP64). AO chi = P(x, y, z) f(r^2) with P = x^a y^b z^c of degree
+// l and f(s) = sum_p c_p exp(-alpha_p s):
+//   d_x chi = P_x f + 2 x P f',   Lap chi = (Lap P) f + P ((4 l + 6) f' + 4 s f'')
+// (Euler: x P_x + y P_y + z P_z = l P). store(c, q, value) receives component
+// c (0 value, 1..3 gradient, 4 Laplacian) of the q-th AO of the shell, in the
+// order xx, xy, xz, yy, yz, zz (a descending, then b descending).
+template <class Store>
+static __device__ __forceinline__ void ao_shell_values(const DevProblem& P, int s, const double* r, Store store) {
+  const int l = P.shell_l[s];
+  const double* C = P.nuc_xyz + 3 * P.shell_center[s];
+  const double x = r[0] - C[0], y = r[1] - C[1], z = r[2] - C[2];
+  const double s2 = x * x + y * y + z * z;
+  double f0 = 0, f1 = 0, f2 = 0;
+  const int p0 = P.shell_prim0[s], np = P.shell_nprim[s];
+  for (int p = 0; p < np; p++) {
+    const double al = P.alpha[p0 + p], cf = P.coef[p0 + p];
+    const double ex = cf * exp(-al * s2);
+    f0 += ex;
+    f1 -= al * ex;
+    f2 += al * al * ex;
+  }
+  const double lapf = (4.0 * l + 6.0) * f1 + 4.0 * s2 * f2;
+  int q = 0;
+  for (int a = l; a >= 0; a--)
+    for (int b = l - a; b >= 0; b--, q++) {
+      const int cc = l - a - b;
+      const double xa = ipow_d(x, a), yb = ipow_d(y, b), zc = ipow_d(z, cc);
+      const double P0 = xa * yb * zc;
+      const double Px = a ? a * ipow_d(x, a - 1) * yb * zc : 0.0;
+      const double Py = b ? b * xa * ipow_d(y, b - 1) * zc : 0.0;
+      const double Pz = cc ? cc * xa * yb * ipow_d(z, cc - 1) : 0.0;
+      double lapP = 0.0;
+      if (a >= 2) lapP += a * (a - 1) * ipow_d(x, a - 2) * yb * zc;
+      if (b >= 2) lapP += b * (b - 1) * xa * ipow_d(y, b - 2) * zc;
+      if (cc >= 2) lapP += cc * (cc - 1) * xa * yb * ipow_d(z, cc - 2);
+      store(0, q, P0 * f0);
+      store(1, q, Px * f0 + 2.0 * x * P0 * f1);
+      store(2, q, Py * f0 + 2.0 * y * P0 * f1);
+      store(3, q, Pz * f0 + 2.0 * z * P0 * f1);
+      store(4, q, lapP * f0 + P0 * lapf);
+    }
+}
+
+}  // namespace mdet

@@ -51,6 +51,15 @@ struct mdet_ctx {
 
 namespace {
 
+size_t final_smem_bytes_host(int n_up, int n_dn, int n_mo, bool mixed) {
+  DevProblem P{};
+  P.n_up = n_up;
+  P.n_dn = n_dn;
+  P.n_elec = n_up + n_dn;
+  P.n_mo = n_mo;
+  return final_smem_bytes(P, mixed);
+}
+
 mdet_status fail(mdet_ctx* c, mdet_status s, const char* fmt, ...) {
   char buf[512];
   va_list ap;
@@ -175,7 +184,7 @@ void free_problem(mdet_ctx* c) {
 
 void free_scratch(mdet_ctx* c) {
   DevScratch& S = c->S;
-  void* ptrs[] = {S.phi, S.phi32, S.Ainv, S.ld0, S.sg0, S.g, S.T, S.T32, S.r, S.vu, S.psit, S.wstat,
+  void* ptrs[] = {S.phi, S.Ainv, S.ld0, S.sg0, S.g, S.T, S.Tdf, S.r, S.vu, S.psit, S.wstat,
                   S.R_stage, S.out_stage};
   for (void* p : ptrs)
     if (p) cudaFree(p);
@@ -205,14 +214,17 @@ mdet_status upload_problem(mdet_ctx* c) {
   UP(c->alpha, P.alpha);
   UP(c->coef, P.coef);
   std::vector<double> B((size_t)c->n_ao * c->n_mo);
-  std::vector<float> B32(B.size());
+  std::vector<float> Bh(B.size()), Bl(B.size());
   for (int mu = 0; mu < c->n_ao; mu++)
     for (int m = 0; m < c->n_mo; m++) {
-      B[(size_t)mu * c->n_mo + m] = c->mo_colmajor[mu + (size_t)c->n_ao * m];
-      B32[(size_t)mu * c->n_mo + m] = (float)B[(size_t)mu * c->n_mo + m];
+      const size_t q = (size_t)mu * c->n_mo + m;
+      B[q] = c->mo_colmajor[mu + (size_t)c->n_ao * m];
+      Bh[q] = (float)B[q];                     // double-float split B = Bh + Bl
+      Bl[q] = (float)(B[q] - (double)Bh[q]);
     }
   UP(B, P.B);
-  UP(B32, P.B32);
+  UP(Bh, P.B_hi);
+  UP(Bl, P.B_lo);
   std::vector<int> occ(2 * kMaxSpin, 0);
   for (int sp = 0; sp < 2; sp++)
     for (size_t a = 0; a < c->ref_occ[sp].size(); a++) occ[sp * kMaxSpin + a] = c->ref_occ[sp][a];
@@ -257,6 +269,10 @@ mdet_status ensure_scratch(mdet_ctx* c, int64_t n_walk) {
   if ((s = dalloc(c, &S.sg0, (size_t)W * 2))) return s;
   if ((s = dalloc(c, &S.g, (size_t)W * N * 4))) return s;
   if ((s = dalloc(c, &S.T, (size_t)N * M * wp))) return s;
+  if (c->precision == MDET_PRECISION_MIXED) {
+    if ((s = dalloc(c, &S.Tdf, (size_t)N * M * wp))) return s;
+    CUDA_TRY(c, cudaMemset(S.Tdf, 0, sizeof(float2) * N * M * wp));
+  }
   if ((s = dalloc(c, &S.r, (size_t)ndt * wp))) return s;
   if ((s = dalloc(c, &S.vu, (size_t)ndt * wp))) return s;
   if ((s = dalloc(c, &S.psit, (size_t)wp))) return s;
@@ -394,6 +410,8 @@ mdet_status mdet_set_ci_expansion(mdet_ctx* c, int64_t n_det, int n_int, const u
   if (n_det < 1 || !det_up || !det_dn || !coef) return fail(c, MDET_E_ARG, "empty expansion or null pointer");
   if (n_det >= (int64_t)1 << 31) return fail(c, MDET_E_ARG, "n_det must be below 2^31");
   const int want_int = (c->n_mo + 63) / 64;
+  if (final_smem_bytes_host(c->n_up, c->n_dn, c->n_mo, c->precision == MDET_PRECISION_MIXED) > 227 * 1024)
+    return fail(c, MDET_E_ARG, "(n_up + n_dn) * n_mo too large for the per-walker epilogue (shared memory)");
   if (n_int != want_int) return fail(c, MDET_E_ARG, "n_int=%d but ceil(n_mo/64)=%d", n_int, want_int);
   c->has_ci = false;
   const uint64_t* in[2] = {det_up, det_dn};
@@ -542,7 +560,6 @@ mdet_status mdet_evaluate(mdet_ctx* c, int64_t n_walk, const double* R, double* 
   if (n_walk == 0) return MDET_OK;
   if (n_walk > (int64_t)1 << 30) return fail(c, MDET_E_ARG, "n_walk above 2^30");
   if (!R || !log_abs_psi || !sign || !grad || !lap) return fail(c, MDET_E_ARG, "null device pointer");
-  if (c->precision != MDET_PRECISION_FP64) return fail(c, MDET_E_STATE, "mixed-precision kernels are not built yet");
   CUDA_TRY(c, cudaSetDevice(c->device));
   mdet_status s = ensure_scratch(c, n_walk);
   if (s != MDET_OK) return s;
@@ -552,18 +569,19 @@ mdet_status mdet_evaluate(mdet_ctx* c, int64_t n_walk, const double* R, double* 
   const bool prof = c->profiling;
 #define STAGE_EVENT(i) \
   if (prof) CUDA_TRY(c, cudaEventRecord(c->ev[i], st))
+  const bool mixed = c->precision == MDET_PRECISION_MIXED;
   STAGE_EVENT(0);
-  CUDA_TRY(c, launch_mo_f64(P, S, n_walk, R, st));
+  CUDA_TRY(c, mixed ? launch_mo_mixed(P, S, n_walk, R, st) : launch_mo_f64(P, S, n_walk, R, st));
   STAGE_EVENT(1);
-  CUDA_TRY(c, launch_ref_tables_f64(P, S, n_walk, st));
+  CUDA_TRY(c, launch_ref_tables(P, S, n_walk, mixed, st));
   STAGE_EVENT(2);
-  CUDA_TRY(c, launch_ratios_f64(P, S, n_walk, st));
+  CUDA_TRY(c, mixed ? launch_ratios_mixed(P, S, n_walk, st) : launch_ratios_f64(P, S, n_walk, st));
   STAGE_EVENT(3);
   CUDA_TRY(c, launch_zero_f64(P, S, n_walk, st));
   STAGE_EVENT(4);
   CUDA_TRY(c, launch_contract_f64(P, S, n_walk, st));
   STAGE_EVENT(5);
-  CUDA_TRY(c, launch_final_f64(P, S, n_walk, R, log_abs_psi, sign, grad, lap, e_local, status, st));
+  CUDA_TRY(c, launch_final(P, S, n_walk, R, log_abs_psi, sign, grad, lap, e_local, status, mixed, st));
   STAGE_EVENT(6);
 #undef STAGE_EVENT
   c->have_profile = prof;

@@ -44,7 +44,8 @@ struct DevProblem {
   const double* alpha;     // [n_prim]
   const double* coef;      // [n_prim]
   const double* B;         // [n_ao][n_mo] row-major (B[mu*n_mo + m])
-  const float* B32;        // same in FP32 (mixed path)
+  const float* B_hi;       // B as double-float pairs (mixed path): B = B_hi + B_lo
+  const float* B_lo;
   const int* ref_occ;      // [2][kMaxSpin] ascending occupied MOs of each reference
   const Exc* exc[2];       // [n_det_sp[s]] excitation records
   // C over the distinct determinants, two orderings (Sec. 2.1, Sec. 2.4)
@@ -61,13 +62,12 @@ struct DevScratch {
   int64_t cap_walk = 0;   // capacity in walkers
   int64_t wp = 0;         // padded walker stride of walker-minor arrays
   double* phi = nullptr;  // [W][5][n_elec][n_mo]  value, d/dx, d/dy, d/dz, Laplacian
-  float* phi32 = nullptr; // same in FP32 (mixed path)
   double* Ainv = nullptr; // [W][n_up^2 + n_dn^2]  inverses of the reference Slater matrices, A[a][i]
   double* ld0 = nullptr;  // [W][2] log|D_ref|
   double* sg0 = nullptr;  // [W][2] sign(D_ref)
   double* g = nullptr;    // [W][n_elec][4]  (d_{i mu} D_ref) / D_ref
   double* T = nullptr;    // [n_up + n_dn][n_mo][wp] walker-minor ratio tables (up block then down block)
-  float* T32 = nullptr;   // same in FP32 (mixed path)
+  float2* Tdf = nullptr;  // same as double-float pairs (hi, lo), mixed path only
   double* r = nullptr;    // [n_det_up + n_det_dn][wp] ratios D_I / D_ref, walker-minor
   double* vu = nullptr;   // [n_det_up + n_det_dn][wp]: v = C r_dn (up rows) then u = C^T r_up
   double* psit = nullptr; // [wp] Psi / (D_ref_up D_ref_dn)
@@ -76,18 +76,23 @@ struct DevScratch {
   double* out_stage = nullptr;
 };
 
-// Kernel launchers (mdet_kernels.cu). Each returns the launch error.
+// Kernel launchers (mdet_kernels.cu, mdet_kernels_mixed.cu). Each returns the launch error.
 cudaError_t launch_mo_f64(const DevProblem& P, const DevScratch& S, int64_t n_walk,
                           const double* R, cudaStream_t st);
-cudaError_t launch_ref_tables_f64(const DevProblem& P, const DevScratch& S, int64_t n_walk,
-                                  cudaStream_t st);
+cudaError_t launch_mo_mixed(const DevProblem& P, const DevScratch& S, int64_t n_walk,
+                            const double* R, cudaStream_t st);
+cudaError_t launch_ref_tables(const DevProblem& P, const DevScratch& S, int64_t n_walk, bool mixed,
+                              cudaStream_t st);
 cudaError_t launch_ratios_f64(const DevProblem& P, const DevScratch& S, int64_t n_walk,
                               cudaStream_t st);
+cudaError_t launch_ratios_mixed(const DevProblem& P, const DevScratch& S, int64_t n_walk,
+                                cudaStream_t st);
 cudaError_t launch_zero_f64(const DevProblem& P, const DevScratch& S, int64_t n_walk, cudaStream_t st);
 cudaError_t launch_contract_f64(const DevProblem& P, const DevScratch& S, int64_t n_walk,
                                 cudaStream_t st);
-cudaError_t launch_final_f64(const DevProblem& P, const DevScratch& S, int64_t n_walk,
-                             const double* R, double* log_abs_psi, int8_t* sign, double* grad,
-                             double* lap, double* e_local, uint32_t* status, cudaStream_t st);
+size_t final_smem_bytes(const DevProblem& P, bool mixed);
+cudaError_t launch_final(const DevProblem& P, const DevScratch& S, int64_t n_walk, const double* R,
+                         double* log_abs_psi, int8_t* sign, double* grad, double* lap, double* e_local,
+                         uint32_t* status, bool mixed, cudaStream_t st);
 
 }  // namespace mdet

@@ -1,12 +1,15 @@
 // FP64 kernels of one evaluation (Sec. 2.2-2.4), in launch order:
 //   k_mo_f64         orbitals and their derivatives at every electron (Sec. 2)
-//   k_ref_f64        LU with partial pivoting of each reference Slater matrix,
+//   k_ref            LU with partial pivoting of each reference Slater matrix,
 //                    its inverse A, log|D_ref|, the table T = A Phi and the
 //                    single-determinant derivatives g (Sec. 2.2; Sec. 5 Table method)
 //   k_ratio_f64      D_I / D_ref = eps_I det T[h_I, p_I] for every distinct
 //                    spin determinant (k x k, k <= 4)
 //   k_spmm_f64       v = C r_dn (plus Psi~ = r_up . v) and u = C^T r_up (Sec. 2.4)
-//   k_final_f64      derivative aggregation and the per-walker epilogue (Eqs. 5-8)
+//   k_final          derivative aggregation and the per-walker epilogue (Eqs. 5-8)
+// k_ref and k_final take a MIXED flag: the mixed-precision variants (and the
+// mixed orbital and ratio kernels of mdet_kernels_mixed.cu) run the
+// per-determinant work in double-float on the FP32 pipe; see df32.cuh.
 //
 // Notation. For spin s with n electrons (rows i) and reference occupied MOs
 // o_1 < ... < o_n (columns a): S_ref[i][a] = phi_{o_a}(r_i), A = S_ref^-1
@@ -28,6 +31,8 @@
 #include <cfloat>
 #include <cmath>
 
+#include "df32.cuh"
+#include "mdet_device.cuh"
 #include "mdet_internal.h"
 
 namespace mdet {
@@ -35,98 +40,6 @@ namespace mdet {
 namespace {
 
 constexpr int kEC = 6;  // electrons per CTA in the orbital kernel
-
-__device__ __forceinline__ double ipow_d(double x, int n) {
-  double r = 1.0;
-  for (int i = 0; i < n; i++) r *= x;
-  return r;
-}
-
-// Determinant of a k x k matrix (k <= 4), row-major in m[4][4].
-template <class F>
-__device__ __forceinline__ F small_det(int k, const F (&m)[4][4]) {
-  if (k == 0) return F(1);
-  if (k == 1) return m[0][0];
-  if (k == 2) return m[0][0] * m[1][1] - m[0][1] * m[1][0];
-  if (k == 3)
-    return m[0][0] * (m[1][1] * m[2][2] - m[1][2] * m[2][1]) - m[0][1] * (m[1][0] * m[2][2] - m[1][2] * m[2][0]) +
-           m[0][2] * (m[1][0] * m[2][1] - m[1][1] * m[2][0]);
-  // Laplace expansion along rows 0 and 1: 2 x 2 minors of rows (0,1) and (2,3)
-  F s01 = m[0][0] * m[1][1] - m[0][1] * m[1][0];
-  F s02 = m[0][0] * m[1][2] - m[0][2] * m[1][0];
-  F s03 = m[0][0] * m[1][3] - m[0][3] * m[1][0];
-  F s12 = m[0][1] * m[1][2] - m[0][2] * m[1][1];
-  F s13 = m[0][1] * m[1][3] - m[0][3] * m[1][1];
-  F s23 = m[0][2] * m[1][3] - m[0][3] * m[1][2];
-  F c01 = m[2][0] * m[3][1] - m[2][1] * m[3][0];
-  F c02 = m[2][0] * m[3][2] - m[2][2] * m[3][0];
-  F c03 = m[2][0] * m[3][3] - m[2][3] * m[3][0];
-  F c12 = m[2][1] * m[3][2] - m[2][2] * m[3][1];
-  F c13 = m[2][1] * m[3][3] - m[2][3] * m[3][1];
-  F c23 = m[2][2] * m[3][3] - m[2][3] * m[3][2];
-  return s01 * c23 - s02 * c13 + s03 * c12 + s12 * c03 - s13 * c02 + s23 * c01;
-}
-
-// Cofactors cof[alpha][beta] = (-1)^(alpha+beta) det(minor without row alpha, column beta), k <= 4.
-template <class F>
-__device__ __forceinline__ void small_cof(int k, const F (&m)[4][4], F (&cof)[4][4]) {
-  if (k == 1) {
-    cof[0][0] = F(1);
-    return;
-  }
-  if (k == 2) {
-    cof[0][0] = m[1][1];
-    cof[0][1] = -m[1][0];
-    cof[1][0] = -m[0][1];
-    cof[1][1] = m[0][0];
-    return;
-  }
-  if (k == 3) {
-#pragma unroll
-    for (int a = 0; a < 3; a++)
-#pragma unroll
-      for (int b = 0; b < 3; b++) {
-        const int r0 = a == 0 ? 1 : 0, r1 = a == 2 ? 1 : 2;
-        const int c0 = b == 0 ? 1 : 0, c1 = b == 2 ? 1 : 2;
-        F d = m[r0][c0] * m[r1][c1] - m[r0][c1] * m[r1][c0];
-        cof[a][b] = ((a + b) & 1) ? -d : d;
-      }
-    return;
-  }
-  // k == 4: each 3 x 3 minor is expanded along the row that shares its pair
-  // ({0,1} or {2,3}) with the removed row, using precomputed 2 x 2 minors of the other pair.
-  F top[4][4], bot[4][4];  // 2 x 2 minors of rows (0,1) and (2,3) for column pairs (x < y)
-#pragma unroll
-  for (int x = 0; x < 4; x++)
-#pragma unroll
-    for (int y = x + 1; y < 4; y++) {
-      top[x][y] = m[0][x] * m[1][y] - m[0][y] * m[1][x];
-      bot[x][y] = m[2][x] * m[3][y] - m[2][y] * m[3][x];
-    }
-#pragma unroll
-  for (int a = 0; a < 4; a++) {
-    const int rho = a < 2 ? 1 - a : 5 - a;  // the remaining row of the removed row's pair
-#pragma unroll
-    for (int b = 0; b < 4; b++) {
-      int cols[3];
-      int q = 0;
-#pragma unroll
-      for (int x = 0; x < 4; x++)
-        if (x != b) cols[q++] = x;
-      // det of the 3 x 3 minor = sum_t (-1)^t m[rho][cols[t]] * D2(other two columns)
-      F d = F(0);
-#pragma unroll
-      for (int t = 0; t < 3; t++) {
-        const int x = t == 0 ? cols[1] : cols[0];
-        const int y = t == 2 ? cols[1] : cols[2];
-        const F d2 = a < 2 ? bot[x][y] : top[x][y];
-        const F term = m[rho][cols[t]] * d2;
-        d = (t & 1) ? d - term : d + term;
-      }
-      cof[a][b] = ((a + b) & 1) ? -d : d;
-    }
-  }
-}
 
 // ---------------------------------------------------------------------------
 // K1: orbitals. grid (n_walk, ceil(n_elec / kEC)); smem X[5][kEC][n_ao].
@@ -150,39 +63,7 @@ __global__ void __launch_bounds__(128) k_mo_f64(DevProblem P, double* __restrict
       continue;
     }
     const double* r = R + (w * N + e_begin + e) * 3;
-    const double* C = P.nuc_xyz + 3 * P.shell_center[s];
-    const double x = r[0] - C[0], y = r[1] - C[1], z = r[2] - C[2];
-    const double s2 = x * x + y * y + z * z;
-    double f0 = 0, f1 = 0, f2 = 0;
-    const int p0 = P.shell_prim0[s], np = P.shell_nprim[s];
-    for (int p = 0; p < np; p++) {
-      const double al = P.alpha[p0 + p], cf = P.coef[p0 + p];
-      const double ex = cf * exp(-al * s2);
-      f0 += ex;
-      f1 -= al * ex;
-      f2 += al * al * ex;
-    }
-    const double lapf = (4.0 * l + 6.0) * f1 + 4.0 * s2 * f2;
-    int q = 0;
-    for (int a = l; a >= 0; a--)
-      for (int b = l - a; b >= 0; b--, q++) {
-        const int cc = l - a - b;
-        const double xa = ipow_d(x, a), yb = ipow_d(y, b), zc = ipow_d(z, cc);
-        const double P0 = xa * yb * zc;
-        const double Px = a ? a * ipow_d(x, a - 1) * yb * zc : 0.0;
-        const double Py = b ? b * xa * ipow_d(y, b - 1) * zc : 0.0;
-        const double Pz = cc ? cc * xa * yb * ipow_d(z, cc - 1) : 0.0;
-        double lapP = 0.0;
-        if (a >= 2) lapP += a * (a - 1) * ipow_d(x, a - 2) * yb * zc;
-        if (b >= 2) lapP += b * (b - 1) * xa * ipow_d(y, b - 2) * zc;
-        if (cc >= 2) lapP += cc * (cc - 1) * xa * yb * ipow_d(z, cc - 2);
-        const int mu = ao0 + q;
-        X[(0 * kEC + e) * K + mu] = P0 * f0;
-        X[(1 * kEC + e) * K + mu] = Px * f0 + 2.0 * x * P0 * f1;
-        X[(2 * kEC + e) * K + mu] = Py * f0 + 2.0 * y * P0 * f1;
-        X[(3 * kEC + e) * K + mu] = Pz * f0 + 2.0 * z * P0 * f1;
-        X[(4 * kEC + e) * K + mu] = lapP * f0 + P0 * lapf;
-      }
+    ao_shell_values(P, s, r, [&](int c, int q, double v) { X[(c * kEC + e) * K + ao0 + q] = v; });
   }
   __syncthreads();
   for (int m = threadIdx.x; m < M; m += blockDim.x) {
@@ -207,8 +88,9 @@ __global__ void __launch_bounds__(128) k_mo_f64(DevProblem P, double* __restrict
 // spin s by Gauss-Jordan elimination with partial pivoting on [S | I] (rows
 // stay in their lanes; the pivot order is a permutation whose parity enters
 // the sign of the determinant). Then every thread computes T and g.
-// smem: aug[2][kMaxSpin][2*kMaxSpin] + A[2][kMaxSpin][kMaxSpin]
-__global__ void __launch_bounds__(64) k_ref_f64(DevProblem P, DevScratch S) {
+// With MIXED the table is also written as double-float pairs for the FP32-pipe kernels.
+template <bool MIXED>
+__global__ void __launch_bounds__(64) k_ref(DevProblem P, DevScratch S) {
   __shared__ double aug[2][kMaxSpin][2 * kMaxSpin];
   __shared__ int rowof[2][kMaxSpin];  // lane whose right half holds row a of A
   __shared__ int bad[2];
@@ -307,7 +189,12 @@ __global__ void __launch_bounds__(64) k_ref_f64(DevProblem P, DevScratch S) {
     double acc = 0.0;
     if (!bad[sp])
       for (int i = 0; i < n; i++) acc = fma(Aat(sp, a, i), S.phi[((w * 5 + 0) * N + e0 + i) * M + m], acc);
-    S.T[(size_t)t * S.wp + w] = bad[sp] ? NAN : acc;
+    if (bad[sp]) acc = NAN;
+    S.T[(size_t)t * S.wp + w] = acc;
+    if (MIXED) {
+      const df32 d = df_from_double(acc);
+      S.Tdf[(size_t)t * S.wp + w] = make_float2(d.hi, d.lo);
+    }
   }
   for (int t = threadIdx.x; t < N * 4; t += blockDim.x) {
     const int e = t >> 2, mu = t & 3;
@@ -401,24 +288,41 @@ __global__ void __launch_bounds__(256) k_spmm_f64(const int* __restrict__ seg, c
 // K6: per walker: W scatter over every determinant, Q = A^T W, Pm = T Q^T,
 // G_{i mu} = g Psi~ + sum_m d_mu phi[i][m] Q[i][m] - sum_b d_mu phi[i][o_b] Pm[b][i],
 // then grad, Laplacian, log|Psi|, sign and E_L. grid n_walk, block 128.
-// smem: T[N][M], W[N][M], Q[N][M] (rows of both spins stacked), A blocks, Pm.
-__global__ void __launch_bounds__(128) k_final_f64(DevProblem P, DevScratch S, const double* __restrict__ R,
-                                                   double* __restrict__ log_abs_psi, int8_t* __restrict__ sign,
-                                                   double* __restrict__ grad, double* __restrict__ lap,
-                                                   double* __restrict__ e_local, uint32_t* __restrict__ status) {
+// FP64 variant: cofactors in FP64, W accumulated with FP64 shared atomics.
+// MIXED variant: cofactors in double-float on the FP32 pipe; W accumulated as
+// a compensated pair of FP32 shared atomics: the atomic returns the old value,
+// so TwoSum(old, x) recovers the rounding error of the addition it performed,
+// which goes into the low word. Q, Pm and G stay FP64.
+// smem: T[N][M] (FP64), W[N][M] (FP64, or hi/lo FP32 pairs then FP64),
+//       Q[N][M], Tdf[N][M] (MIXED), A blocks, Pm.
+template <bool MIXED>
+__global__ void __launch_bounds__(128) k_final(DevProblem P, DevScratch S, const double* __restrict__ R,
+                                               double* __restrict__ log_abs_psi, int8_t* __restrict__ sign,
+                                               double* __restrict__ grad, double* __restrict__ lap,
+                                               double* __restrict__ e_local, uint32_t* __restrict__ status) {
   extern __shared__ double sm[];
   const int nu = P.n_up, nd = P.n_dn, N = nu + nd, M = P.n_mo;
+  const int NM = N * M;
   const int64_t w = blockIdx.x, wp = S.wp;
-  double* Ts = sm;                 // [N][M]
-  double* Ws = Ts + N * M;         // [N][M]
-  double* Qs = Ws + N * M;         // [N][M]
-  double* As = Qs + N * M;         // [nu*nu + nd*nd]
+  double* Ts = sm;                      // [N][M]
+  double* Ws = Ts + NM;                 // [N][M]
+  double* Qs = Ws + NM;                 // [N][M]
+  double* As = Qs + NM;                 // [nu*nu + nd*nd]
   double* Pm = As + nu * nu + nd * nd;  // [nu*nu + nd*nd]  Pm[b][i] per spin
+  float2* Tdf = reinterpret_cast<float2*>(Pm + nu * nu + nd * nd);  // [N][M] (MIXED)
+  float* Whi = reinterpret_cast<float*>(Ws);                          // MIXED: [N][M] hi words
+  float* Wlo = Whi + NM;                                              //        [N][M] lo words
   __shared__ double red[4];
   __shared__ double Gs[kMaxSpin * 2][4];
-  for (int t = threadIdx.x; t < N * M; t += blockDim.x) {
+  for (int t = threadIdx.x; t < NM; t += blockDim.x) {
     Ts[t] = S.T[(size_t)t * wp + w];
-    Ws[t] = 0.0;
+    if (MIXED) {
+      Tdf[t] = S.Tdf[(size_t)t * wp + w];
+      Whi[t] = 0.0f;
+      Wlo[t] = 0.0f;
+    } else {
+      Ws[t] = 0.0;
+    }
   }
   for (int t = threadIdx.x; t < nu * nu + nd * nd; t += blockDim.x) As[t] = S.Ainv[w * (nu * nu + nd * nd) + t];
   __syncthreads();
@@ -429,28 +333,58 @@ __global__ void __launch_bounds__(128) k_final_f64(DevProblem P, DevScratch S, c
     if (e.k == 0) continue;
     const double wgt = (e.eps < 0 ? -1.0 : 1.0) * S.vu[(size_t)t * wp + w];
     if (wgt == 0.0) continue;
-    const double* Tb = Ts + (sp ? nu * M : 0);
-    double* Wb = Ws + (sp ? nu * M : 0);
-    double m[4][4], cof[4][4];
+    const int off = sp ? nu * M : 0;
+    if (MIXED) {
+      df32 m[4][4], cof[4][4];
 #pragma unroll
-    for (int a = 0; a < 4; a++)
+      for (int a = 0; a < 4; a++)
 #pragma unroll
-      for (int b = 0; b < 4; b++) m[a][b] = (a < e.k && b < e.k) ? Tb[e.h[a] * M + e.p[b]] : 0.0;
-    small_cof(e.k, m, cof);
+        for (int b = 0; b < 4; b++) {
+          const float2 v = (a < e.k && b < e.k) ? Tdf[off + e.h[a] * M + e.p[b]] : make_float2(0.f, 0.f);
+          m[a][b] = df32(v.x, v.y);
+        }
+      small_cof(e.k, m, cof);
+      const df32 wd = df_from_double(wgt);
 #pragma unroll
-    for (int a = 0; a < 4; a++)
+      for (int a = 0; a < 4; a++)
 #pragma unroll
-      for (int b = 0; b < 4; b++)
-        if (a < e.k && b < e.k) atomicAdd(Wb + e.h[a] * M + e.p[b], wgt * cof[a][b]);
+        for (int b = 0; b < 4; b++)
+          if (a < e.k && b < e.k) {
+            const df32 x = cof[a][b] * wd;
+            const int slot = off + e.h[a] * M + e.p[b];
+            const float old = atomicAdd(Whi + slot, x.hi);
+            float s_, err;
+            two_sum(old, x.hi, s_, err);
+            atomicAdd(Wlo + slot, __fadd_rn(err, x.lo));
+          }
+    } else {
+      double m[4][4], cof[4][4];
+#pragma unroll
+      for (int a = 0; a < 4; a++)
+#pragma unroll
+        for (int b = 0; b < 4; b++) m[a][b] = (a < e.k && b < e.k) ? Ts[off + e.h[a] * M + e.p[b]] : 0.0;
+      small_cof(e.k, m, cof);
+#pragma unroll
+      for (int a = 0; a < 4; a++)
+#pragma unroll
+        for (int b = 0; b < 4; b++)
+          if (a < e.k && b < e.k) atomicAdd(Ws + off + e.h[a] * M + e.p[b], wgt * cof[a][b]);
+    }
   }
   __syncthreads();
+  // MIXED: W as FP64 goes into the table pairs' space, which the scatter no longer needs
+  double* Wd = MIXED ? reinterpret_cast<double*>(Tdf) : Ws;
+  if (MIXED) {
+    for (int t = threadIdx.x; t < NM; t += blockDim.x) Wd[t] = (double)Whi[t] + (double)Wlo[t];
+    __syncthreads();
+  }
   // Q[i][m] = sum_a A[a][i] W[a][m] (per spin block)
-  for (int t = threadIdx.x; t < N * M; t += blockDim.x) {
+  for (int t = threadIdx.x; t < NM; t += blockDim.x) {
     const int row = t / M, m = t - row * M;
     const int sp = row < nu ? 0 : 1;
     const int n = sp ? nd : nu, e0 = sp ? nu : 0, i = row - e0;
     const double* A = As + (sp ? nu * nu : 0);
-    const double* Wb = Ws + e0 * M;
+    const double* Wb = Wd + e0 * M;
     double acc = 0.0;
     for (int a = 0; a < n; a++) acc = fma(A[a * n + i], Wb[a * M + m], acc);
     Qs[t] = acc;
@@ -556,8 +490,12 @@ cudaError_t launch_mo_f64(const DevProblem& P, const DevScratch& S, int64_t n_wa
   return cudaGetLastError();
 }
 
-cudaError_t launch_ref_tables_f64(const DevProblem& P, const DevScratch& S, int64_t n_walk, cudaStream_t st) {
-  k_ref_f64<<<(unsigned)n_walk, 64, 0, st>>>(P, S);
+cudaError_t launch_ref_tables(const DevProblem& P, const DevScratch& S, int64_t n_walk, bool mixed,
+                              cudaStream_t st) {
+  if (mixed)
+    k_ref<true><<<(unsigned)n_walk, 64, 0, st>>>(P, S);
+  else
+    k_ref<false><<<(unsigned)n_walk, 64, 0, st>>>(P, S);
   return cudaGetLastError();
 }
 
@@ -596,16 +534,21 @@ cudaError_t launch_contract_f64(const DevProblem& P, const DevScratch& S, int64_
   return cudaGetLastError();
 }
 
-cudaError_t launch_final_f64(const DevProblem& P, const DevScratch& S, int64_t n_walk, const double* R,
-                             double* log_abs_psi, int8_t* sign, double* grad, double* lap, double* e_local,
-                             uint32_t* status, cudaStream_t st) {
-  const int N = P.n_elec, M = P.n_mo;
-  const size_t smem = sizeof(double) * (3 * (size_t)N * M + 2 * (P.n_up * P.n_up + P.n_dn * P.n_dn));
+size_t final_smem_bytes(const DevProblem& P, bool mixed) {
+  const size_t NM = (size_t)P.n_elec * P.n_mo;
+  return sizeof(double) * (3 * NM + 2 * (size_t)(P.n_up * P.n_up + P.n_dn * P.n_dn)) + (mixed ? 8 * NM : 0);
+}
+
+cudaError_t launch_final(const DevProblem& P, const DevScratch& S, int64_t n_walk, const double* R,
+                         double* log_abs_psi, int8_t* sign, double* grad, double* lap, double* e_local,
+                         uint32_t* status, bool mixed, cudaStream_t st) {
+  const size_t smem = final_smem_bytes(P, mixed);
+  auto kern = mixed ? k_final<true> : k_final<false>;
   if (smem > 48 * 1024) {
-    cudaError_t e = cudaFuncSetAttribute(k_final_f64, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
   }
-  k_final_f64<<<(unsigned)n_walk, 128, smem, st>>>(P, S, R, log_abs_psi, sign, grad, lap, e_local, status);
+  kern<<<(unsigned)n_walk, 128, smem, st>>>(P, S, R, log_abs_psi, sign, grad, lap, e_local, status);
   return cudaGetLastError();
 }
 
