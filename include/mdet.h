@@ -192,7 +192,33 @@ enum {
 mdet_status mdet_set_profiling(mdet_ctx* ctx, int enable);
 mdet_status mdet_get_profile(mdet_ctx* ctx, float* ms);
 
-/* Sizes and excitation statistics (host only; works without a device). */
+/*
+ * Psi~ = r_up . (C r_dn) per walker, without any device allocation.
+ *
+ * The paper has no counterpart: this entry point exists for callers that
+ * cannot allocate device memory when they call it (a pooled or custom device
+ * allocator that owns all of the GPU's memory, or a runtime that forbids
+ * allocation after start-up). It runs the row-ordered contraction kernel of
+ * mdet_evaluate on ratios the caller supplies, keeping the intermediate
+ * v = C r_dn in a static device array of MDET_NOALLOC_SCRATCH_DOUBLES doubles
+ * (32 MiB) that every GPU loading this library holds until the process exits.
+ *   r          device, [n_det_up + n_det_dn][ld] walker-minor ratios D_I / D_ref
+ *              of the distinct determinants in the context's order (up block,
+ *              then down block; mdet_get_ratios gives them walker-major),
+ *              16-byte aligned; ld a multiple of 128 and >= n_walk
+ *   psi_tilde  device, [n_walk]: Psi / (D_ref_up D_ref_dn)
+ * Asynchronous on `stream`. Fails with MDET_E_ARG when
+ * (n_det_up + 1) * ld exceeds MDET_NOALLOC_SCRATCH_DOUBLES. The first call on
+ * a device looks up the array's device address (cudaGetSymbolAddress) and
+ * should come before any stream capture on that device. Every call shares the
+ * one array and leaves its contents behind; it clears what it uses before use,
+ * and calls that overlap on the GPU (other streams, other threads) race.
+ */
+#define MDET_NOALLOC_SCRATCH_DOUBLES (4u * 1024u * 1024u)
+mdet_status mdet_psi_tilde_noalloc(mdet_ctx* ctx, int64_t n_walk, const double* r, int64_t ld,
+                                   double* psi_tilde, void* stream);
+
+/* Sizes and excitation statistics (host only; works without a device). *//* Sizes and excitation statistics (host only; works without a device). */
 mdet_status mdet_get_stats(const mdet_ctx* ctx, mdet_stats* out);
 
 /*

@@ -70,11 +70,13 @@ def load_library(build_if_missing: bool = True):
     L.mdet_get_spin_dets.argtypes = [vp, i32, vp, vp, vp]
     L.mdet_get_ci_matrix.argtypes = [vp, vp, vp, vp]
     L.mdet_omega_sort.argtypes = [i64, i32, vp, vp]
+    L.mdet_psi_tilde_noalloc.argtypes = [vp, i64, vp, i64, vp, vp]
     L.mdet_set_profiling.argtypes = [vp, i32]
     L.mdet_get_profile.argtypes = [vp, vp]
     for name in ("mdet_create", "mdet_set_system", "mdet_set_orbitals", "mdet_set_ci_expansion", "mdet_evaluate",
                  "mdet_evaluate_host", "mdet_get_ratios", "mdet_get_stats", "mdet_get_spin_dets",
-                 "mdet_get_ci_matrix", "mdet_omega_sort", "mdet_set_profiling", "mdet_get_profile"):
+                 "mdet_get_ci_matrix", "mdet_omega_sort", "mdet_set_profiling", "mdet_get_profile",
+                 "mdet_psi_tilde_noalloc"):
         getattr(L, name).restype = i32
     _lib = L
     return L
@@ -216,6 +218,19 @@ class Context:
         self._check(self._L.mdet_get_ratios(self._h, n_walk, _ptr(r_up), _ptr(r_dn), _ptr(ld0), _ptr(sg0)),
                     "mdet_get_ratios")
         return r_up, r_dn, ld0, sg0
+
+    NOALLOC_SCRATCH_DOUBLES = 4 * 1024 * 1024
+
+    def psi_tilde_noalloc(self, r, ld, psi_tilde, stream=None):
+        """Psi~ = r_up . (C r_dn) from walker-minor ratios r (CUDA float64,
+        [n_det_up + n_det_dn, ld]) into psi_tilde (CUDA float64, [n_walk]),
+        using the library's static scratch instead of any device allocation."""
+        import torch
+        if stream is None:
+            stream = torch.cuda.current_stream(psi_tilde.device)
+        sp = stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream)
+        self._check(self._L.mdet_psi_tilde_noalloc(self._h, psi_tilde.shape[0], r.data_ptr(), int(ld),
+                                                   psi_tilde.data_ptr(), sp), "mdet_psi_tilde_noalloc")
 
     STAGES = ("orbitals", "reference", "ratios", "zero", "contract", "final")
 

@@ -286,6 +286,14 @@ mdet_status ensure_scratch(mdet_ctx* c, int64_t n_walk) {
 
 }  // namespace
 
+namespace mdet {
+const DevProblem* ctx_problem(const mdet_ctx* c, int* device) {
+  if (!c || c->device < 0 || !c->has_ci) return nullptr;
+  if (device) *device = c->device;
+  return &c->P;
+}
+}  // namespace mdet
+
 extern "C" {
 
 const char* mdet_status_string(mdet_status s) {

@@ -90,6 +90,12 @@ cudaError_t launch_ratios_mixed(const DevProblem& P, const DevScratch& S, int64_
 cudaError_t launch_zero_f64(const DevProblem& P, const DevScratch& S, int64_t n_walk, cudaStream_t st);
 cudaError_t launch_contract_f64(const DevProblem& P, const DevScratch& S, int64_t n_walk,
                                 cudaStream_t st);
+// v = C r_dn over the row-major copy of C with Psi~ = r_up . v accumulated in
+// psit, for walker-minor arrays of leading dimension ld (a multiple of 128).
+cudaError_t launch_spmm_rows_f64(const DevProblem& P, const double* r_dn, const double* r_up, double* v,
+                                 double* psit, int64_t ld, int64_t n_walk, cudaStream_t st);
+// Device index and uploaded problem of a context (null when it has none).
+const DevProblem* ctx_problem(const mdet_ctx* ctx, int* device);
 size_t final_smem_bytes(const DevProblem& P, bool mixed);
 cudaError_t launch_final(const DevProblem& P, const DevScratch& S, int64_t n_walk, const double* R,
                          double* log_abs_psi, int8_t* sign, double* grad, double* lap, double* e_local,

@@ -534,6 +534,15 @@ cudaError_t launch_contract_f64(const DevProblem& P, const DevScratch& S, int64_
   return cudaGetLastError();
 }
 
+cudaError_t launch_spmm_rows_f64(const DevProblem& P, const double* r_dn, const double* r_up, double* v,
+                                 double* psit, int64_t ld, int64_t n_walk, cudaStream_t st) {
+  const int chunk = 512;
+  const int64_t nchunks = (P.nnz + chunk - 1) / chunk;
+  dim3 grid((unsigned)((nchunks + 7) / 8), (unsigned)((n_walk + 127) / 128));
+  k_spmm_f64<<<grid, 256, 0, st>>>(P.csr_row, P.csr_col, P.csr_val, P.nnz, chunk, r_dn, v, ld, r_up, psit);
+  return cudaGetLastError();
+}
+
 size_t final_smem_bytes(const DevProblem& P, bool mixed) {
   const size_t NM = (size_t)P.n_elec * P.n_mo;
   return sizeof(double) * (3 * NM + 2 * (size_t)(P.n_up * P.n_up + P.n_dn * P.n_dn)) + (mixed ? 8 * NM : 0);
