@@ -212,6 +212,8 @@ def run_ours(args):
     ctxs = {}
     for pname in [primary] + others:
         ctx = pkg.Context.from_workload(wl, device=local, precision=prec_of[pname])
+        if args.chunks is not None:
+            ctx.set_walker_chunks(args.chunks)
         ctxs[pname] = ctx
         out = ctx.alloc_outputs(W)
         step_ms, kern, clocks = _time_steps(ctx, Rdev, out, flush, stream, args.steps, args.warmup, dist,
@@ -301,6 +303,7 @@ def main():
     p.add_argument("--no-compare", dest="compare", action="store_false",
                    help="skip timing the other precision in the same run")
     p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--chunks", type=int, default=None, help="walker chunks of the mixed path (default: library's)")
     p.add_argument("--ref-sample", type=int, default=32)
     p.add_argument("--traffic", type=float, default=None, help="DRAM bytes per launch of the dominant kernel (ncu)")
     args = p.parse_args()

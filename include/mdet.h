@@ -175,10 +175,24 @@ mdet_status mdet_get_ratios(mdet_ctx* ctx, int64_t n_walk, double* r_up, double*
                             double* log_d0, int8_t* sign_d0);
 
 /*
+ * Walker chunking of the mixed-precision evaluation: a batch is cut into
+ * n_chunks chunks (multiples of 256 walkers) evaluated on the context's own
+ * streams, forked from and joined back to the caller's stream, so the FP32-pipe
+ * stages of one chunk overlap the FP64 contraction of another (the FP64
+ * contractions themselves run one after another). 0 selects the default (1,
+ * no overlap), 1 disables the overlap. Values above 4 are clamped. The FP64 path always
+ * runs as one chunk on the caller's stream.
+ */
+mdet_status mdet_set_walker_chunks(mdet_ctx* ctx, int n_chunks);
+
+/*
+ * Stage timing./*
  * Stage timing. With profiling on, every mdet_evaluate records CUDA events on
  * its stream around each stage; mdet_get_profile waits for the last one and
  * writes the durations in milliseconds of the last evaluation, in the order
- * MDET_STAGE_* below (ms: [MDET_N_STAGES]). Off by default.
+ * MDET_STAGE_* below (ms: [MDET_N_STAGES]), summed over walker chunks (with
+ * chunks the stages of different chunks overlap, so the sum can exceed the
+ * step time). Off by default.
  */
 enum {
   MDET_STAGE_ORBITALS = 0,  /* AO values and AO->MO product (Sec. 2) */
@@ -217,6 +231,15 @@ mdet_status mdet_get_profile(mdet_ctx* ctx, float* ms);
 #define MDET_NOALLOC_SCRATCH_DOUBLES (4u * 1024u * 1024u)
 mdet_status mdet_psi_tilde_noalloc(mdet_ctx* ctx, int64_t n_walk, const double* r, int64_t ld,
                                    double* psi_tilde, void* stream);
+
+/*
+ * Diagnostic of the double-float arithmetic used by the mixed path: for n
+ * device values x_i <= 0, y_df[i] = double-float exp(x_i), y_ref[i] = FP64
+ * exp(x_i), prod_df[i] = double-float x_i * x_{(i+1) mod n} + x_i (all device
+ * pointers). Synchronous.
+ */
+mdet_status mdet_selftest_df32(int device, int64_t n, const double* x, double* y_df, double* y_ref,
+                               double* prod_df);
 
 /* Sizes and excitation statistics (host only; works without a device). *//* Sizes and excitation statistics (host only; works without a device). */
 mdet_status mdet_get_stats(const mdet_ctx* ctx, mdet_stats* out);

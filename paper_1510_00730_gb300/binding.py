@@ -72,11 +72,13 @@ def load_library(build_if_missing: bool = True):
     L.mdet_omega_sort.argtypes = [i64, i32, vp, vp]
     L.mdet_psi_tilde_noalloc.argtypes = [vp, i64, vp, i64, vp, vp]
     L.mdet_set_profiling.argtypes = [vp, i32]
+    L.mdet_set_walker_chunks.argtypes = [vp, i32]
+    L.mdet_selftest_df32.argtypes = [i32, i64, vp, vp, vp, vp]
     L.mdet_get_profile.argtypes = [vp, vp]
     for name in ("mdet_create", "mdet_set_system", "mdet_set_orbitals", "mdet_set_ci_expansion", "mdet_evaluate",
                  "mdet_evaluate_host", "mdet_get_ratios", "mdet_get_stats", "mdet_get_spin_dets",
                  "mdet_get_ci_matrix", "mdet_omega_sort", "mdet_set_profiling", "mdet_get_profile",
-                 "mdet_psi_tilde_noalloc"):
+                 "mdet_psi_tilde_noalloc", "mdet_set_walker_chunks", "mdet_selftest_df32"):
         getattr(L, name).restype = i32
     _lib = L
     return L
@@ -101,6 +103,18 @@ def omega_sort(dets) -> np.ndarray:
     if st:
         raise MdetError(st, "mdet_omega_sort failed")
     return order
+
+
+def selftest_df32(x):
+    """Double-float exp and product against FP64 on the device (x: CUDA float64, <= 0)."""
+    import torch
+    L = load_library()
+    y_df, y_ref, prod = torch.empty_like(x), torch.empty_like(x), torch.empty_like(x)
+    st = L.mdet_selftest_df32(x.device.index or 0, x.numel(), x.data_ptr(), y_df.data_ptr(), y_ref.data_ptr(),
+                              prod.data_ptr())
+    if st:
+        raise MdetError(st, "mdet_selftest_df32 failed")
+    return y_df, y_ref, prod
 
 
 class Context:
@@ -233,6 +247,10 @@ class Context:
                                                    psi_tilde.data_ptr(), sp), "mdet_psi_tilde_noalloc")
 
     STAGES = ("orbitals", "reference", "ratios", "zero", "contract", "final")
+
+    def set_walker_chunks(self, n_chunks):
+        """Mixed precision: evaluate a batch in n_chunks overlapping chunks (0 = default, 1 = none)."""
+        self._check(self._L.mdet_set_walker_chunks(self._h, int(n_chunks)), "mdet_set_walker_chunks")
 
     def set_profiling(self, enable=True):
         self._check(self._L.mdet_set_profiling(self._h, int(bool(enable))), "mdet_set_profiling")

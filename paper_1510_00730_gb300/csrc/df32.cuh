@@ -66,4 +66,48 @@ static __device__ __forceinline__ df32 operator*(df32 x, df32 y) {
   return {s, t};
 }
 
+// exp(t) for t <= 0 in double-float. Cody-Waite reduction t = k ln2 + r with
+// ln2 split into three floats of 16, 24 and 24 significant bits (k * kLn2a is
+// exact for |k| < 256 and k * kLn2b is made exact with TwoProd), so r carries
+// the full double-float accuracy; |r| <= ln2/2. exp(r) is the Taylor series to
+// degree 13 (truncation below 5e-18 relative) in Horner form with 1/n! as
+// double-float constants, then scaled by 2^k. Arguments below -87 (results
+// below the FP32 normal range) return 0.
+__device__ __constant__ static const float kLn2a = 0x1.62e4p-1f;       // ln 2, leading 16 bits
+__device__ __constant__ static const float kLn2b = 0x1.7f7d1cp-20f;    // next 24 bits
+__device__ __constant__ static const float kLn2c = 0x1.ef357ap-45f;    // next 24 bits
+__device__ __constant__ static const float kInvFact[14][2] = {          // 1/n! as (hi, lo)
+    {0x1p+0f, 0.0f},
+    {0x1p+0f, 0.0f},
+    {0x1p-1f, 0.0f},
+    {0x1.555556p-3f, -0x1.555556p-28f},
+    {0x1.555556p-5f, -0x1.555556p-30f},
+    {0x1.111112p-7f, -0x1.dddddep-32f},
+    {0x1.6c16c2p-10f, -0x1.27d27ep-35f},
+    {0x1.a01a02p-13f, -0x1.7f97fap-39f},
+    {0x1.a01a02p-16f, -0x1.7f97fap-42f},
+    {0x1.71de3ap-19f, 0x1.55b1ccp-45f},
+    {0x1.27e4fcp-22f, -0x1.10ec14p-47f},
+    {0x1.ae6456p-26f, 0x1.fd5138p-52f},
+    {0x1.1eed8ep-29f, 0x1.ff1b12p-54f},
+    {0x1.612462p-33f, -0x1.8af25ep-58f}};
+
+static __device__ __forceinline__ df32 df_exp_nonpos(df32 t) {
+  if (!(t.hi > -87.0f)) return df32(0.0f, 0.0f);
+  const float kf = rintf(__fmul_rn(t.hi, 1.44269504f));
+  // r = t - k ln2, each piece of k ln2 exact in double-float
+  df32 r = t + df32(__fmul_rn(-kf, kLn2a), 0.0f);
+  {
+    const float p = __fmul_rn(-kf, kLn2b);
+    const float e = __fmaf_rn(-kf, kLn2b, -p);
+    r = r + df32(p, e);
+  }
+  r = r + df32(__fmul_rn(-kf, kLn2c), 0.0f);
+  df32 p(kInvFact[13][0], kInvFact[13][1]);
+#pragma unroll
+  for (int n = 12; n >= 0; n--) p = p * r + df32(kInvFact[n][0], kInvFact[n][1]);
+  const int k = (int)kf;
+  return df32(ldexpf(p.hi, k), ldexpf(p.lo, k));
+}
+
 }  // namespace mdet

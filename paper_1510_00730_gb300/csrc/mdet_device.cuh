@@ -3,6 +3,7 @@
 
 #include <cuda_runtime.h>
 
+#include "df32.cuh"
 #include "mdet_internal.h"
 
 namespace mdet {
@@ -140,6 +141,59 @@ static __device__ __forceinline__ void ao_shell_values(const DevProblem& P, int 
       store(1, q, Px * f0 + 2.0 * x * P0 * f1);
       store(2, q, Py * f0 + 2.0 * y * P0 * f1);
       store(3, q, Pz * f0 + 2.0 * z * P0 * f1);
+      store(4, q, lapP * f0 + P0 * lapf);
+    }
+}
+
+// The same AO values in double-float arithmetic on the FP32 pipe (mixed
+// path): coordinates, exponents and coefficients arrive as (hi, lo) pairs and
+// exp is df_exp_nonpos. Same formulas, component order and store() contract.
+static __device__ __forceinline__ df32 df_ipow(df32 x, int n) {
+  df32 r(1);
+  for (int i = 0; i < n; i++) r = r * x;
+  return r;
+}
+
+template <class Store>
+static __device__ __forceinline__ void ao_shell_values_df(const DevProblem& P, int s, const df32* r, Store store) {
+  const int l = P.shell_l[s];
+  const float2* C = P.nuc_df + 3 * P.shell_center[s];
+  const df32 x = r[0] - df32(C[0].x, C[0].y);
+  const df32 y = r[1] - df32(C[1].x, C[1].y);
+  const df32 z = r[2] - df32(C[2].x, C[2].y);
+  const df32 s2 = x * x + y * y + z * z;
+  df32 f0(0), f1(0), f2(0);
+  const int p0 = P.shell_prim0[s], np = P.shell_nprim[s];
+  for (int p = 0; p < np; p++) {
+    const float2 a2 = P.alpha_df[p0 + p], c2 = P.coef_df[p0 + p];
+    const df32 al(a2.x, a2.y), cf(c2.x, c2.y);
+    const df32 ex = cf * df_exp_nonpos(-(al * s2));
+    const df32 ae = al * ex;
+    f0 = f0 + ex;
+    f1 = f1 - ae;
+    f2 = f2 + al * ae;
+  }
+  const df32 lapf = df32(4 * l + 6) * f1 + df32(4) * (s2 * f2);
+  const df32 two(2);
+  int q = 0;
+  for (int a = l; a >= 0; a--)
+    for (int b = l - a; b >= 0; b--, q++) {
+      const int cc = l - a - b;
+      const df32 xa = df_ipow(x, a), yb = df_ipow(y, b), zc = df_ipow(z, cc);
+      const df32 yz = yb * zc;
+      const df32 P0 = xa * yz;
+      const df32 Px = a ? df32(a) * (df_ipow(x, a - 1) * yz) : df32(0);
+      const df32 Py = b ? df32(b) * (xa * df_ipow(y, b - 1) * zc) : df32(0);
+      const df32 Pz = cc ? df32(cc) * (xa * yb * df_ipow(z, cc - 1)) : df32(0);
+      df32 lapP(0);
+      if (a >= 2) lapP = lapP + df32(a * (a - 1)) * (df_ipow(x, a - 2) * yz);
+      if (b >= 2) lapP = lapP + df32(b * (b - 1)) * (xa * df_ipow(y, b - 2) * zc);
+      if (cc >= 2) lapP = lapP + df32(cc * (cc - 1)) * (xa * yb * df_ipow(z, cc - 2));
+      const df32 P0f1 = two * (P0 * f1);
+      store(0, q, P0 * f0);
+      store(1, q, Px * f0 + x * P0f1);
+      store(2, q, Py * f0 + y * P0f1);
+      store(3, q, Pz * f0 + z * P0f1);
       store(4, q, lapP * f0 + P0 * lapf);
     }
 }

@@ -43,10 +43,17 @@ struct mdet_ctx {
   cudaStream_t own_stream = nullptr;
   cudaStream_t last_stream = nullptr;
   int64_t last_walk = 0;
+  // walker chunks evaluated on their own streams (mixed precision): the FP32-pipe
+  // stages of one chunk overlap the FP64 contraction of another
+  static constexpr int kMaxChunks = 4;
+  int n_chunks_cfg = 0;  // 0: automatic
+  cudaStream_t cs[kMaxChunks] = {};
+  cudaEvent_t fork = nullptr, joined[kMaxChunks] = {}, contracted[kMaxChunks] = {};
   // stage timing
   bool profiling = false;
   bool have_profile = false;
-  cudaEvent_t ev[MDET_N_STAGES + 1] = {};
+  int prof_chunks = 0;
+  cudaEvent_t ev[kMaxChunks][MDET_N_STAGES + 1] = {};
 };
 
 namespace {
@@ -225,6 +232,18 @@ mdet_status upload_problem(mdet_ctx* c) {
   UP(B, P.B);
   UP(Bh, P.B_hi);
   UP(Bl, P.B_lo);
+  auto split = [](const std::vector<double>& v) {
+    std::vector<float2> o(v.size());
+    for (size_t i = 0; i < v.size(); i++) {
+      const float h = (float)v[i];
+      o[i] = make_float2(h, (float)(v[i] - (double)h));
+    }
+    return o;
+  };
+  std::vector<float2> a_df = split(c->alpha), c_df = split(c->coef), x_df = split(c->nuc_xyz);
+  UP(a_df, P.alpha_df);
+  UP(c_df, P.coef_df);
+  UP(x_df, P.nuc_df);
   std::vector<int> occ(2 * kMaxSpin, 0);
   for (int sp = 0; sp < 2; sp++)
     for (size_t a = 0; a < c->ref_occ[sp].size(); a++) occ[sp * kMaxSpin + a] = c->ref_occ[sp][a];
@@ -274,7 +293,7 @@ mdet_status ensure_scratch(mdet_ctx* c, int64_t n_walk) {
     CUDA_TRY(c, cudaMemset(S.Tdf, 0, sizeof(float2) * N * M * wp));
   }
   if ((s = dalloc(c, &S.r, (size_t)ndt * wp))) return s;
-  if ((s = dalloc(c, &S.vu, (size_t)ndt * wp))) return s;
+  if ((s = dalloc(c, &S.vu, (size_t)ndt * wp))) return s;  // walker-major [wp][ndt]
   if ((s = dalloc(c, &S.psit, (size_t)wp))) return s;
   if ((s = dalloc(c, &S.wstat, (size_t)W))) return s;
   // padded walker columns of the tables must hold finite values
@@ -327,7 +346,14 @@ mdet_status mdet_create(mdet_ctx** out, int device, int precision) {
       delete c;
       return MDET_E_CUDA;
     }
-    if (cudaSetDevice(device) != cudaSuccess || cudaStreamCreateWithFlags(&c->own_stream, cudaStreamNonBlocking) != cudaSuccess) {
+    bool ok = cudaSetDevice(device) == cudaSuccess &&
+              cudaStreamCreateWithFlags(&c->own_stream, cudaStreamNonBlocking) == cudaSuccess &&
+              cudaEventCreateWithFlags(&c->fork, cudaEventDisableTiming) == cudaSuccess;
+    for (int i = 0; ok && i < mdet_ctx::kMaxChunks; i++)
+      ok = cudaStreamCreateWithFlags(&c->cs[i], cudaStreamNonBlocking) == cudaSuccess &&
+           cudaEventCreateWithFlags(&c->joined[i], cudaEventDisableTiming) == cudaSuccess &&
+           cudaEventCreateWithFlags(&c->contracted[i], cudaEventDisableTiming) == cudaSuccess;
+    if (!ok) {
       delete c;
       return MDET_E_CUDA;
     }
@@ -343,8 +369,14 @@ void mdet_destroy(mdet_ctx* c) {
     cudaDeviceSynchronize();
     free_scratch(c);
     free_problem(c);
-    for (int i = 0; i <= MDET_N_STAGES; i++)
-      if (c->ev[i]) cudaEventDestroy(c->ev[i]);
+    for (int k = 0; k < mdet_ctx::kMaxChunks; k++) {
+      for (int i = 0; i <= MDET_N_STAGES; i++)
+        if (c->ev[k][i]) cudaEventDestroy(c->ev[k][i]);
+      if (c->cs[k]) cudaStreamDestroy(c->cs[k]);
+      if (c->joined[k]) cudaEventDestroy(c->joined[k]);
+      if (c->contracted[k]) cudaEventDestroy(c->contracted[k]);
+    }
+    if (c->fork) cudaEventDestroy(c->fork);
     if (c->own_stream) cudaStreamDestroy(c->own_stream);
   }
   delete c;
@@ -573,25 +605,56 @@ mdet_status mdet_evaluate(mdet_ctx* c, int64_t n_walk, const double* R, double* 
   if (s != MDET_OK) return s;
   cudaStream_t st = (cudaStream_t)stream;
   const DevProblem& P = c->P;
-  const DevScratch& S = c->S;
-  const bool prof = c->profiling;
-#define STAGE_EVENT(i) \
-  if (prof) CUDA_TRY(c, cudaEventRecord(c->ev[i], st))
   const bool mixed = c->precision == MDET_PRECISION_MIXED;
-  STAGE_EVENT(0);
-  CUDA_TRY(c, mixed ? launch_mo_mixed(P, S, n_walk, R, st) : launch_mo_f64(P, S, n_walk, R, st));
-  STAGE_EVENT(1);
-  CUDA_TRY(c, launch_ref_tables(P, S, n_walk, mixed, st));
-  STAGE_EVENT(2);
-  CUDA_TRY(c, mixed ? launch_ratios_mixed(P, S, n_walk, st) : launch_ratios_f64(P, S, n_walk, st));
-  STAGE_EVENT(3);
-  CUDA_TRY(c, launch_zero_f64(P, S, n_walk, st));
-  STAGE_EVENT(4);
-  CUDA_TRY(c, launch_contract_f64(P, S, n_walk, st));
-  STAGE_EVENT(5);
-  CUDA_TRY(c, launch_final(P, S, n_walk, R, log_abs_psi, sign, grad, lap, e_local, status, mixed, st));
-  STAGE_EVENT(6);
+  const bool prof = c->profiling;
+  // chunking: mixed precision splits large batches so chunks overlap on separate streams
+  int nch = 1;
+  if (mixed) {
+    const int64_t tiles = (n_walk + kWalkerPad - 1) / kWalkerPad;
+    nch = c->n_chunks_cfg > 0 ? c->n_chunks_cfg : 1;
+    nch = (int)std::min<int64_t>(std::min<int64_t>(nch, tiles), mdet_ctx::kMaxChunks);
+  }
+  const int64_t tiles = (n_walk + kWalkerPad - 1) / kWalkerPad;
+  if (prof)
+    for (int k = 0; k < nch; k++)
+      for (int i = 0; i <= MDET_N_STAGES; i++)
+        if (!c->ev[k][i]) CUDA_TRY(c, cudaEventCreate(&c->ev[k][i]));
+  if (nch > 1) CUDA_TRY(c, cudaEventRecord(c->fork, st));
+  const int64_t N = P.n_elec;
+  for (int k = 0; k < nch; k++) {
+    const int64_t t0 = tiles * k / nch, t1 = tiles * (k + 1) / nch;
+    const int64_t off = t0 * kWalkerPad;
+    const int64_t n = std::min<int64_t>(t1 * kWalkerPad, n_walk) - off;
+    cudaStream_t ks = nch > 1 ? c->cs[k] : st;
+    if (nch > 1) CUDA_TRY(c, cudaStreamWaitEvent(ks, c->fork, 0));
+    const DevScratch S = scratch_view(c->S, P, off);
+#define STAGE_EVENT(i) \
+  if (prof) CUDA_TRY(c, cudaEventRecord(c->ev[k][i], ks))
+    const double* Rk = R + off * N * 3;
+    STAGE_EVENT(0);
+    CUDA_TRY(c, mixed ? launch_mo_mixed(P, S, n, Rk, ks) : launch_mo_f64(P, S, n, Rk, ks));
+    STAGE_EVENT(1);
+    CUDA_TRY(c, launch_ref_tables(P, S, n, mixed, ks));
+    STAGE_EVENT(2);
+    CUDA_TRY(c, mixed ? launch_ratios_mixed(P, S, n, ks) : launch_ratios_f64(P, S, n, ks));
+    STAGE_EVENT(3);
+    CUDA_TRY(c, launch_zero_f64(P, S, n, ks));
+    // the FP64 contractions of successive chunks run one after another
+    if (nch > 1 && k > 0) CUDA_TRY(c, cudaStreamWaitEvent(ks, c->contracted[k - 1], 0));
+    STAGE_EVENT(4);
+    CUDA_TRY(c, launch_contract_f64(P, S, n, ks));
+    STAGE_EVENT(5);
+    if (nch > 1) CUDA_TRY(c, cudaEventRecord(c->contracted[k], ks));
+    CUDA_TRY(c, launch_final(P, S, n, Rk, log_abs_psi + off, sign + off, grad + off * N * 3, lap + off * N,
+                             e_local ? e_local + off : nullptr, status ? status + off : nullptr, mixed, ks));
+    STAGE_EVENT(6);
 #undef STAGE_EVENT
+    if (nch > 1) {
+      CUDA_TRY(c, cudaEventRecord(c->joined[k], ks));
+      CUDA_TRY(c, cudaStreamWaitEvent(st, c->joined[k], 0));
+    }
+  }
+  c->prof_chunks = nch;
   c->have_profile = prof;
   c->last_stream = st;
   c->last_walk = n_walk;
@@ -668,12 +731,16 @@ mdet_status mdet_get_ratios(mdet_ctx* c, int64_t n_walk, double* r_up, double* r
   return MDET_OK;
 }
 
+mdet_status mdet_set_walker_chunks(mdet_ctx* c, int n_chunks) {
+  if (!c || n_chunks < 0) return MDET_E_ARG;
+  c->n_chunks_cfg = std::min(n_chunks, (int)mdet_ctx::kMaxChunks);
+  return MDET_OK;
+}
+
 mdet_status mdet_set_profiling(mdet_ctx* c, int enable) {
   if (!c) return MDET_E_ARG;
   if (c->device < 0) return fail(c, MDET_E_NODEVICE, "context has no device");
   CUDA_TRY(c, cudaSetDevice(c->device));
-  if (enable && !c->ev[0])
-    for (int i = 0; i <= MDET_N_STAGES; i++) CUDA_TRY(c, cudaEventCreate(&c->ev[i]));
   c->profiling = enable != 0;
   c->have_profile = false;
   return MDET_OK;
@@ -683,8 +750,24 @@ mdet_status mdet_get_profile(mdet_ctx* c, float* ms) {
   if (!c || !ms) return MDET_E_ARG;
   if (!c->have_profile) return fail(c, MDET_E_STATE, "no profiled evaluation yet");
   CUDA_TRY(c, cudaSetDevice(c->device));
-  CUDA_TRY(c, cudaEventSynchronize(c->ev[MDET_N_STAGES]));
-  for (int i = 0; i < MDET_N_STAGES; i++) CUDA_TRY(c, cudaEventElapsedTime(&ms[i], c->ev[i], c->ev[i + 1]));
+  for (int i = 0; i < MDET_N_STAGES; i++) ms[i] = 0.0f;
+  for (int k = 0; k < c->prof_chunks; k++) {
+    CUDA_TRY(c, cudaEventSynchronize(c->ev[k][MDET_N_STAGES]));
+    for (int i = 0; i < MDET_N_STAGES; i++) {
+      float t = 0.0f;
+      CUDA_TRY(c, cudaEventElapsedTime(&t, c->ev[k][i], c->ev[k][i + 1]));
+      ms[i] += t;
+    }
+  }
+  return MDET_OK;
+}
+
+mdet_status mdet_selftest_df32(int device, int64_t n, const double* x, double* y_df, double* y_ref,
+                               double* prod_df) {
+  if (n < 1 || !x || !y_df || !y_ref || !prod_df || device < 0) return MDET_E_ARG;
+  if (cudaSetDevice(device) != cudaSuccess) return MDET_E_CUDA;
+  if (launch_selftest_df(n, x, y_df, y_ref, prod_df, nullptr) != cudaSuccess) return MDET_E_CUDA;
+  if (cudaDeviceSynchronize() != cudaSuccess) return MDET_E_CUDA;
   return MDET_OK;
 }
 

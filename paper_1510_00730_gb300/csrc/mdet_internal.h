@@ -12,7 +12,7 @@ namespace mdet {
 constexpr int kMaxSpin = MDET_MAX_SPIN_ELEC;
 constexpr int kMaxExc = MDET_MAX_EXC;
 constexpr int kMaxL = MDET_MAX_L;
-constexpr int kWalkerPad = 128;  // walker-minor arrays are padded to a multiple of this
+constexpr int kWalkerPad = 256;  // walker-minor arrays are padded to a multiple of this
 
 // Excitation of one distinct spin determinant relative to the reference of its
 // spin: columns h[0..k) of the reference Slater matrix (hole positions, in the
@@ -46,6 +46,9 @@ struct DevProblem {
   const double* B;         // [n_ao][n_mo] row-major (B[mu*n_mo + m])
   const float* B_hi;       // B as double-float pairs (mixed path): B = B_hi + B_lo
   const float* B_lo;
+  const float2* alpha_df;  // exponents, coefficients and nuclear positions as (hi, lo) pairs
+  const float2* coef_df;
+  const float2* nuc_df;
   const int* ref_occ;      // [2][kMaxSpin] ascending occupied MOs of each reference
   const Exc* exc[2];       // [n_det_sp[s]] excitation records
   // C over the distinct determinants, two orderings (Sec. 2.1, Sec. 2.4)
@@ -69,7 +72,7 @@ struct DevScratch {
   double* T = nullptr;    // [n_up + n_dn][n_mo][wp] walker-minor ratio tables (up block then down block)
   float2* Tdf = nullptr;  // same as double-float pairs (hi, lo), mixed path only
   double* r = nullptr;    // [n_det_up + n_det_dn][wp] ratios D_I / D_ref, walker-minor
-  double* vu = nullptr;   // [n_det_up + n_det_dn][wp]: v = C r_dn (up rows) then u = C^T r_up
+  double* vu = nullptr;   // walker-major [wp][n_det_up + n_det_dn]: v = C r_dn (up) then u = C^T r_up (down)
   double* psit = nullptr; // [wp] Psi / (D_ref_up D_ref_dn)
   uint32_t* wstat = nullptr;  // [W] status bits
   double* R_stage = nullptr;  // host-API staging buffers
@@ -90,12 +93,17 @@ cudaError_t launch_ratios_mixed(const DevProblem& P, const DevScratch& S, int64_
 cudaError_t launch_zero_f64(const DevProblem& P, const DevScratch& S, int64_t n_walk, cudaStream_t st);
 cudaError_t launch_contract_f64(const DevProblem& P, const DevScratch& S, int64_t n_walk,
                                 cudaStream_t st);
+// A view of the scratch for walkers [off, off + n): walker-major arrays move by
+// whole walkers, walker-minor arrays by columns (off must be a multiple of kWalkerPad).
+DevScratch scratch_view(const DevScratch& S, const DevProblem& P, int64_t off);
 // v = C r_dn over the row-major copy of C with Psi~ = r_up . v accumulated in
 // psit, for walker-minor arrays of leading dimension ld (a multiple of 128).
 cudaError_t launch_spmm_rows_f64(const DevProblem& P, const double* r_dn, const double* r_up, double* v,
                                  double* psit, int64_t ld, int64_t n_walk, cudaStream_t st);
 // Device index and uploaded problem of a context (null when it has none).
 const DevProblem* ctx_problem(const mdet_ctx* ctx, int* device);
+cudaError_t launch_selftest_df(int64_t n, const double* x, double* y_df, double* y_ref, double* prod_df,
+                               cudaStream_t st);
 size_t final_smem_bytes(const DevProblem& P, bool mixed);
 cudaError_t launch_final(const DevProblem& P, const DevScratch& S, int64_t n_walk, const double* R,
                          double* log_abs_psi, int8_t* sign, double* grad, double* lap, double* e_local,

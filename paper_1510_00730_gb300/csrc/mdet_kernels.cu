@@ -28,6 +28,7 @@
 //   sum_I w_I d_{i mu} D_I / D_ref = g_{i mu} Psi~ + sum_{a,m} A[a][i] Y_{i mu}[m] W[a][m],
 //   W[a][m] = sum_I w_I eps_I cof(M_I)[alpha][beta] over (h_alpha, p_beta) = (a, m),
 // so the per-determinant derivative vectors are never stored.
+#include <algorithm>
 #include <cfloat>
 #include <cmath>
 
@@ -285,6 +286,63 @@ __global__ void __launch_bounds__(256) k_spmm_f64(const int* __restrict__ seg, c
 }
 
 // ---------------------------------------------------------------------------
+// K5 (form used by mdet_evaluate): the same segmented product with 8 walkers
+// per lane (256 per warp). Work items are (chunk of nonzeros, group of 256
+// walkers), chunks fastest so that warps in flight share the same walker
+// columns of x in L2; the loop also serves a persistent launch with fewer
+// blocks. Output y is walker-major: y[w * ldy + seg_off + seg], the layout the
+// epilogue reads.
+__global__ void __launch_bounds__(128) k_spmm_wm(const int* __restrict__ seg, const int* __restrict__ gidx,
+                                                 const double* __restrict__ val, int64_t nnz, int chunk,
+                                                 int64_t n_chunks, int64_t n_groups,
+                                                 const double* __restrict__ x, int64_t wp,
+                                                 double* __restrict__ y, int64_t ldy, int seg_off,
+                                                 const double* __restrict__ rdot, double* __restrict__ psit) {
+  const int lane = threadIdx.x & 31;
+  const int64_t nwarps = (int64_t)gridDim.x * (blockDim.x >> 5);
+  for (int64_t item = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); item < n_chunks * n_groups;
+       item += nwarps) {
+    const int64_t ch = item % n_chunks, grp = item / n_chunks;
+    const int64_t k0 = ch * chunk, k1 = min(k0 + (int64_t)chunk, nnz);
+    const int64_t wb = grp * 256 + lane * 8;
+    double a[8];
+#pragma unroll
+    for (int j = 0; j < 8; j++) a[j] = 0.0;
+    int cur = __ldg(seg + k0);
+    auto flush = [&](int sg) {
+#pragma unroll
+      for (int j = 0; j < 8; j++) atomicAdd(y + (wb + j) * ldy + seg_off + sg, a[j]);
+      if (rdot) {
+        const double* rp = rdot + (size_t)sg * wp + wb;
+#pragma unroll
+        for (int j = 0; j < 8; j++) atomicAdd(psit + wb + j, rp[j] * a[j]);
+      }
+    };
+    for (int64_t k = k0; k < k1; k++) {
+      const int sg = __ldg(seg + k);
+      if (sg != cur) {
+        flush(cur);
+        cur = sg;
+#pragma unroll
+        for (int j = 0; j < 8; j++) a[j] = 0.0;
+      }
+      const double c = __ldg(val + k);
+      const double2* xp = reinterpret_cast<const double2*>(x + (size_t)__ldg(gidx + k) * wp + wb);
+      const double2 x0 = __ldg(xp), x1 = __ldg(xp + 1), x2 = __ldg(xp + 2), x3 = __ldg(xp + 3);
+      a[0] = fma(c, x0.x, a[0]);
+      a[1] = fma(c, x0.y, a[1]);
+      a[2] = fma(c, x1.x, a[2]);
+      a[3] = fma(c, x1.y, a[3]);
+      a[4] = fma(c, x2.x, a[4]);
+      a[5] = fma(c, x2.y, a[5]);
+      a[6] = fma(c, x3.x, a[6]);
+      a[7] = fma(c, x3.y, a[7]);
+    }
+    flush(cur);
+  }
+}
+
+// ---------------------------------------------------------------------------
 // K6: per walker: W scatter over every determinant, Q = A^T W, Pm = T Q^T,
 // G_{i mu} = g Psi~ + sum_m d_mu phi[i][m] Q[i][m] - sum_b d_mu phi[i][o_b] Pm[b][i],
 // then grad, Laplacian, log|Psi|, sign and E_L. grid n_walk, block 128.
@@ -327,11 +385,16 @@ __global__ void __launch_bounds__(128) k_final(DevProblem P, DevScratch S, const
   for (int t = threadIdx.x; t < nu * nu + nd * nd; t += blockDim.x) As[t] = S.Ainv[w * (nu * nu + nd * nd) + t];
   __syncthreads();
   const int nu_det = P.n_det_sp[0], ntot = nu_det + P.n_det_sp[1];
-  for (int t = threadIdx.x; t < ntot; t += blockDim.x) {
+  // each thread walks its own contiguous block of determinants, so the lanes
+  // of a warp hold determinants far apart in the (degree, key) order; those
+  // rarely share a (hole, particle) slot, which keeps the shared atomics apart
+  const int per = (ntot + blockDim.x - 1) / blockDim.x;
+  const int t_begin = threadIdx.x * per, t_end = min(ntot, t_begin + per);
+  for (int t = t_begin; t < t_end; t++) {
     const int sp = t < nu_det ? 0 : 1;
     const Exc e = P.exc[sp][sp ? t - nu_det : t];
     if (e.k == 0) continue;
-    const double wgt = (e.eps < 0 ? -1.0 : 1.0) * S.vu[(size_t)t * wp + w];
+    const double wgt = (e.eps < 0 ? -1.0 : 1.0) * S.vu[w * ntot + t];
     if (wgt == 0.0) continue;
     const int off = sp ? nu * M : 0;
     if (MIXED) {
@@ -508,30 +571,58 @@ cudaError_t launch_ratios_f64(const DevProblem& P, const DevScratch& S, int64_t 
 }
 
 cudaError_t launch_zero_f64(const DevProblem& P, const DevScratch& S, int64_t n_walk, cudaStream_t st) {
-  (void)n_walk;
   const int64_t ndt = (int64_t)P.n_det_sp[0] + P.n_det_sp[1];
-  cudaError_t e = cudaMemsetAsync(S.vu, 0, sizeof(double) * ndt * S.wp, st);
+  const int64_t npad = (n_walk + kWalkerPad - 1) / kWalkerPad * kWalkerPad;
+  cudaError_t e = cudaMemsetAsync(S.vu, 0, sizeof(double) * ndt * npad, st);
   if (e != cudaSuccess) return e;
-  return cudaMemsetAsync(S.psit, 0, sizeof(double) * S.wp, st);
+  return cudaMemsetAsync(S.psit, 0, sizeof(double) * npad, st);
 }
 
 cudaError_t launch_contract_f64(const DevProblem& P, const DevScratch& S, int64_t n_walk, cudaStream_t st) {
-  cudaError_t e;
+  static int n_sm = 0;
+  if (!n_sm) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n_sm <= 0) n_sm = 132;
+  }
   const int chunk = 512;
-  const int64_t nchunks = (P.nnz + chunk - 1) / chunk;
-  const int64_t wgroups = (n_walk + 127) / 128;
-  dim3 grid((unsigned)((nchunks + 7) / 8), (unsigned)wgroups);
+  const int64_t n_chunks = (P.nnz + chunk - 1) / chunk;
+  const int64_t n_groups = (n_walk + 255) / 256;
+  const int64_t items = n_chunks * n_groups;
+  // one work item per warp (full occupancy hides the L2 latency of the gathers)
+  const int64_t blocks = (items + 3) / 4;
+  (void)n_sm;
+  const int64_t ndt = (int64_t)P.n_det_sp[0] + P.n_det_sp[1];
   const double* r_up = S.r;
   const double* r_dn = S.r + (size_t)P.n_det_sp[0] * S.wp;
-  double* v = S.vu;
-  double* u = S.vu + (size_t)P.n_det_sp[0] * S.wp;
-  // v = C r_dn (rows = up determinants) and Psi~ = r_up . v
-  k_spmm_f64<<<grid, 256, 0, st>>>(P.csr_row, P.csr_col, P.csr_val, P.nnz, chunk, r_dn, v, S.wp, r_up, S.psit);
-  e = cudaGetLastError();
+  // v = C r_dn (rows = up determinants) with Psi~ = r_up . v
+  k_spmm_wm<<<(unsigned)blocks, 128, 0, st>>>(P.csr_row, P.csr_col, P.csr_val, P.nnz, chunk, n_chunks, n_groups,
+                                               r_dn, S.wp, S.vu, ndt, 0, r_up, S.psit);
+  cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   // u = C^T r_up (columns = down determinants), in the paper's column-major order
-  k_spmm_f64<<<grid, 256, 0, st>>>(P.csc_col, P.csc_row, P.csc_val, P.nnz, chunk, r_up, u, S.wp, nullptr, nullptr);
+  k_spmm_wm<<<(unsigned)blocks, 128, 0, st>>>(P.csc_col, P.csc_row, P.csc_val, P.nnz, chunk, n_chunks, n_groups,
+                                               r_up, S.wp, S.vu, ndt, P.n_det_sp[0], nullptr, nullptr);
   return cudaGetLastError();
+}
+
+DevScratch scratch_view(const DevScratch& S, const DevProblem& P, int64_t off) {
+  DevScratch V = S;
+  if (off == 0) return V;
+  const int64_t N = P.n_elec, M = P.n_mo;
+  const int64_t ndt = (int64_t)P.n_det_sp[0] + P.n_det_sp[1];
+  V.phi = S.phi + off * 5 * N * M;
+  V.Ainv = S.Ainv + off * (P.n_up * P.n_up + P.n_dn * P.n_dn);
+  V.ld0 = S.ld0 + off * 2;
+  V.sg0 = S.sg0 + off * 2;
+  V.g = S.g + off * N * 4;
+  V.wstat = S.wstat + off;
+  V.vu = S.vu + off * ndt;
+  V.T = S.T + off;  // walker-minor: a column offset with the same stride
+  if (S.Tdf) V.Tdf = S.Tdf + off;
+  V.r = S.r + off;
+  V.psit = S.psit + off;
+  return V;
 }
 
 cudaError_t launch_spmm_rows_f64(const DevProblem& P, const double* r_dn, const double* r_up, double* v,

@@ -21,21 +21,28 @@ namespace {
 constexpr int kECm = 6;  // electrons per CTA in the orbital kernel
 
 // Orbitals. grid (n_walk, ceil(n_elec / kECm)), block 128. AO values and
-// derivatives are formed in FP64 (ao_shell_values), split into FP32 pairs
-// x = xh + xl in shared memory, and multiplied by B = Bh + Bl with a
-// compensated dot product: the leading product xh*bh is made exact with an FMA
-// (TwoProd), accumulated with TwoSum, and the cross terms xh*bl + xl*bh plus
-// all rounding errors go into a second FP32 accumulator (the Dot2 scheme of
-// Ogita, Rump and Oishi, extended to split inputs). Phi = s + c is stored in FP64.
+// derivatives are formed in double-float arithmetic on the FP32 pipe
+// (ao_shell_values_df), stored as FP32 pairs x = xh + xl in shared memory, and
+// multiplied by B = Bh + Bl with a compensated dot product: the leading
+// product xh*bh is made exact with an FMA (TwoProd), accumulated with TwoSum,
+// and the cross terms xh*bl + xl*bh plus all rounding errors go into a second
+// FP32 accumulator (the Dot2 scheme of Ogita, Rump and Oishi, extended to split
+// inputs). Phi = s + c is stored in FP64.
 __global__ void __launch_bounds__(128) k_mo_mixed(DevProblem P, double* __restrict__ phi,
                                                   const double* __restrict__ R) {
   extern __shared__ float smf[];
+  __shared__ df32 rdf[kECm][3];
   const int K = P.n_ao, M = P.n_mo, N = P.n_elec;
   const int64_t w = blockIdx.x;
   const int e_begin = blockIdx.y * kECm;
   const int ne = min(kECm, N - e_begin);
   float* Xh = smf;                  // [(c * kECm + e) * K + mu]
   float* Xl = smf + 5 * kECm * K;
+  if (threadIdx.x < 3 * ne) {
+    const int e = threadIdx.x / 3, d = threadIdx.x - 3 * e;
+    rdf[e][d] = df_from_double(R[(w * N + e_begin + e) * 3 + d]);
+  }
+  __syncthreads();
   for (int t = threadIdx.x; t < kECm * P.n_shell; t += blockDim.x) {
     const int e = t / P.n_shell, s = t - e * P.n_shell;
     const int l = P.shell_l[s], ao0 = P.shell_ao0[s], nc = (l + 1) * (l + 2) / 2;
@@ -47,9 +54,7 @@ __global__ void __launch_bounds__(128) k_mo_mixed(DevProblem P, double* __restri
         }
       continue;
     }
-    const double* r = R + (w * N + e_begin + e) * 3;
-    ao_shell_values(P, s, r, [&](int c, int q, double v) {
-      const df32 d = df_from_double(v);
+    ao_shell_values_df(P, s, rdf[e], [&](int c, int q, df32 d) {
       Xh[(c * kECm + e) * K + ao0 + q] = d.hi;
       Xl[(c * kECm + e) * K + ao0 + q] = d.lo;
     });
@@ -109,6 +114,20 @@ __global__ void __launch_bounds__(128) k_ratio_df(DevProblem P, DevScratch S) {
   }
 }
 
+// Self-check of the double-float building blocks against FP64 on the device:
+// y_df[i] = double-float exp(x_i), y_ref[i] = CUDA's FP64 exp(x_i) (x_i <= 0),
+// and prod_df[i] = double-float product x_i * x_{i+1} for comparison with FP64.
+__global__ void k_selftest_df(int64_t n, const double* __restrict__ x, double* __restrict__ y_df,
+                              double* __restrict__ y_ref, double* __restrict__ prod_df) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const df32 a = df_from_double(x[i]);
+  y_df[i] = df_to_double(df_exp_nonpos(a));
+  y_ref[i] = exp(x[i]);
+  const df32 b = df_from_double(x[(i + 1) % n]);
+  prod_df[i] = df_to_double(a * b + a);
+}
+
 }  // namespace
 
 cudaError_t launch_mo_mixed(const DevProblem& P, const DevScratch& S, int64_t n_walk, const double* R,
@@ -120,6 +139,12 @@ cudaError_t launch_mo_mixed(const DevProblem& P, const DevScratch& S, int64_t n_
   }
   dim3 grid((unsigned)n_walk, (P.n_elec + kECm - 1) / kECm);
   k_mo_mixed<<<grid, 128, smem, st>>>(P, S.phi, R);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_selftest_df(int64_t n, const double* x, double* y_df, double* y_ref, double* prod_df,
+                               cudaStream_t st) {
+  k_selftest_df<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(n, x, y_df, y_ref, prod_df);
   return cudaGetLastError();
 }
 

@@ -24,6 +24,30 @@ pytestmark = pytest.mark.gpu
 torch = pytest.importorskip("torch")
 
 
+def test_double_float_exp_and_product():
+    """The mixed path's double-float exp (Cody-Waite reduction + Taylor series)
+    and product against CUDA's FP64 exp and FP64 arithmetic. For -50 <= t <= 0
+    the relative error is below 2e-14 plus exp's conditioning |t| times the
+    rounding of t to double-float (2^-48); below -50 the low word runs into
+    FP32's subnormal range, so the bound is absolute (4e-14 exp(-50)), far below
+    any AO value that matters next to the others of its row."""
+    from paper_1510_00730_gb300.binding import selftest_df32
+    x = -torch.cat([torch.logspace(-8, math.log10(87.0), 20000, dtype=torch.float64),
+                    torch.rand(20000, dtype=torch.float64) * 87.0, torch.zeros(1, dtype=torch.float64)]).to("cuda:0")
+    y_df, y_ref, prod = selftest_df32(x)
+    err = (y_df - y_ref).abs()
+    hi = x >= -50.0
+    bound = 2e-14 + x[hi].abs() * 2.0 ** -48
+    rel = (err[hi] / y_ref[hi].abs() / bound).max().item()
+    assert rel < 1.0, rel
+    assert err[~hi].max().item() < 4e-14 * math.exp(-50.0)
+    xn = x.cpu().numpy()
+    want = xn * np.roll(xn, -1) + xn
+    got = prod.cpu().numpy()
+    scale = np.abs(xn * np.roll(xn, -1)) + np.abs(xn) + 1e-300
+    assert np.max(np.abs(got - want) / scale) < 1e-13
+
+
 def _gpu_eval(ctx, R):
     Rt = torch.from_numpy(np.ascontiguousarray(R)).to("cuda:0")
     out = ctx.evaluate(Rt)
@@ -91,6 +115,18 @@ def test_ragged_walker_counts(n_walk, prec):
     ref = oracle.evaluate(wl)
     ctx = pkg.Context.from_workload(wl, device=0, precision=prec)
     rep = compare(_gpu_eval(ctx, wl.R), ref, **TOL[prec])
+    assert rep["ok"], rep
+
+
+@pytest.mark.parametrize("chunks", [1, 2, 3, 4])
+def test_mixed_walker_chunks(chunks):
+    """Mixed precision with the batch cut into chunks evaluated on overlapping
+    streams (ragged: 900 walkers = 3.5 tiles of 256)."""
+    wl = synth.oxygen_like_1k(n_walk=900, seed=99)
+    ref = oracle.evaluate(wl)
+    ctx = pkg.Context.from_workload(wl, device=0, precision=pkg.PRECISION_MIXED)
+    ctx.set_walker_chunks(chunks)
+    rep = compare(_gpu_eval(ctx, wl.R), ref, **TOL[pkg.PRECISION_MIXED])
     assert rep["ok"], rep
 
 
