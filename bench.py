@@ -218,8 +218,9 @@ def run_ours(args):
         out = ctx.alloc_outputs(W)
         step_ms, kern, clocks = _time_steps(ctx, Rdev, out, flush, stream, args.steps, args.warmup, dist,
                                             _gpu_index(local) if pname == primary else None)
+        n_fb = int(((out["status"] & pkg.WS_FALLBACK) != 0).sum().item())
         ms = _max_over_ranks(statistics.mean(step_ms), dist, dev)
-        results[pname] = dict(ms=ms, value=W * world / (ms / 1e3), kern=kern, clocks=clocks)
+        results[pname] = dict(ms=ms, value=W * world / (ms / 1e3), kern=kern, clocks=clocks, n_fb=n_fb)
         del out
     st = ctxs[primary].stats()
     main = results[primary]
@@ -272,10 +273,11 @@ def run_ours(args):
                     "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms},
             "gpu_launches": 6 * args.steps,
             "kernels_ms": kern,
+            "fallback_walkers": main["n_fb"],
             "roofline": roofline}
     for pname in others:
         line[pname] = {"value": results[pname]["value"], "ms_per_step": results[pname]["ms"],
-                       "kernels_ms": results[pname]["kern"]}
+                       "kernels_ms": results[pname]["kern"], "fallback_walkers": results[pname]["n_fb"]}
 
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         from tests.parity import walker_quantiles
@@ -292,6 +294,67 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
+def run_batched(args):
+    """The 64-expansion uneven workload: every expansion autotuned, then all
+    evaluations replayed as one CUDA-graph launch; value = walkers of all
+    expansions per second of graph time."""
+    import numpy as np
+    import torch
+
+    import paper_1510_00730_gb300 as pkg
+    from paper_1510_00730_gb300 import synth
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    prec = {"mixed": pkg.PRECISION_MIXED, "fp64": pkg.PRECISION_FP64}[args.precision]
+    wls = synth.batched_uneven()
+    ctxs = [pkg.Context.from_workload(wl, device=0, precision=prec) for wl in wls]
+    Rs = [torch.from_numpy(wl.R).to(dev) for wl in wls]
+    t0 = time.perf_counter()
+    tunes = [c.autotune(R, budget_ms=args.tune_ms) for c, R in zip(ctxs, Rs)]
+    tune_s = time.perf_counter() - t0
+    batch = pkg.Batch(ctxs, Rs, n_streams=args.streams)
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    for _ in range(args.warmup):
+        batch.launch()
+    torch.cuda.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    with ClockSampler(_gpu_index(0)) as clk:
+        for s in range(args.steps):
+            flush.fill_(float(s))
+            ev[s][0].record(stream)
+            batch.launch()
+            ev[s][1].record(stream)
+        torch.cuda.synchronize()
+    ms = statistics.mean(a.elapsed_time(b) for a, b in ev)
+    W = sum(wl.n_walk for wl in wls)
+    # time of each expansion alone (no batching), for the gain of sharing the GPU
+    solo = 0.0
+    for c, R in zip(ctxs, Rs):
+        out = c.alloc_outputs(R.shape[0])
+        c.evaluate(R, out=out)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        c.evaluate(R, out=out)
+        b.record(stream)
+        torch.cuda.synchronize()
+        solo += a.elapsed_time(b)
+    line = {"metric": "walker-steps/s, 64 uneven expansions in one graph launch", "value": W / (ms / 1e3),
+            "unit": UNIT, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+            "higher_is_better": True, "dtype": "f64" if prec == pkg.PRECISION_FP64 else "f64+f32x2",
+            "data": "synthetic",
+            "config": {"workload": "batched_uneven_64", "precision": args.precision, "walkers_total": W,
+                       "n_det_total": int(sum(wl.n_det for wl in wls)), "streams": args.streams,
+                       "autotune_s": tune_s, "l2": "flushed between timed steps"},
+            "sum_of_solo_ms": solo, "batch_gain": solo / ms,
+            "tuning_histogram": {k: dict(zip(*np.unique([t[k] for t in tunes], return_counts=True)))
+                                 for k in ("spmm_chunk", "mo_ec", "walker_chunks")},
+            "clocks": clk.summary(), "gpu_launches": 6 * len(wls) * args.steps}
+    line["tuning_histogram"] = {k: {str(a): int(b) for a, b in v.items()} for k, v in line["tuning_histogram"].items()}
+    print(json.dumps(line), flush=True)
+    batch.close()
+
+
 def main():
     p = argparse.ArgumentParser()
     p.add_argument("--gpus", type=int, default=1)
@@ -304,6 +367,8 @@ def main():
                    help="skip timing the other precision in the same run")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--chunks", type=int, default=None, help="walker chunks of the mixed path (default: library's)")
+    p.add_argument("--streams", type=int, default=8, help="streams of the batched workload")
+    p.add_argument("--tune-ms", type=float, default=60.0, help="autotuner budget per expansion (batched workload)")
     p.add_argument("--ref-sample", type=int, default=32)
     p.add_argument("--traffic", type=float, default=None, help="DRAM bytes per launch of the dominant kernel (ncu)")
     args = p.parse_args()
@@ -311,6 +376,8 @@ def main():
         args.warmup = 3
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == "batched_uneven_64":
+        run_batched(args)
     else:
         run_ours(args)
 

@@ -65,6 +65,9 @@ enum {
 #define MDET_WS_REF_ILLCOND 0x2u    /* reference pivot ratio below 1e-13: results may lose accuracy */
 #define MDET_WS_PSI_ZERO 0x4u       /* Psi == 0 (walker on the nodal surface): log = -inf, sign 0, ratios NaN */
 #define MDET_WS_NONFINITE 0x8u      /* an output is Inf or NaN */
+#define MDET_WS_FALLBACK 0x10u      /* the ratio-table result was estimated too inaccurate (or the
+                                       reference singular): the walker was re-evaluated by full LU
+                                       of every determinant (see mdet_set_fallback) */
 
 typedef struct {
   int32_t n_up, n_dn, n_ao, n_mo, n_int;
@@ -175,6 +178,25 @@ mdet_status mdet_get_ratios(mdet_ctx* ctx, int64_t n_walk, double* r_up, double*
                             double* log_d0, int8_t* sign_d0);
 
 /*
+ * Stability control (the paper's O(N^3) fallback of Sec. 2.2, adapted to the
+ * ratio table). The table result of a walker carries relative errors of about
+ * u cond_1(S_ref) C, with u the unit roundoff of the table arithmetic (2^-53
+ * FP64, about 2^-47 double-float), cond_1(S_ref) = |S_ref|_1 |S_ref^-1|_1 of
+ * its reference Slater matrix, and C the cancellation ratio (sum of |terms| /
+ * max(|result|, rms over the walker's electrons)) of its gradient and Laplacian
+ * sums, with the terms added in quadrature (mdet_get_error_estimates). A walker whose estimate exceeds tol (default 1e-6 for mixed, 1e-8 for
+ * FP64 precision), or whose reference is singular, is re-evaluated on the GPU
+ * in FP64 by LU of every distinct determinant, its own contraction and
+ * epilogue; its status gets MDET_WS_FALLBACK. At most max_walkers walkers per
+ * evaluation are re-evaluated (default 64; the scratch grows with it);
+ * further ones keep the table result and MDET_WS_REF_ILLCOND. tol <= 0
+ * disables the fallback. Supported for n_up, n_dn <= MDET_FALLBACK_MAX_SPIN.
+ */
+#define MDET_FALLBACK_MAX_SPIN 17
+mdet_status mdet_set_fallback(mdet_ctx* ctx, double tol, int max_walkers);
+
+/*
+ * Walker chunking of the mixed-precision evaluation/*
  * Walker chunking of the mixed-precision evaluation: a batch is cut into
  * n_chunks chunks (multiples of 256 walkers) evaluated on the context's own
  * streams, forked from and joined back to the caller's stream, so the FP32-pipe
@@ -186,6 +208,66 @@ mdet_status mdet_get_ratios(mdet_ctx* ctx, int64_t n_walk, double* r_up, double*
 mdet_status mdet_set_walker_chunks(mdet_ctx* ctx, int n_chunks);
 
 /*
+ * Tile shapes of the evaluation kernels (SURVEY-level tuning knobs, no paper
+ * counterpart): spmm_chunk nonzeros of C per warp in the contraction (64..8192),
+ * mo_ec electrons per thread block in the orbital kernels (4, 6 or 8),
+ * walker_chunks as in mdet_set_walker_chunks. best_ms and trials are filled by
+ * mdet_autotune (the fastest step time seen and the configurations timed).
+ */
+typedef struct {
+  int32_t spmm_chunk;
+  int32_t mo_ec;
+  int32_t walker_chunks;
+  float best_ms;
+  int32_t trials;
+} mdet_tuning;
+
+mdet_status mdet_get_tuning(const mdet_ctx* ctx, mdet_tuning* out);
+mdet_status mdet_set_tuning(mdet_ctx* ctx, const mdet_tuning* in);
+
+/*
+ * Autotuner: times full evaluations of the n_walk walkers at R (device
+ * pointer, [n_walk][n_up+n_dn][3]) with CUDA events on the context's stream and
+ * picks the tile shapes by coordinate descent over spmm_chunk in
+ * {256, 512, 1024, 2048}, mo_ec in {4, 6, 8} and (mixed precision)
+ * walker_chunks in {1, 2, 4}, stopping when budget_ms of GPU time is spent.
+ * The winner is stored in the context and returned in *out (may be null).
+ * Allocates temporary output buffers; synchronous.
+ */
+mdet_status mdet_autotune(mdet_ctx* ctx, int64_t n_walk, const double* R, double budget_ms, mdet_tuning* out);
+
+/*
+ * Batched evaluation of several independent expansions (contexts) on one
+ * device, e.g. wavefunctions of different systems or states, of uneven sizes.
+ * Per context i: n_walk[i] walkers at R[i] and output pointers as in
+ * mdet_evaluate (e_local[i] / status[i] may be null; the arrays e_local and
+ * status themselves may be null). Contexts are spread over n_streams streams
+ * (1..16) by longest-processing-time-first on a cost estimate, so small and
+ * large expansions share the GPU.
+ *
+ * mdet_batch_evaluate launches directly, forked from and joined to `stream`.
+ * mdet_batch_create records the same launches once into a CUDA graph (after
+ * one uncaptured warm-up evaluation that sizes every context's scratch), and
+ * mdet_batch_launch replays all evaluations as one graph launch on `stream`.
+ * The pointers given to mdet_batch_create are baked into the graph: refill the
+ * same R buffers between launches. A batch must be destroyed before its
+ * contexts, and a context's tuning or size must not change while a batch
+ * refers to it.
+ */
+typedef struct mdet_batch mdet_batch;
+mdet_status mdet_batch_evaluate(int n_ctx, mdet_ctx* const* ctxs, const int64_t* n_walk, const double* const* R,
+                                double* const* log_abs_psi, int8_t* const* sign, double* const* grad,
+                                double* const* lap, double* const* e_local, uint32_t* const* status,
+                                int n_streams, void* stream);
+mdet_status mdet_batch_create(mdet_batch** out, int n_ctx, mdet_ctx* const* ctxs, const int64_t* n_walk,
+                              const double* const* R, double* const* log_abs_psi, int8_t* const* sign,
+                              double* const* grad, double* const* lap, double* const* e_local,
+                              uint32_t* const* status, int n_streams);
+mdet_status mdet_batch_launch(mdet_batch* b, void* stream);
+void mdet_batch_destroy(mdet_batch* b);
+
+/*
+ * Stage timing./*
  * Stage timing./*
  * Stage timing. With profiling on, every mdet_evaluate records CUDA events on
  * its stream around each stage; mdet_get_profile waits for the last one and
@@ -240,6 +322,17 @@ mdet_status mdet_psi_tilde_noalloc(mdet_ctx* ctx, int64_t n_walk, const double* 
  */
 mdet_status mdet_selftest_df32(int device, int64_t n, const double* x, double* y_df, double* y_ref,
                                double* prod_df);
+
+/*
+ * Diagnostics of the last evaluation (host copies, synchronises its stream):
+ * cond1 [n_walk][2], cond_1 of the reference Slater matrix of each spin;
+ * est [n_walk][2], the first-order error estimates of the walker's table
+ * result: u cond_1 times the cancellation ratio of its derivative sums with
+ * the terms summed in magnitude (est[w][0], a worst case) and in quadrature
+ * (est[w][1], the one mdet_set_fallback compares with its tolerance). Either
+ * pointer may be null. Meaningful when the fallback is enabled.
+ */
+mdet_status mdet_get_error_estimates(mdet_ctx* ctx, int64_t n_walk, double* cond1, double* est);
 
 /* Sizes and excitation statistics (host only; works without a device). *//* Sizes and excitation statistics (host only; works without a device). */
 mdet_status mdet_get_stats(const mdet_ctx* ctx, mdet_stats* out);

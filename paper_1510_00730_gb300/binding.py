@@ -20,6 +20,7 @@ WS_REF_SINGULAR = 0x1
 WS_REF_ILLCOND = 0x2
 WS_PSI_ZERO = 0x4
 WS_NONFINITE = 0x8
+WS_FALLBACK = 0x10
 MAX_EXC = 4
 
 _lib = None
@@ -29,6 +30,11 @@ class MdetError(RuntimeError):
     def __init__(self, status, msg):
         super().__init__(msg)
         self.status = status
+
+
+class _Tuning(C.Structure):
+    _fields_ = [("spmm_chunk", C.c_int32), ("mo_ec", C.c_int32), ("walker_chunks", C.c_int32),
+                ("best_ms", C.c_float), ("trials", C.c_int32)]
 
 
 class _Stats(C.Structure):
@@ -73,12 +79,25 @@ def load_library(build_if_missing: bool = True):
     L.mdet_psi_tilde_noalloc.argtypes = [vp, i64, vp, i64, vp, vp]
     L.mdet_set_profiling.argtypes = [vp, i32]
     L.mdet_set_walker_chunks.argtypes = [vp, i32]
+    L.mdet_set_fallback.argtypes = [vp, C.c_double, i32]
+    L.mdet_get_error_estimates.argtypes = [vp, i64, vp, vp]
     L.mdet_selftest_df32.argtypes = [i32, i64, vp, vp, vp, vp]
+    L.mdet_get_tuning.argtypes = [vp, C.POINTER(_Tuning)]
+    L.mdet_set_tuning.argtypes = [vp, C.POINTER(_Tuning)]
+    L.mdet_autotune.argtypes = [vp, i64, vp, C.c_double, C.POINTER(_Tuning)]
+    pp = C.POINTER(C.c_void_p)
+    L.mdet_batch_evaluate.argtypes = [i32, pp, C.POINTER(C.c_int64), pp, pp, pp, pp, pp, pp, pp, i32, vp]
+    L.mdet_batch_create.argtypes = [C.POINTER(vp), i32, pp, C.POINTER(C.c_int64), pp, pp, pp, pp, pp, pp, pp, i32]
+    L.mdet_batch_launch.argtypes = [vp, vp]
+    L.mdet_batch_destroy.argtypes = [vp]
+    L.mdet_batch_destroy.restype = None
     L.mdet_get_profile.argtypes = [vp, vp]
     for name in ("mdet_create", "mdet_set_system", "mdet_set_orbitals", "mdet_set_ci_expansion", "mdet_evaluate",
                  "mdet_evaluate_host", "mdet_get_ratios", "mdet_get_stats", "mdet_get_spin_dets",
                  "mdet_get_ci_matrix", "mdet_omega_sort", "mdet_set_profiling", "mdet_get_profile",
-                 "mdet_psi_tilde_noalloc", "mdet_set_walker_chunks", "mdet_selftest_df32"):
+                 "mdet_psi_tilde_noalloc", "mdet_set_walker_chunks", "mdet_selftest_df32", "mdet_get_tuning",
+                 "mdet_set_tuning", "mdet_autotune", "mdet_batch_evaluate", "mdet_batch_create", "mdet_batch_launch", "mdet_set_fallback",
+                 "mdet_get_error_estimates"):
         getattr(L, name).restype = i32
     _lib = L
     return L
@@ -248,6 +267,35 @@ class Context:
 
     STAGES = ("orbitals", "reference", "ratios", "zero", "contract", "final")
 
+    def tuning(self):
+        t = _Tuning()
+        self._check(self._L.mdet_get_tuning(self._h, C.byref(t)), "mdet_get_tuning")
+        return dict(spmm_chunk=t.spmm_chunk, mo_ec=t.mo_ec, walker_chunks=t.walker_chunks, best_ms=t.best_ms,
+                    trials=t.trials)
+
+    def set_tuning(self, spmm_chunk=512, mo_ec=6, walker_chunks=0):
+        t = _Tuning(spmm_chunk, mo_ec, walker_chunks, 0.0, 0)
+        self._check(self._L.mdet_set_tuning(self._h, C.byref(t)), "mdet_set_tuning")
+
+    def autotune(self, R, budget_ms=200.0):
+        """Pick tile shapes by timing evaluations of the walkers R (CUDA float64)."""
+        t = _Tuning()
+        self._check(self._L.mdet_autotune(self._h, R.shape[0], R.data_ptr(), float(budget_ms), C.byref(t)),
+                    "mdet_autotune")
+        return dict(spmm_chunk=t.spmm_chunk, mo_ec=t.mo_ec, walker_chunks=t.walker_chunks, best_ms=t.best_ms,
+                    trials=t.trials)
+
+    def set_fallback(self, tol, max_walkers=64):
+        """Re-evaluate walkers whose estimated table error exceeds tol by full LU (tol <= 0: off)."""
+        self._check(self._L.mdet_set_fallback(self._h, float(tol), int(max_walkers)), "mdet_set_fallback")
+
+    def error_estimates(self, n_walk):
+        """cond_1 of the references [n_walk, 2] and the table error estimates [n_walk, 2] of the last evaluation."""
+        c1 = np.empty((n_walk, 2))
+        est = np.empty((n_walk, 2))
+        self._check(self._L.mdet_get_error_estimates(self._h, n_walk, _ptr(c1), _ptr(est)), "mdet_get_error_estimates")
+        return c1, est
+
     def set_walker_chunks(self, n_chunks):
         """Mixed precision: evaluate a batch in n_chunks overlapping chunks (0 = default, 1 = none)."""
         self._check(self._L.mdet_set_walker_chunks(self._h, int(n_chunks)), "mdet_set_walker_chunks")
@@ -287,3 +335,71 @@ class Context:
         val = np.empty(n)
         self._check(self._L.mdet_get_ci_matrix(self._h, _ptr(row), _ptr(col), _ptr(val)), "mdet_get_ci_matrix")
         return row, col, val
+
+
+def _ptr_array(vals):
+    arr = (C.c_void_p * len(vals))()
+    for i, v in enumerate(vals):
+        arr[i] = v
+    return arr
+
+
+def _batch_args(ctxs, Rs, outs):
+    n = len(ctxs)
+    nw = (C.c_int64 * n)(*[int(R.shape[0]) for R in Rs])
+    keys = ("log_abs_psi", "sign", "grad", "lap", "e_local", "status")
+    cols = [_ptr_array([o[k].data_ptr() for o in outs]) for k in keys]
+    return n, _ptr_array([c._h.value for c in ctxs]), nw, _ptr_array([R.data_ptr() for R in Rs]), cols
+
+
+def batch_evaluate(ctxs, Rs, outs=None, n_streams=4, stream=None):
+    """Evaluate several contexts (same device) on concurrent streams."""
+    import torch
+    if outs is None:
+        outs = [c.alloc_outputs(R.shape[0]) for c, R in zip(ctxs, Rs)]
+    if stream is None:
+        stream = torch.cuda.current_stream(Rs[0].device)
+    n, hs, nw, rp, cols = _batch_args(ctxs, Rs, outs)
+    L = load_library()
+    st = L.mdet_batch_evaluate(n, hs, nw, rp, *cols, int(n_streams), stream.cuda_stream)
+    if st:
+        raise MdetError(st, "mdet_batch_evaluate failed: %s" % L.mdet_status_string(st).decode())
+    return outs
+
+
+class Batch:
+    """All evaluations of a list of contexts recorded once as a CUDA graph and
+    replayed with one launch. The R tensors and outputs are baked in: refill R
+    in place between launches."""
+
+    def __init__(self, ctxs, Rs, outs=None, n_streams=4):
+        if outs is None:
+            outs = [c.alloc_outputs(R.shape[0]) for c, R in zip(ctxs, Rs)]
+        self.ctxs, self.Rs, self.outs = list(ctxs), list(Rs), outs
+        self._L = load_library()
+        n, hs, nw, rp, cols = _batch_args(ctxs, Rs, outs)
+        h = C.c_void_p()
+        st = self._L.mdet_batch_create(C.byref(h), n, hs, nw, rp, *cols, int(n_streams))
+        if st:
+            raise MdetError(st, "mdet_batch_create failed: %s" % self._L.mdet_status_string(st).decode())
+        self._h = h
+
+    def launch(self, stream=None):
+        import torch
+        if stream is None:
+            stream = torch.cuda.current_stream(self.Rs[0].device)
+        st = self._L.mdet_batch_launch(self._h, stream.cuda_stream)
+        if st:
+            raise MdetError(st, "mdet_batch_launch failed")
+        return self.outs
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            self._L.mdet_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

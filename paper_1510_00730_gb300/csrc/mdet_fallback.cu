@@ -1,0 +1,309 @@
+// Stability fallback: walkers whose reference Slater matrix is too
+// ill-conditioned for the reference-relative ratio table are re-evaluated by
+// the plain cubic method (LU of every distinct determinant, the paper's
+// "no Sherman-Morrison" mode of Table 2, and its O(N^3) fallback of Sec. 2.2),
+// in FP64, followed by their own contraction and epilogue (Eqs. 2, 5-8).
+//
+//   k_fb_list    compacts the flagged walkers into a device list (no host sync)
+//   k_fb_dets    one thread per (determinant, flagged walker): in-place
+//                Gauss-Jordan inversion with partial pivoting of the Slater
+//                matrix, log|D|, sign and (d_{i mu} D)/D = sum_a d_mu phi_{o_a}(r_i) (S^-1)_{a i}
+//   k_fb_scale   per flagged walker: common scale of its determinant values
+//   k_fb_rows    (rows, walker) blocks: v = C d_dn, u = C^T d_up, Psi, gradient
+//                and Laplacian sums, reduced per block then with atomics
+//   k_fb_out     per flagged walker: potential energy and outputs
+#include <cfloat>
+#include <cmath>
+
+#include "mdet_internal.h"
+
+namespace mdet {
+
+namespace {
+
+constexpr int kFbMax = MDET_FALLBACK_MAX_SPIN;
+
+__global__ void k_fb_list(const DevProblem P, uint32_t* __restrict__ wstat, uint32_t* __restrict__ status,
+                          int64_t n_walk, int* __restrict__ list) {
+  const int64_t w = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (w >= n_walk) return;
+  const uint32_t st = wstat[w];
+  if (!(st & MDET_WS_FALLBACK)) return;
+  const int i = atomicAdd(list, 1);
+  if (i < P.fallback_cap) {
+    list[1 + i] = (int)w;
+  } else {  // beyond the fallback capacity: keep the table result, flagged
+    const uint32_t s2 = (st & ~MDET_WS_FALLBACK) | MDET_WS_REF_ILLCOND;
+    wstat[w] = s2;
+    if (status) status[w] = s2;
+  }
+}
+
+__global__ void __launch_bounds__(64) k_fb_dets(DevProblem P, DevScratch S) {
+  const int slot = blockIdx.y;
+  const int count = min(S.fb_list[0], P.fallback_cap);
+  if (slot >= count) return;
+  const int64_t w = S.fb_list[1 + slot];
+  extern __shared__ double fsm[];
+  const int nu = P.n_up, nd = P.n_dn, N = nu + nd, M = P.n_mo, nmax = max(nu, nd);
+  const int nu_det = P.n_det_sp[0], ntot = nu_det + P.n_det_sp[1];
+  const int stride = 2 + 4 * nmax;
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= ntot) return;
+  const int sp = t < nu_det ? 0 : 1;
+  const int n = sp ? nd : nu, e0 = sp ? nu : 0;
+  const Exc e = P.exc[sp][sp ? t - nu_det : t];
+  int cols[kFbMax];
+  const int* occ = P.ref_occ + sp * kMaxSpin;
+  for (int a = 0; a < n; a++) cols[a] = occ[a];
+  for (int q = 0; q < e.k; q++) cols[e.h[q]] = e.p[q];
+  double* A = fsm + threadIdx.x * nmax * nmax;  // n x n, row-major, stride n
+  const double* ph = S.phi + (size_t)w * 5 * N * M;
+  for (int i = 0; i < n; i++)
+    for (int a = 0; a < n; a++) A[i * n + a] = ph[(size_t)(e0 + i) * M + cols[a]];
+  int piv[kFbMax];
+  double logabs = 0.0, sgn = e.eps < 0 ? -1.0 : 1.0;
+  bool singular = false;
+  for (int k = 0; k < n; k++) {
+    int p = k;
+    double best = fabs(A[k * n + k]);
+    for (int i = k + 1; i < n; i++)
+      if (fabs(A[i * n + k]) > best) {
+        best = fabs(A[i * n + k]);
+        p = i;
+      }
+    piv[k] = p;
+    if (!(best > 0.0)) {
+      singular = true;
+      break;
+    }
+    if (p != k) {
+      sgn = -sgn;
+      for (int j = 0; j < n; j++) {
+        const double tmp = A[k * n + j];
+        A[k * n + j] = A[p * n + j];
+        A[p * n + j] = tmp;
+      }
+    }
+    const double d = A[k * n + k];
+    logabs += log(fabs(d));
+    if (d < 0) sgn = -sgn;
+    const double inv = 1.0 / d;
+    A[k * n + k] = 1.0;
+    for (int j = 0; j < n; j++) A[k * n + j] *= inv;
+    for (int i = 0; i < n; i++) {
+      if (i == k) continue;
+      const double f = A[i * n + k];
+      A[i * n + k] = 0.0;
+      if (f != 0.0)
+        for (int j = 0; j < n; j++) A[i * n + j] = fma(-f, A[k * n + j], A[i * n + j]);
+    }
+  }
+  double* rec = S.fb + ((size_t)slot * ntot + t) * stride;
+  if (singular) {
+    rec[0] = -INFINITY;
+    rec[1] = 0.0;
+    for (int q = 0; q < 4 * n; q++) rec[2 + q] = 0.0;
+    return;
+  }
+  // (P S)^-1 = S^-1 P^-1: undo the row interchanges on the columns, last first
+  for (int k = n - 1; k >= 0; k--)
+    if (piv[k] != k)
+      for (int i = 0; i < n; i++) {
+        const double tmp = A[i * n + k];
+        A[i * n + k] = A[i * n + piv[k]];
+        A[i * n + piv[k]] = tmp;
+      }
+  rec[0] = logabs;
+  rec[1] = sgn;
+  for (int i = 0; i < n; i++)
+    for (int mu = 0; mu < 4; mu++) {
+      const double* dph = ph + ((size_t)(1 + mu) * N + e0 + i) * M;
+      double acc = 0.0;
+      for (int a = 0; a < n; a++) acc = fma(dph[cols[a]], A[a * n + i], acc);
+      rec[2 + i * 4 + mu] = acc;
+    }
+}
+
+__device__ __forceinline__ double block_max(double v, double* red) {
+#pragma unroll
+  for (int off = 16; off; off >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, off));
+  __syncthreads();
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+  __syncthreads();
+  double r = -INFINITY;
+  for (int q = 0; q < (int)(blockDim.x >> 5); q++) r = fmax(r, red[q]);
+  return r;
+}
+
+// Per flagged walker: common scale per spin (the largest log|D| of its nonzero
+// determinants), scaled values d = sign exp(log|D| - L) in place and in a
+// contiguous copy for the gathers, and cleared accumulators.
+// acc layout per slot: [0] L_up, [1] L_dn, [2] Psi, [3..3+4N) G[i][mu].
+__global__ void __launch_bounds__(256) k_fb_scale(DevProblem P, DevScratch S) {
+  const int slot = blockIdx.x;
+  const int count = min(S.fb_list[0], P.fallback_cap);
+  if (slot >= count) return;
+  const int nu = P.n_up, nd = P.n_dn, N = nu + nd, nmax = max(nu, nd);
+  const int nu_det = P.n_det_sp[0], ntot = nu_det + P.n_det_sp[1];
+  const int stride = 2 + 4 * nmax;
+  double* rec = S.fb + (size_t)slot * ntot * stride;
+  double* dv = S.fb + (size_t)P.fallback_cap * ntot * stride + (size_t)slot * ntot;
+  double* acc = S.fb_acc + (size_t)slot * (3 + 4 * 2 * kFbMax);
+  __shared__ double red[8];
+  double lu = -INFINITY, ld = -INFINITY;
+  for (int t = threadIdx.x; t < ntot; t += blockDim.x)
+    if (rec[(size_t)t * stride + 1] != 0.0) {
+      if (t < nu_det) lu = fmax(lu, rec[(size_t)t * stride]);
+      else ld = fmax(ld, rec[(size_t)t * stride]);
+    }
+  double Lu = block_max(lu, red);
+  double Ld = block_max(ld, red);
+  if (!(Lu > -INFINITY)) Lu = 0.0;
+  if (!(Ld > -INFINITY)) Ld = 0.0;
+  for (int t = threadIdx.x; t < ntot; t += blockDim.x) {
+    double* r = rec + (size_t)t * stride;
+    r[0] = r[1] == 0.0 ? 0.0 : r[1] * exp(r[0] - (t < nu_det ? Lu : Ld));
+    dv[t] = r[0];
+  }
+  for (int q = threadIdx.x; q < 1 + 4 * N; q += blockDim.x) acc[2 + q] = 0.0;
+  if (threadIdx.x == 0) {
+    acc[0] = Lu;
+    acc[1] = Ld;
+  }
+}
+
+// grid (ceil(ntot / 256), count slots): one thread per up row (v = C d_dn,
+// Psi and the up-electron sums) or down column (u = C^T d_up, the
+// down-electron sums); block sums in shared memory, then one atomic per value.
+__global__ void __launch_bounds__(256) k_fb_rows(DevProblem P, DevScratch S) {
+  const int slot = blockIdx.y;
+  const int count = min(S.fb_list[0], P.fallback_cap);
+  if (slot >= count) return;
+  const int nu = P.n_up, nd = P.n_dn, N = nu + nd, nmax = max(nu, nd);
+  const int nu_det = P.n_det_sp[0], ntot = nu_det + P.n_det_sp[1];
+  const int stride = 2 + 4 * nmax;
+  const double* rec = S.fb + (size_t)slot * ntot * stride;
+  const double* dv = S.fb + (size_t)P.fallback_cap * ntot * stride + (size_t)slot * ntot;
+  double* acc = S.fb_acc + (size_t)slot * (3 + 4 * 2 * kFbMax);
+  __shared__ double G[1 + 4 * 2 * kFbMax];  // Psi, then G
+  for (int q = threadIdx.x; q < 1 + 4 * N; q += blockDim.x) G[q] = 0.0;
+  __syncthreads();
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t < nu_det) {
+    double v = 0.0;
+    for (int k = P.csr_ptr[t]; k < P.csr_ptr[t + 1]; k++) v = fma(P.csr_val[k], dv[nu_det + P.csr_col[k]], v);
+    const double* r = rec + (size_t)t * stride;
+    const double vd = v * r[0];
+    if (vd != 0.0) {
+      atomicAdd(&G[0], vd);
+      for (int q = 0; q < 4 * nu; q++) atomicAdd(&G[1 + q], vd * r[2 + q]);
+    }
+  } else if (t < ntot) {
+    const int J = t - nu_det;
+    double u = 0.0;
+    for (int k = P.csc_ptr[J]; k < P.csc_ptr[J + 1]; k++) u = fma(P.csc_val[k], dv[P.csc_row[k]], u);
+    const double* r = rec + (size_t)t * stride;
+    const double ud = u * r[0];
+    if (ud != 0.0)
+      for (int q = 0; q < 4 * nd; q++) atomicAdd(&G[1 + 4 * nu + q], ud * r[2 + q]);
+  }
+  __syncthreads();
+  for (int q = threadIdx.x; q < 1 + 4 * N; q += blockDim.x)
+    if (G[q] != 0.0) atomicAdd(&acc[2 + q], G[q]);
+}
+
+// Per flagged walker: potential energy and the outputs.
+__global__ void __launch_bounds__(64) k_fb_out(DevProblem P, DevScratch S, const double* __restrict__ R,
+                                               double* __restrict__ log_abs_psi, int8_t* __restrict__ sign,
+                                               double* __restrict__ grad, double* __restrict__ lap,
+                                               double* __restrict__ e_local, uint32_t* __restrict__ status) {
+  const int slot = blockIdx.x;
+  const int count = min(S.fb_list[0], P.fallback_cap);
+  if (slot >= count) return;
+  const int64_t w = S.fb_list[1 + slot];
+  const int nu = P.n_up, nd = P.n_dn, N = nu + nd;
+  const double* acc = S.fb_acc + (size_t)slot * (3 + 4 * 2 * kFbMax);
+  const double* G = acc + 3;
+  __shared__ double red[2];
+  double vp = 0.0;
+  const double* rr = R + w * N * 3;
+  for (int q = threadIdx.x; q < N * P.n_nuc; q += blockDim.x) {
+    const int i = q / P.n_nuc, A = q - i * P.n_nuc;
+    const double dx = rr[3 * i] - P.nuc_xyz[3 * A], dy = rr[3 * i + 1] - P.nuc_xyz[3 * A + 1],
+                 dz = rr[3 * i + 2] - P.nuc_xyz[3 * A + 2];
+    vp -= P.Z[A] / sqrt(dx * dx + dy * dy + dz * dz);
+  }
+  for (int q = threadIdx.x; q < N * N; q += blockDim.x) {
+    const int i = q / N, j = q - i * N;
+    if (j <= i) continue;
+    const double dx = rr[3 * i] - rr[3 * j], dy = rr[3 * i + 1] - rr[3 * j + 1], dz = rr[3 * i + 2] - rr[3 * j + 2];
+    vp += 1.0 / sqrt(dx * dx + dy * dy + dz * dz);
+  }
+  if (threadIdx.x == 0)
+    for (int A = 0; A < P.n_nuc; A++)
+      for (int B = A + 1; B < P.n_nuc; B++) {
+        const double dx = P.nuc_xyz[3 * A] - P.nuc_xyz[3 * B], dy = P.nuc_xyz[3 * A + 1] - P.nuc_xyz[3 * B + 1],
+                     dz = P.nuc_xyz[3 * A + 2] - P.nuc_xyz[3 * B + 2];
+        vp += P.Z[A] * P.Z[B] / sqrt(dx * dx + dy * dy + dz * dz);
+      }
+#pragma unroll
+  for (int off = 16; off; off >>= 1) vp += __shfl_xor_sync(0xffffffffu, vp, off);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = vp;
+  __syncthreads();
+  const double Ps = acc[2];
+  const double inv = 1.0 / Ps;
+  for (int i = threadIdx.x; i < N; i += blockDim.x) {
+    grad[(w * N + i) * 3 + 0] = G[4 * i + 0] * inv;
+    grad[(w * N + i) * 3 + 1] = G[4 * i + 1] * inv;
+    grad[(w * N + i) * 3 + 2] = G[4 * i + 2] * inv;
+    lap[w * N + i] = G[4 * i + 3] * inv;
+  }
+  if (threadIdx.x == 0) {
+    double tl = 0.0;
+    for (int i = 0; i < N; i++) tl += G[4 * i + 3];
+    const double el = -0.5 * tl * inv + red[0] + red[1];
+    const double lg = log(fabs(Ps)) + acc[0] + acc[1];
+    log_abs_psi[w] = lg;
+    sign[w] = (int8_t)((Ps > 0.0) - (Ps < 0.0));
+    if (e_local) e_local[w] = el;
+    uint32_t st = (S.wstat[w] & (MDET_WS_REF_SINGULAR | MDET_WS_REF_ILLCOND)) | MDET_WS_FALLBACK;
+    if (Ps == 0.0) st |= MDET_WS_PSI_ZERO;
+    if (!isfinite(lg) || !isfinite(el)) st |= MDET_WS_NONFINITE;
+    S.wstat[w] = st;
+    if (status) status[w] = st;
+  }
+}
+
+}  // namespace
+
+cudaError_t launch_fallback(const DevProblem& P, const DevScratch& S, int64_t n_walk, const double* R,
+                            double* log_abs_psi, int8_t* sign, double* grad, double* lap, double* e_local,
+                            uint32_t* status, cudaStream_t st) {
+  if (!(P.fallback_tol > 0.0) || !S.fb || P.n_up > kFbMax) return cudaSuccess;
+  cudaError_t e = cudaMemsetAsync(S.fb_list, 0, sizeof(int), st);
+  if (e != cudaSuccess) return e;
+  k_fb_list<<<(unsigned)((n_walk + 255) / 256), 256, 0, st>>>(P, S.wstat, status, n_walk, S.fb_list);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  const int nmax = P.n_up > P.n_dn ? P.n_up : P.n_dn;
+  const int ntot = P.n_det_sp[0] + P.n_det_sp[1];
+  const size_t smem = sizeof(double) * 64 * nmax * nmax;
+  static size_t attr_bytes = 0;
+  if (smem > attr_bytes) {
+    if ((e = cudaFuncSetAttribute(k_fb_dets, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess)
+      return e;
+    attr_bytes = smem;
+  }
+  dim3 g1((ntot + 63) / 64, P.fallback_cap);
+  k_fb_dets<<<g1, 64, smem, st>>>(P, S);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  k_fb_scale<<<P.fallback_cap, 256, 0, st>>>(P, S);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  dim3 g2((ntot + 255) / 256, P.fallback_cap);
+  k_fb_rows<<<g2, 256, 0, st>>>(P, S);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  k_fb_out<<<P.fallback_cap, 64, 0, st>>>(P, S, R, log_abs_psi, sign, grad, lap, e_local, status);
+  return cudaGetLastError();
+}
+
+}  // namespace mdet

@@ -47,6 +47,12 @@ struct mdet_ctx {
   // stages of one chunk overlap the FP64 contraction of another
   static constexpr int kMaxChunks = 4;
   int n_chunks_cfg = 0;  // 0: automatic
+  double fallback_tol = 0.0;  // set from the precision in mdet_create
+  int fallback_cap = 64;
+  std::vector<int32_t> csr_ptr, csc_ptr;
+  int spmm_chunk = 512;  // tile shapes (mdet_set_tuning / mdet_autotune)
+  int mo_ec = 6;
+  mdet_tuning last_tune{};
   cudaStream_t cs[kMaxChunks] = {};
   cudaEvent_t fork = nullptr, joined[kMaxChunks] = {}, contracted[kMaxChunks] = {};
   // stage timing
@@ -191,8 +197,8 @@ void free_problem(mdet_ctx* c) {
 
 void free_scratch(mdet_ctx* c) {
   DevScratch& S = c->S;
-  void* ptrs[] = {S.phi, S.Ainv, S.ld0, S.sg0, S.g, S.T, S.Tdf, S.r, S.vu, S.psit, S.wstat,
-                  S.R_stage, S.out_stage};
+  void* ptrs[] = {S.phi, S.Ainv, S.ld0, S.sg0, S.g, S.kap, S.est, S.T, S.Tdf, S.r, S.vu, S.psit, S.wstat,
+                  S.fb, S.fb_list, S.fb_acc, S.R_stage, S.out_stage};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   S = DevScratch{};
@@ -209,6 +215,10 @@ mdet_status upload_problem(mdet_ctx* c) {
   P.n_det_sp[0] = (int)c->exc[0].size();
   P.n_det_sp[1] = (int)c->exc[1].size();
   P.nnz = c->n_det;
+  P.spmm_chunk = c->spmm_chunk;
+  P.mo_ec = c->mo_ec;
+  P.fallback_tol = c->fallback_tol;
+  P.fallback_cap = c->fallback_cap;
   mdet_status s;
 #define UP(vec, dst) if ((s = upload(c, vec, &dst)) != MDET_OK) return s
   UP(c->Z, P.Z);
@@ -256,6 +266,8 @@ mdet_status upload_problem(mdet_ctx* c) {
   UP(c->coo_col, P.csc_col);
   UP(c->coo_row, P.csc_row);
   UP(c->coo_val, P.csc_val);
+  UP(c->csr_ptr, P.csr_ptr);
+  UP(c->csc_ptr, P.csc_ptr);
 #undef UP
   free_scratch(c);  // sizes depend on the problem
   return MDET_OK;
@@ -287,6 +299,8 @@ mdet_status ensure_scratch(mdet_ctx* c, int64_t n_walk) {
   if ((s = dalloc(c, &S.ld0, (size_t)W * 2))) return s;
   if ((s = dalloc(c, &S.sg0, (size_t)W * 2))) return s;
   if ((s = dalloc(c, &S.g, (size_t)W * N * 4))) return s;
+  if ((s = dalloc(c, &S.kap, (size_t)W * 2))) return s;
+  if ((s = dalloc(c, &S.est, (size_t)W * 2))) return s;
   if ((s = dalloc(c, &S.T, (size_t)N * M * wp))) return s;
   if (c->precision == MDET_PRECISION_MIXED) {
     if ((s = dalloc(c, &S.Tdf, (size_t)N * M * wp))) return s;
@@ -296,6 +310,12 @@ mdet_status ensure_scratch(mdet_ctx* c, int64_t n_walk) {
   if ((s = dalloc(c, &S.vu, (size_t)ndt * wp))) return s;  // walker-major [wp][ndt]
   if ((s = dalloc(c, &S.psit, (size_t)wp))) return s;
   if ((s = dalloc(c, &S.wstat, (size_t)W))) return s;
+  if (P.fallback_tol > 0.0 && P.n_up <= MDET_FALLBACK_MAX_SPIN) {
+    const int64_t nmax = std::max(P.n_up, P.n_dn);
+    if ((s = dalloc(c, &S.fb, (size_t)P.fallback_cap * ndt * (3 + 4 * nmax)))) return s;
+    if ((s = dalloc(c, &S.fb_list, (size_t)P.fallback_cap + 1))) return s;
+    if ((s = dalloc(c, &S.fb_acc, (size_t)P.fallback_cap * (3 + 8 * MDET_FALLBACK_MAX_SPIN)))) return s;
+  }
   // padded walker columns of the tables must hold finite values
   CUDA_TRY(c, cudaMemset(S.T, 0, sizeof(double) * N * M * wp));
   S.cap_walk = W;
@@ -340,6 +360,7 @@ mdet_status mdet_create(mdet_ctx** out, int device, int precision) {
   if (!c) return MDET_E_OOM;
   c->device = device;
   c->precision = precision;
+  c->fallback_tol = precision == MDET_PRECISION_MIXED ? 1e-5 : 1e-6;
   if (device >= 0) {
     int n = 0;
     if (cudaGetDeviceCount(&n) != cudaSuccess || device >= n) {
@@ -582,6 +603,14 @@ mdet_status mdet_set_ci_expansion(mdet_ctx* c, int64_t n_det, int n_int, const u
     c->csr_col[q] = idx_of[1][ord[q]];
     c->csr_val[q] = coef[ord[q]];
   }
+  c->csr_ptr.assign(nup + 1, 0);
+  c->csc_ptr.assign(ndn + 1, 0);
+  for (int64_t q = 0; q < n_det; q++) {
+    c->csr_ptr[c->csr_row[q] + 1]++;
+    c->csc_ptr[c->coo_col[q] + 1]++;
+  }
+  for (int64_t i = 0; i < nup; i++) c->csr_ptr[i + 1] += c->csr_ptr[i];
+  for (int64_t j = 0; j < ndn; j++) c->csc_ptr[j + 1] += c->csc_ptr[j];
   c->n_det = n_det;
   c->n_int = n_int;
   mdet_status s = upload_problem(c);
@@ -655,6 +684,8 @@ mdet_status mdet_evaluate(mdet_ctx* c, int64_t n_walk, const double* R, double* 
     }
   }
   c->prof_chunks = nch;
+  // stability fallback over the whole batch, after every chunk has finished
+  CUDA_TRY(c, launch_fallback(P, c->S, n_walk, R, log_abs_psi, sign, grad, lap, e_local, status, st));
   c->have_profile = prof;
   c->last_stream = st;
   c->last_walk = n_walk;
@@ -731,6 +762,17 @@ mdet_status mdet_get_ratios(mdet_ctx* c, int64_t n_walk, double* r_up, double* r
   return MDET_OK;
 }
 
+mdet_status mdet_set_fallback(mdet_ctx* c, double tol, int max_walkers) {
+  if (!c || max_walkers < 1 || max_walkers > 65535) return MDET_E_ARG;
+  const bool resize = max_walkers != c->fallback_cap || (tol > 0.0 && !c->S.fb && c->S.cap_walk > 0);
+  c->fallback_tol = tol;
+  c->fallback_cap = max_walkers;
+  c->P.fallback_tol = tol;
+  c->P.fallback_cap = max_walkers;
+  if (resize) free_scratch(c);  // the fallback scratch is sized by the cap
+  return MDET_OK;
+}
+
 mdet_status mdet_set_walker_chunks(mdet_ctx* c, int n_chunks) {
   if (!c || n_chunks < 0) return MDET_E_ARG;
   c->n_chunks_cfg = std::min(n_chunks, (int)mdet_ctx::kMaxChunks);
@@ -768,6 +810,267 @@ mdet_status mdet_selftest_df32(int device, int64_t n, const double* x, double* y
   if (cudaSetDevice(device) != cudaSuccess) return MDET_E_CUDA;
   if (launch_selftest_df(n, x, y_df, y_ref, prod_df, nullptr) != cudaSuccess) return MDET_E_CUDA;
   if (cudaDeviceSynchronize() != cudaSuccess) return MDET_E_CUDA;
+  return MDET_OK;
+}
+
+mdet_status mdet_get_tuning(const mdet_ctx* c, mdet_tuning* out) {
+  if (!c || !out) return MDET_E_ARG;
+  *out = c->last_tune;
+  out->spmm_chunk = c->spmm_chunk;
+  out->mo_ec = c->mo_ec;
+  out->walker_chunks = c->n_chunks_cfg;
+  return MDET_OK;
+}
+
+mdet_status mdet_set_tuning(mdet_ctx* c, const mdet_tuning* t) {
+  if (!c || !t) return MDET_E_ARG;
+  if (t->spmm_chunk < 64 || t->spmm_chunk > 8192) return fail(c, MDET_E_ARG, "spmm_chunk outside 64..8192");
+  if (t->mo_ec != 4 && t->mo_ec != 6 && t->mo_ec != 8) return fail(c, MDET_E_ARG, "mo_ec must be 4, 6 or 8");
+  if (t->walker_chunks < 0) return fail(c, MDET_E_ARG, "walker_chunks < 0");
+  c->spmm_chunk = t->spmm_chunk;
+  c->mo_ec = t->mo_ec;
+  c->n_chunks_cfg = std::min(t->walker_chunks, (int)mdet_ctx::kMaxChunks);
+  c->P.spmm_chunk = c->spmm_chunk;
+  c->P.mo_ec = c->mo_ec;
+  return MDET_OK;
+}
+
+mdet_status mdet_autotune(mdet_ctx* c, int64_t n_walk, const double* R, double budget_ms, mdet_tuning* out) {
+  if (!c) return MDET_E_ARG;
+  if (c->device < 0) return fail(c, MDET_E_NODEVICE, "context has no device");
+  if (!c->has_ci) return fail(c, MDET_E_STATE, "set_ci_expansion must come first");
+  if (n_walk < 1 || !R || budget_ms <= 0) return fail(c, MDET_E_ARG, "bad autotune arguments");
+  CUDA_TRY(c, cudaSetDevice(c->device));
+  const int64_t N = c->n_up + c->n_dn;
+  double *d_log = nullptr, *d_grad = nullptr, *d_lap = nullptr;
+  int8_t* d_sign = nullptr;
+  mdet_status s;
+  if ((s = dalloc(c, &d_log, n_walk)) || (s = dalloc(c, &d_grad, 3 * N * n_walk)) ||
+      (s = dalloc(c, &d_lap, N * n_walk)) || (s = dalloc(c, &d_sign, n_walk))) {
+    cudaFree(d_log); cudaFree(d_grad); cudaFree(d_lap); cudaFree(d_sign);
+    return s;
+  }
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  const bool prof = c->profiling;
+  c->profiling = false;
+  cudaStream_t st = c->own_stream;
+  double spent = 0.0;
+  int trials = 0;
+  auto timed = [&](const mdet_tuning& t, float* ms) -> mdet_status {
+    mdet_status r = mdet_set_tuning(c, &t);
+    if (r) return r;
+    if ((r = mdet_evaluate(c, n_walk, R, d_log, d_sign, d_grad, d_lap, nullptr, nullptr, st))) return r;
+    CUDA_TRY(c, cudaEventRecord(e0, st));
+    for (int q = 0; q < 2; q++)
+      if ((r = mdet_evaluate(c, n_walk, R, d_log, d_sign, d_grad, d_lap, nullptr, nullptr, st))) return r;
+    CUDA_TRY(c, cudaEventRecord(e1, st));
+    CUDA_TRY(c, cudaEventSynchronize(e1));
+    CUDA_TRY(c, cudaEventElapsedTime(ms, e0, e1));
+    *ms *= 0.5f;
+    spent += 3.0 * *ms;
+    trials++;
+    return MDET_OK;
+  };
+  mdet_tuning cur{};
+  mdet_get_tuning(c, &cur);
+  if (cur.walker_chunks == 0) cur.walker_chunks = 1;
+  float best = 0.0f;
+  s = timed(cur, &best);
+  const bool mixed = c->precision == MDET_PRECISION_MIXED;
+  const int chunks[] = {256, 512, 1024, 2048}, ecs[] = {4, 6, 8}, wcs[] = {1, 2, 4};
+  for (int param = 0; param < 3 && s == MDET_OK; param++) {
+    const int* vals = param == 0 ? chunks : (param == 1 ? ecs : wcs);
+    const int nv = param == 0 ? 4 : 3;
+    if (param == 2 && !mixed) break;
+    for (int q = 0; q < nv && s == MDET_OK && spent < budget_ms; q++) {
+      mdet_tuning t = cur;
+      int* field = param == 0 ? &t.spmm_chunk : (param == 1 ? &t.mo_ec : &t.walker_chunks);
+      if (*field == vals[q]) continue;
+      *field = vals[q];
+      float ms = 0.0f;
+      s = timed(t, &ms);
+      if (s == MDET_OK && ms < best) {
+        best = ms;
+        cur = t;
+      }
+    }
+  }
+  mdet_status s2 = mdet_set_tuning(c, &cur);
+  if (s == MDET_OK) s = s2;
+  c->profiling = prof;
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaStreamSynchronize(st);
+  cudaFree(d_log); cudaFree(d_grad); cudaFree(d_lap); cudaFree(d_sign);
+  c->last_tune = cur;
+  c->last_tune.best_ms = best;
+  c->last_tune.trials = trials;
+  if (out && s == MDET_OK) *out = c->last_tune;
+  return s;
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Batches of contexts
+struct mdet_batch {
+  int device = -1;
+  cudaStream_t origin = nullptr;
+  std::vector<cudaStream_t> streams;
+  std::vector<cudaEvent_t> joins;
+  cudaEvent_t fork = nullptr;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  std::vector<mdet_ctx*> ctxs;
+};
+
+namespace {
+
+void batch_release(mdet_batch* b) {
+  if (!b) return;
+  if (b->device >= 0) cudaSetDevice(b->device);
+  if (b->exec) cudaGraphExecDestroy(b->exec);
+  if (b->graph) cudaGraphDestroy(b->graph);
+  for (cudaStream_t st : b->streams) cudaStreamDestroy(st);
+  for (cudaEvent_t e : b->joins) cudaEventDestroy(e);
+  if (b->fork) cudaEventDestroy(b->fork);
+  if (b->origin) cudaStreamDestroy(b->origin);
+  delete b;
+}
+
+mdet_status batch_setup(mdet_batch* b, int n_ctx, mdet_ctx* const* ctxs, int n_streams) {
+  if (n_ctx < 1 || !ctxs || n_streams < 1 || n_streams > 16) return MDET_E_ARG;
+  b->device = -1;
+  for (int i = 0; i < n_ctx; i++) {
+    if (!ctxs[i] || !ctxs[i]->has_ci || ctxs[i]->device < 0) return MDET_E_STATE;
+    if (b->device < 0) b->device = ctxs[i]->device;
+    if (ctxs[i]->device != b->device) return MDET_E_ARG;
+    for (int j = 0; j < i; j++)
+      if (ctxs[j] == ctxs[i]) return MDET_E_ARG;  // a context may appear once
+  }
+  if (cudaSetDevice(b->device) != cudaSuccess) return MDET_E_CUDA;
+  if (cudaStreamCreateWithFlags(&b->origin, cudaStreamNonBlocking) != cudaSuccess) return MDET_E_CUDA;
+  if (cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming) != cudaSuccess) return MDET_E_CUDA;
+  b->streams.assign(n_streams, nullptr);
+  b->joins.assign(n_streams, nullptr);
+  for (int k = 0; k < n_streams; k++)
+    if (cudaStreamCreateWithFlags(&b->streams[k], cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&b->joins[k], cudaEventDisableTiming) != cudaSuccess)
+      return MDET_E_CUDA;
+  b->ctxs.assign(ctxs, ctxs + n_ctx);
+  return MDET_OK;
+}
+
+// Fork from `origin`, evaluate every context on its stream, join back.
+mdet_status batch_enqueue(mdet_batch* b, const int64_t* n_walk, const double* const* R, double* const* log_abs_psi,
+                          int8_t* const* sign, double* const* grad, double* const* lap, double* const* e_local,
+                          uint32_t* const* status, cudaStream_t origin) {
+  const int n_ctx = (int)b->ctxs.size(), ns = (int)b->streams.size();
+  // longest processing time first onto the least-loaded stream
+  std::vector<double> cost(n_ctx);
+  for (int i = 0; i < n_ctx; i++) {
+    const mdet_ctx* c = b->ctxs[i];
+    const double N = c->n_up + c->n_dn;
+    const double per_walk = 4.0 * (double)c->n_det +
+                            (c->precision == MDET_PRECISION_MIXED ? 0.2 : 2.0) * 5.0 * N * c->n_ao * c->n_mo +
+                            40.0 * (double)(c->exc[0].size() + c->exc[1].size());
+    cost[i] = per_walk * (double)n_walk[i];
+  }
+  std::vector<int> order(n_ctx);
+  for (int i = 0; i < n_ctx; i++) order[i] = i;
+  std::sort(order.begin(), order.end(), [&](int a, int c2) { return cost[a] > cost[c2]; });
+  std::vector<double> load(ns, 0.0);
+  if (cudaEventRecord(b->fork, origin) != cudaSuccess) return MDET_E_CUDA;
+  for (int k = 0; k < ns; k++)
+    if (cudaStreamWaitEvent(b->streams[k], b->fork, 0) != cudaSuccess) return MDET_E_CUDA;
+  for (int i : order) {
+    const int k = (int)(std::min_element(load.begin(), load.end()) - load.begin());
+    load[k] += cost[i];
+    mdet_status s = mdet_evaluate(b->ctxs[i], n_walk[i], R[i], log_abs_psi[i], sign[i], grad[i], lap[i],
+                                  e_local ? e_local[i] : nullptr, status ? status[i] : nullptr, b->streams[k]);
+    if (s != MDET_OK) return s;
+  }
+  for (int k = 0; k < ns; k++) {
+    if (cudaEventRecord(b->joins[k], b->streams[k]) != cudaSuccess) return MDET_E_CUDA;
+    if (cudaStreamWaitEvent(origin, b->joins[k], 0) != cudaSuccess) return MDET_E_CUDA;
+  }
+  return MDET_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+mdet_status mdet_batch_evaluate(int n_ctx, mdet_ctx* const* ctxs, const int64_t* n_walk, const double* const* R,
+                                double* const* log_abs_psi, int8_t* const* sign, double* const* grad,
+                                double* const* lap, double* const* e_local, uint32_t* const* status,
+                                int n_streams, void* stream) {
+  if (!n_walk || !R || !log_abs_psi || !sign || !grad || !lap) return MDET_E_ARG;
+  mdet_batch* b = new (std::nothrow) mdet_batch();
+  if (!b) return MDET_E_OOM;
+  mdet_status s = batch_setup(b, n_ctx, ctxs, n_streams);
+  if (s == MDET_OK) s = batch_enqueue(b, n_walk, R, log_abs_psi, sign, grad, lap, e_local, status, (cudaStream_t)stream);
+  // streams and events may be destroyed with work pending: the runtime defers it
+  batch_release(b);
+  return s;
+}
+
+mdet_status mdet_batch_create(mdet_batch** out, int n_ctx, mdet_ctx* const* ctxs, const int64_t* n_walk,
+                              const double* const* R, double* const* log_abs_psi, int8_t* const* sign,
+                              double* const* grad, double* const* lap, double* const* e_local,
+                              uint32_t* const* status, int n_streams) {
+  if (!out || !n_walk || !R || !log_abs_psi || !sign || !grad || !lap) return MDET_E_ARG;
+  *out = nullptr;
+  mdet_batch* b = new (std::nothrow) mdet_batch();
+  if (!b) return MDET_E_OOM;
+  mdet_status s = batch_setup(b, n_ctx, ctxs, n_streams);
+  // one uncaptured pass sizes every scratch and sets every kernel attribute
+  if (s == MDET_OK) s = batch_enqueue(b, n_walk, R, log_abs_psi, sign, grad, lap, e_local, status, b->origin);
+  if (s == MDET_OK && cudaStreamSynchronize(b->origin) != cudaSuccess) s = MDET_E_CUDA;
+  std::vector<bool> prof(n_ctx > 0 ? n_ctx : 0);
+  if (s == MDET_OK) {
+    for (int i = 0; i < n_ctx; i++) {
+      prof[i] = ctxs[i]->profiling;
+      ctxs[i]->profiling = false;
+    }
+    if (cudaStreamBeginCapture(b->origin, cudaStreamCaptureModeRelaxed) != cudaSuccess) s = MDET_E_CUDA;
+    if (s == MDET_OK) {
+      mdet_status se = batch_enqueue(b, n_walk, R, log_abs_psi, sign, grad, lap, e_local, status, b->origin);
+      cudaError_t ee = cudaStreamEndCapture(b->origin, &b->graph);
+      if (se != MDET_OK) s = se;
+      else if (ee != cudaSuccess) s = MDET_E_CUDA;
+    }
+    if (s == MDET_OK && cudaGraphInstantiate(&b->exec, b->graph, 0) != cudaSuccess) s = MDET_E_CUDA;
+    for (int i = 0; i < n_ctx; i++) ctxs[i]->profiling = prof[i];
+  }
+  if (s != MDET_OK) {
+    batch_release(b);
+    return s;
+  }
+  *out = b;
+  return MDET_OK;
+}
+
+mdet_status mdet_batch_launch(mdet_batch* b, void* stream) {
+  if (!b || !b->exec) return MDET_E_ARG;
+  if (cudaSetDevice(b->device) != cudaSuccess) return MDET_E_CUDA;
+  if (cudaGraphLaunch(b->exec, (cudaStream_t)stream) != cudaSuccess) return MDET_E_CUDA;
+  return MDET_OK;
+}
+
+void mdet_batch_destroy(mdet_batch* b) { batch_release(b); }
+
+mdet_status mdet_get_error_estimates(mdet_ctx* c, int64_t n_walk, double* cond1, double* est) {
+  if (!c) return MDET_E_ARG;
+  if (c->device < 0) return fail(c, MDET_E_NODEVICE, "context has no device");
+  if (!c->has_ci || c->last_walk == 0) return fail(c, MDET_E_STATE, "no evaluation yet");
+  if (n_walk < 0 || n_walk > c->last_walk) return fail(c, MDET_E_ARG, "n_walk beyond the last evaluation");
+  CUDA_TRY(c, cudaSetDevice(c->device));
+  CUDA_TRY(c, cudaStreamSynchronize(c->last_stream));
+  if (cond1) CUDA_TRY(c, cudaMemcpy(cond1, c->S.kap, n_walk * 2 * sizeof(double), cudaMemcpyDeviceToHost));
+  if (est) CUDA_TRY(c, cudaMemcpy(est, c->S.est, n_walk * 2 * sizeof(double), cudaMemcpyDeviceToHost));
   return MDET_OK;
 }
 

@@ -34,6 +34,10 @@ struct DevProblem {
   int n_shell, n_ao, n_mo, n_prim;
   int n_det_sp[2];        // distinct determinants per spin
   int64_t nnz;            // products
+  int spmm_chunk;         // tuning: nonzeros per warp in the contraction
+  int mo_ec;              // tuning: electrons per CTA in the orbital kernels (4, 6 or 8)
+  double fallback_tol;    // estimated relative error above which a walker is re-evaluated by full LU (<= 0: off)
+  int fallback_cap;       // walkers re-evaluated per evaluation at most
   const double* Z;        // [n_nuc]
   const double* nuc_xyz;  // [n_nuc][3]
   const int* shell_l;     // [n_shell]
@@ -58,6 +62,8 @@ struct DevProblem {
   const int* csc_col;      // [nnz] column (down index), sorted by column then row
   const int* csc_row;      // [nnz]
   const double* csc_val;   // [nnz]
+  const int* csr_ptr;      // [n_det_up + 1] row starts of the row-major order
+  const int* csc_ptr;      // [n_det_dn + 1] column starts of the column-major order
 };
 
 // Per-evaluation scratch (owned by the context, grown on demand).
@@ -69,12 +75,17 @@ struct DevScratch {
   double* ld0 = nullptr;  // [W][2] log|D_ref|
   double* sg0 = nullptr;  // [W][2] sign(D_ref)
   double* g = nullptr;    // [W][n_elec][4]  (d_{i mu} D_ref) / D_ref
+  double* kap = nullptr;  // [W][2] cond_1 of each reference Slater matrix
+  double* est = nullptr;  // [W][2] error estimates of the table result (l1 and l2 forms)
   double* T = nullptr;    // [n_up + n_dn][n_mo][wp] walker-minor ratio tables (up block then down block)
   float2* Tdf = nullptr;  // same as double-float pairs (hi, lo), mixed path only
   double* r = nullptr;    // [n_det_up + n_det_dn][wp] ratios D_I / D_ref, walker-minor
   double* vu = nullptr;   // walker-major [wp][n_det_up + n_det_dn]: v = C r_dn (up) then u = C^T r_up (down)
   double* psit = nullptr; // [wp] Psi / (D_ref_up D_ref_dn)
   uint32_t* wstat = nullptr;  // [W] status bits
+  double* fb = nullptr;       // fallback: [cap][n_det_up + n_det_dn][2 + 4 max(n_up, n_dn)], then [cap][ndt] values
+  int* fb_list = nullptr;     // fallback: [1 + cap] count, then walker indices
+  double* fb_acc = nullptr;   // fallback: [cap][3 + 8 MDET_FALLBACK_MAX_SPIN] scales, Psi, G
   double* R_stage = nullptr;  // host-API staging buffers
   double* out_stage = nullptr;
 };
@@ -100,6 +111,9 @@ DevScratch scratch_view(const DevScratch& S, const DevProblem& P, int64_t off);
 // psit, for walker-minor arrays of leading dimension ld (a multiple of 128).
 cudaError_t launch_spmm_rows_f64(const DevProblem& P, const double* r_dn, const double* r_up, double* v,
                                  double* psit, int64_t ld, int64_t n_walk, cudaStream_t st);
+cudaError_t launch_fallback(const DevProblem& P, const DevScratch& S, int64_t n_walk, const double* R,
+                            double* log_abs_psi, int8_t* sign, double* grad, double* lap, double* e_local,
+                            uint32_t* status, cudaStream_t st);
 // Device index and uploaded problem of a context (null when it has none).
 const DevProblem* ctx_problem(const mdet_ctx* ctx, int* device);
 cudaError_t launch_selftest_df(int64_t n, const double* x, double* y_df, double* y_ref, double* prod_df,

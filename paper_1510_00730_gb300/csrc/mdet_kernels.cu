@@ -40,13 +40,14 @@ namespace mdet {
 
 namespace {
 
-constexpr int kEC = 6;  // electrons per CTA in the orbital kernel
 
 // ---------------------------------------------------------------------------
-// K1: orbitals. grid (n_walk, ceil(n_elec / kEC)); smem X[5][kEC][n_ao].
+// K1: orbitals. grid (n_walk, ceil(n_elec / kEC)); smem X[5][kEC][n_ao]; kEC (electrons
+// per CTA) is a tuning parameter.
 // AO chi = P(x, y, z) f(r^2), P = x^a y^b z^c (degree l), f(s) = sum_p c_p e^{-alpha_p s}:
 //   d_x chi = P_x f + 2 x P f',   Lap chi = (Lap P) f + P ((4 l + 6) f' + 4 s f'')
 // (Euler: x P_x + y P_y + z P_z = l P). Then Phi[c][e][m] = sum_mu X[c][e][mu] B[mu][m].
+template <int kEC>
 __global__ void __launch_bounds__(128) k_mo_f64(DevProblem P, double* __restrict__ phi,
                                                 const double* __restrict__ R) {
   extern __shared__ double smem[];
@@ -110,6 +111,14 @@ __global__ void __launch_bounds__(64) k_ref(DevProblem P, DevScratch S) {
       }
     }
     __syncwarp();
+    // |S|_1: largest absolute column sum (lane c sums column c)
+    double cs = 0.0;
+    if (lane < n)
+      for (int i = 0; i < n; i++) cs += fabs(aug[sp][i][lane]);
+#pragma unroll
+    for (int off = 16; off; off >>= 1) cs = fmax(cs, __shfl_xor_sync(0xffffffffu, cs, off));
+    const double normS = cs;
+    __syncwarp();
     bool used = false;
     int step = -1;
     double logd = 0.0, sgn = 1.0, pmax = 0.0, pmin = DBL_MAX;
@@ -161,12 +170,21 @@ __global__ void __launch_bounds__(64) k_ref(DevProblem P, DevScratch S) {
     for (int off = 16; off; off >>= 1) inv_cnt += __shfl_xor_sync(0xffffffffu, inv_cnt, off);
     if (inv_cnt & 1) sgn = -sgn;
     if (lane < n && !singular) rowof[sp][step] = lane;
+    // |A|_1 (the rows of A sit permuted across lanes; column sums do not care)
+    double ca = 0.0;
+    if (lane < n && !singular)
+      for (int i = 0; i < n; i++) ca += fabs(aug[sp][i][n + lane]);
+#pragma unroll
+    for (int off = 16; off; off >>= 1) ca = fmax(ca, __shfl_xor_sync(0xffffffffu, ca, off));
+    const double kappa1 = normS * ca;
     if (lane == 0) {
       bad[sp] = singular;
       S.ld0[w * 2 + sp] = singular ? -INFINITY : logd;
       S.sg0[w * 2 + sp] = singular ? 0.0 : sgn;
       uint32_t st = singular ? MDET_WS_REF_SINGULAR : 0u;
       if (!singular && pmin < 1e-13 * pmax) st |= MDET_WS_REF_ILLCOND;
+      S.kap[w * 2 + sp] = singular ? INFINITY : kappa1;
+      if (P.fallback_tol > 0.0 && P.n_up <= MDET_FALLBACK_MAX_SPIN && singular) st |= MDET_WS_FALLBACK;
       stf[sp] = st;
     }
   }
@@ -372,6 +390,9 @@ __global__ void __launch_bounds__(128) k_final(DevProblem P, DevScratch S, const
   float* Wlo = Whi + NM;                                              //        [N][M] lo words
   __shared__ double red[4];
   __shared__ double Gs[kMaxSpin * 2][4];
+  __shared__ float Ga[kMaxSpin * 2][4];
+  __shared__ float G2[kMaxSpin * 2][4];
+  __shared__ float rmsG[4], estw[2][4];
   for (int t = threadIdx.x; t < NM; t += blockDim.x) {
     Ts[t] = S.T[(size_t)t * wp + w];
     if (MIXED) {
@@ -477,10 +498,24 @@ __global__ void __launch_bounds__(128) k_final(DevProblem P, DevScratch S, const
     const double* dphi = S.phi + ((w * 5 + 1 + mu) * N + e) * M;
     const double* Qr = Qs + e * M;
     double acc = S.g[(w * N + e) * 4 + mu] * psit;
-    for (int m = 0; m < M; m++) acc = fma(dphi[m], Qr[m], acc);
+    // magnitudes of the terms, for the error estimate (FP32 is plenty for an estimate)
+    float aab = fabsf((float)acc), aa2 = aab * aab;
+    for (int m = 0; m < M; m++) {
+      acc = fma(dphi[m], Qr[m], acc);
+      const float tm = fabsf((float)dphi[m] * (float)Qr[m]);
+      aab += tm;
+      aa2 = fmaf(tm, tm, aa2);
+    }
     const double* Pb = Pm + (sp ? nu * nu : 0);
-    for (int b = 0; b < n; b++) acc = fma(-dphi[occ[b]], Pb[b * n + i], acc);
+    for (int b = 0; b < n; b++) {
+      acc = fma(-dphi[occ[b]], Pb[b * n + i], acc);
+      const float tm = fabsf((float)dphi[occ[b]] * (float)Pb[b * n + i]);
+      aab += tm;
+      aa2 = fmaf(tm, tm, aa2);
+    }
     Gs[e][mu] = acc;
+    Ga[e][mu] = aab;
+    G2[e][mu] = sqrtf(aa2);
   }
   __syncthreads();
   // potential energy: electron-nucleus, electron-electron, nucleus-nucleus
@@ -520,6 +555,45 @@ __global__ void __launch_bounds__(128) k_final(DevProblem P, DevScratch S, const
     finite &= isfinite(gx) && isfinite(gy) && isfinite(gz) && isfinite(lp);
   }
   const int all_finite = __syncthreads_and(finite);
+  // first-order error estimate of the table result: the terms of each
+  // derivative sum carry relative errors ~ u cond_1(S_ref), so the error of G
+  // relative to max(|G|, rms over the walker's electrons) is about
+  // u cond_1 (sum of |terms|) / max(|G|, rms), or with the terms added in
+  // quadrature for independent rounding errors
+  const bool fb_on = P.fallback_tol > 0.0 && P.n_up <= MDET_FALLBACK_MAX_SPIN;
+  if (fb_on) {
+    if (threadIdx.x < 4) {
+      float r = 0.0f;
+      for (int i = 0; i < N; i++) r += (float)Gs[i][threadIdx.x] * (float)Gs[i][threadIdx.x];
+      rmsG[threadIdx.x] = sqrtf(r / N);
+    }
+    __syncthreads();
+    const float u = MIXED ? 0x1p-47f : 0x1p-53f;
+    float e1 = 0.0f, e2 = 0.0f;
+    for (int t = threadIdx.x; t < N * 4; t += blockDim.x) {
+      const int i = t >> 2, mu = t & 3;
+      const float kap = (float)fmin(S.kap[w * 2 + (i < nu ? 0 : 1)], 1e30);
+      const float den = fmaxf(fabsf((float)Gs[i][mu]), rmsG[mu]);
+      e1 = fmaxf(e1, u * kap * Ga[i][mu] / den);
+      e2 = fmaxf(e2, u * kap * G2[i][mu] / den);
+    }
+#pragma unroll
+    for (int off = 16; off; off >>= 1) {
+      e1 = fmaxf(e1, __shfl_xor_sync(0xffffffffu, e1, off));
+      e2 = fmaxf(e2, __shfl_xor_sync(0xffffffffu, e2, off));
+    }
+    __shared__ float wmax[2][4];
+    if ((threadIdx.x & 31) == 0) {
+      wmax[0][threadIdx.x >> 5] = e1;
+      wmax[1][threadIdx.x >> 5] = e2;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      estw[0][0] = fmaxf(fmaxf(wmax[0][0], wmax[0][1]), fmaxf(wmax[0][2], wmax[0][3]));
+      estw[1][0] = fmaxf(fmaxf(wmax[1][0], wmax[1][1]), fmaxf(wmax[1][2], wmax[1][3]));
+    }
+    __syncthreads();
+  }
   if (threadIdx.x == 0) {
     double tl = 0.0;
     for (int i = 0; i < N; i++) tl += Gs[i][3];
@@ -531,6 +605,11 @@ __global__ void __launch_bounds__(128) k_final(DevProblem P, DevScratch S, const
     sign[w] = (int8_t)(sg > 0 ? s : (sg < 0 ? -s : 0));
     if (e_local) e_local[w] = el;
     uint32_t st = S.wstat[w];
+    if (fb_on) {
+      S.est[w * 2] = estw[0][0];
+      S.est[w * 2 + 1] = estw[1][0];
+      if (!(estw[1][0] <= (float)P.fallback_tol)) st |= MDET_WS_FALLBACK;
+    }
     if (psit == 0.0) st |= MDET_WS_PSI_ZERO;
     if (!all_finite || !isfinite(el) || !isfinite(lg)) st |= MDET_WS_NONFINITE;
     S.wstat[w] = st;
@@ -541,16 +620,28 @@ __global__ void __launch_bounds__(128) k_final(DevProblem P, DevScratch S, const
 }  // namespace
 
 // ---------------------------------------------------------------------------
+template <int EC>
+static cudaError_t launch_mo_f64_ec(const DevProblem& P, const DevScratch& S, int64_t n_walk, const double* R,
+                                   cudaStream_t st) {
+  const size_t smem = sizeof(double) * 5 * EC * P.n_ao;
+  static size_t attr_bytes = 0;  // dynamic shared memory opted in so far (static arrays come on top)
+  if (smem > attr_bytes) {
+    cudaError_t e = cudaFuncSetAttribute(k_mo_f64<EC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    attr_bytes = smem;
+  }
+  dim3 grid((unsigned)n_walk, (P.n_elec + EC - 1) / EC);
+  k_mo_f64<EC><<<grid, 128, smem, st>>>(P, S.phi, R);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_mo_f64(const DevProblem& P, const DevScratch& S, int64_t n_walk, const double* R,
                           cudaStream_t st) {
-  const size_t smem = sizeof(double) * 5 * kEC * P.n_ao;
-  if (smem > 48 * 1024) {
-    cudaError_t e = cudaFuncSetAttribute(k_mo_f64, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
+  switch (P.mo_ec) {
+    case 4: return launch_mo_f64_ec<4>(P, S, n_walk, R, st);
+    case 8: return launch_mo_f64_ec<8>(P, S, n_walk, R, st);
+    default: return launch_mo_f64_ec<6>(P, S, n_walk, R, st);
   }
-  dim3 grid((unsigned)n_walk, (P.n_elec + kEC - 1) / kEC);
-  k_mo_f64<<<grid, 128, smem, st>>>(P, S.phi, R);
-  return cudaGetLastError();
 }
 
 cudaError_t launch_ref_tables(const DevProblem& P, const DevScratch& S, int64_t n_walk, bool mixed,
@@ -585,7 +676,7 @@ cudaError_t launch_contract_f64(const DevProblem& P, const DevScratch& S, int64_
     cudaGetDevice(&dev);
     if (cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n_sm <= 0) n_sm = 132;
   }
-  const int chunk = 512;
+  const int chunk = P.spmm_chunk > 0 ? P.spmm_chunk : 512;
   const int64_t n_chunks = (P.nnz + chunk - 1) / chunk;
   const int64_t n_groups = (n_walk + 255) / 256;
   const int64_t items = n_chunks * n_groups;
@@ -616,6 +707,8 @@ DevScratch scratch_view(const DevScratch& S, const DevProblem& P, int64_t off) {
   V.ld0 = S.ld0 + off * 2;
   V.sg0 = S.sg0 + off * 2;
   V.g = S.g + off * N * 4;
+  V.kap = S.kap + off * 2;
+  V.est = S.est + off * 2;
   V.wstat = S.wstat + off;
   V.vu = S.vu + off * ndt;
   V.T = S.T + off;  // walker-minor: a column offset with the same stride
@@ -644,9 +737,11 @@ cudaError_t launch_final(const DevProblem& P, const DevScratch& S, int64_t n_wal
                          uint32_t* status, bool mixed, cudaStream_t st) {
   const size_t smem = final_smem_bytes(P, mixed);
   auto kern = mixed ? k_final<true> : k_final<false>;
-  if (smem > 48 * 1024) {
+  static size_t attr_bytes[2] = {0, 0};  // dynamic shared memory opted in so far (static arrays come on top)
+  if (smem > attr_bytes[mixed]) {
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
+    attr_bytes[mixed] = smem;
   }
   kern<<<(unsigned)n_walk, 128, smem, st>>>(P, S, R, log_abs_psi, sign, grad, lap, e_local, status);
   return cudaGetLastError();

@@ -18,8 +18,6 @@ namespace mdet {
 
 namespace {
 
-constexpr int kECm = 6;  // electrons per CTA in the orbital kernel
-
 // Orbitals. grid (n_walk, ceil(n_elec / kECm)), block 128. AO values and
 // derivatives are formed in double-float arithmetic on the FP32 pipe
 // (ao_shell_values_df), stored as FP32 pairs x = xh + xl in shared memory, and
@@ -28,6 +26,7 @@ constexpr int kECm = 6;  // electrons per CTA in the orbital kernel
 // and the cross terms xh*bl + xl*bh plus all rounding errors go into a second
 // FP32 accumulator (the Dot2 scheme of Ogita, Rump and Oishi, extended to split
 // inputs). Phi = s + c is stored in FP64.
+template <int kECm>
 __global__ void __launch_bounds__(128) k_mo_mixed(DevProblem P, double* __restrict__ phi,
                                                   const double* __restrict__ R) {
   extern __shared__ float smf[];
@@ -130,16 +129,28 @@ __global__ void k_selftest_df(int64_t n, const double* __restrict__ x, double* _
 
 }  // namespace
 
+template <int EC>
+static cudaError_t launch_mo_mixed_ec(const DevProblem& P, const DevScratch& S, int64_t n_walk, const double* R,
+                                     cudaStream_t st) {
+  const size_t smem = sizeof(float) * 2 * 5 * EC * P.n_ao;
+  static size_t attr_bytes = 0;  // dynamic shared memory opted in so far (static arrays come on top)
+  if (smem > attr_bytes) {
+    cudaError_t e = cudaFuncSetAttribute(k_mo_mixed<EC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    attr_bytes = smem;
+  }
+  dim3 grid((unsigned)n_walk, (P.n_elec + EC - 1) / EC);
+  k_mo_mixed<EC><<<grid, 128, smem, st>>>(P, S.phi, R);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_mo_mixed(const DevProblem& P, const DevScratch& S, int64_t n_walk, const double* R,
                             cudaStream_t st) {
-  const size_t smem = sizeof(float) * 2 * 5 * kECm * P.n_ao;
-  if (smem > 48 * 1024) {
-    cudaError_t e = cudaFuncSetAttribute(k_mo_mixed, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
+  switch (P.mo_ec) {
+    case 4: return launch_mo_mixed_ec<4>(P, S, n_walk, R, st);
+    case 8: return launch_mo_mixed_ec<8>(P, S, n_walk, R, st);
+    default: return launch_mo_mixed_ec<6>(P, S, n_walk, R, st);
   }
-  dim3 grid((unsigned)n_walk, (P.n_elec + kECm - 1) / kECm);
-  k_mo_mixed<<<grid, 128, smem, st>>>(P, S.phi, R);
-  return cudaGetLastError();
 }
 
 cudaError_t launch_selftest_df(int64_t n, const double* x, double* y_df, double* y_ref, double* prod_df,

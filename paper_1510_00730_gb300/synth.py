@@ -272,6 +272,38 @@ def tiny(n_up=2, n_dn=2, n_mo=5, n_det=None, n_walk=4, seed=7, k_max=2, shells=(
                          n_det, k_max, n_walk, coef_law="lognormal", n_unique=nu)
 
 
+def _shell_counts(rng, n_ao):
+    """s/p/d/f shell counts whose Cartesian AOs add up to n_ao exactly."""
+    while True:
+        n_f = int(rng.integers(0, 1 + n_ao // 60))
+        n_d = int(rng.integers(1, 1 + n_ao // 15))
+        n_p = int(rng.integers(1, 1 + n_ao // 8))
+        n_s = n_ao - 10 * n_f - 6 * n_d - 3 * n_p
+        if n_s >= 2:
+            return (n_s, n_p, n_d, n_f)
+
+
+def batched_uneven(n_exp=64, seed=151000734, walkers=(256, 4096), n_det_range=(1e3, 1e6),
+                   elec_range=(8, 34), ao_range=(40, 160)):
+    """Independent expansions of uneven size: N_elec uniform in [8, 34] split as
+    evenly as possible between the spins (up >= down), AOs uniform in [40, 160],
+    N_MO = max(round(0.73 N_AO), N_up + 4), N_det log-uniform in [1e3, 1e6],
+    walkers uniform in [256, 4096], degrees up to 4."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for i in range(n_exp):
+        ne = int(rng.integers(elec_range[0], elec_range[1] + 1))
+        n_up, n_dn = (ne + 1) // 2, ne // 2
+        n_ao = int(rng.integers(ao_range[0], ao_range[1] + 1))
+        n_mo = min(n_ao, 255, max(int(round(0.73 * n_ao)), n_up + 4))
+        n_det = int(round(math.exp(rng.uniform(math.log(n_det_range[0]), math.log(n_det_range[1])))))
+        n_walk = int(rng.integers(walkers[0], walkers[1] + 1))
+        wl = make_workload("uneven_%02d" % i, seed * 100 + i, n_up, n_dn, ne, _shell_counts(rng, n_ao),
+                           (0.03, 1.0e5), n_mo, n_det, 4, n_walk)
+        out.append(wl)
+    return out
+
+
 WORKLOADS = {
     "oxygen_like_1k": oxygen_like_1k,
     "chlorine_like_100k": chlorine_like_100k,

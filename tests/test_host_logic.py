@@ -197,3 +197,20 @@ def test_unique_counts_follow_generator():
     assert (st["n_det_up"], st["n_det_dn"]) == wl.meta["n_unique"] == (900, 900)
     assert st["max_degree"] == [4, 4]
     assert sum(st["degree_hist"][0]) == 900
+
+
+def test_uneven_batch_generator_ranges():
+    """The 64-expansion uneven workload follows its recipe: 8-34 electrons split
+    as evenly as possible, 40-160 AOs, N_MO = max(round(0.73 N_AO), N_up + 4),
+    10^3-10^6 determinants, 256-4,096 walkers."""
+    wls = synth.batched_uneven()
+    assert len(wls) == 64
+    for wl in wls:
+        ne = wl.n_up + wl.n_dn
+        assert 8 <= ne <= 34 and wl.n_up - wl.n_dn in (0, 1)
+        assert 40 <= wl.n_ao <= 160
+        assert wl.n_mo == min(wl.n_ao, 255, max(int(round(0.73 * wl.n_ao)), wl.n_up + 4))
+        assert 1000 <= wl.n_det <= 1_000_000
+        assert 256 <= wl.n_walk <= 4096
+    nd = np.log10([wl.n_det for wl in wls])
+    assert nd.min() < 3.6 and nd.max() > 5.4   # spans the decades
