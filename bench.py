@@ -27,6 +27,9 @@ METRIC = "walker-steps/s (Ψ,∇Ψ,∇²Ψ), 17e⁻, N_det=750k: mixed vs FP64 a
 UNIT = "walker-steps/s"
 FP64_PEAK_TFLOPS = 1.25     # nominal dense FP64 of one GB300 (recipe table); see the design doc
 CPU_SAMPLE_WALKERS = 96     # bounded oracle sample for the CPU baseline (~10-30 s of CPU work)
+# dram__bytes_read.sum + dram__bytes_write.sum of one k_spmm_wm launch on the 750k workload with
+# 8,192 walkers (ncu capture summarised in profiles/mixed_chlorine_like_750k.md)
+SPMM_TRAFFIC_750K = None
 
 
 def _env_int(k, d):
@@ -248,14 +251,18 @@ def run_ours(args):
     h2d = W * N * 3 * 8
     d2h = W * (8 + 1 + 3 * N * 8 + N * 8 + 8 + 4)
 
-    # roofline of the dominant kernel: the FP64 sparse contraction, 2 launches per step
-    # (v = C r_dn, u = C^T r_up), each 2 FLOP per nonzero per walker
+    # roofline of the dominant kernel: the FP64 sparse contraction k_spmm_wm, 2 launches per
+    # step (v = C r_dn, u = C^T r_up), each 2 FLOP per nonzero per walker
     kern = main["kern"]
     flops_launch = 2.0 * st["n_det"] * W
     launch_ms = kern["contract"] / 2
     achieved = flops_launch / (launch_ms / 1e3) / 1e12
-    roofline = {"kernel": "k_spmm_f64", "bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS,
-                "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS, "traffic": args.traffic,
+    traffic = args.traffic
+    if traffic is None and args.workload == "chlorine_like_750k" and W == 8192:
+        traffic = SPMM_TRAFFIC_750K
+    roofline = {"kernel": "k_spmm_wm", "bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS,
+                "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS, "traffic": traffic,
+                "traffic_unit": "bytes per launch (ncu dram read + write)",
                 "peak_source": "nominal FP64 of the recipe table (no measured FP64 peak)",
                 "flops_per_launch": flops_launch, "launch_ms": launch_ms}
 
@@ -355,6 +362,61 @@ def run_batched(args):
     batch.close()
 
 
+def run_learned(args):
+    """The learned Metropolis proposal on the chlorine-like 10^5-determinant
+    expansion with 8,192 walkers: a chain of drift-diffusion moves (limited
+    drift) generates 2^20 configurations, the perceptron is trained on them
+    on the GPU (generalised speed measure), and both movers then run the same
+    number of steps from the same walkers. value = autocorrelation-corrected
+    samples/s of <E_L> with the learned move (walker-steps/s / tau_int(E_L),
+    Sokal window c = 5); the drift-diffusion chain is reported beside it."""
+    import math
+
+    import torch
+
+    import paper_1510_00730_gb300 as pkg
+    from paper_1510_00730_gb300 import binding as B
+    from paper_1510_00730_gb300 import synth
+    from paper_1510_00730_gb300.vmc import VMC, measure_chain, train_esjd
+    torch.cuda.set_device(0)
+    wl = synth.chlorine_like_100k(n_walk=8192)
+    prec = {"mixed": pkg.PRECISION_MIXED, "fp64": pkg.PRECISION_FP64}[args.precision]
+    ctx = pkg.Context.from_workload(wl, device=0, precision=prec)
+    tau = 3e-5
+    n_chain = max(args.steps, 100)
+    dd = VMC(ctx, wl.R, seed=2, drift_tau=tau)
+    dd.run(500, tau=tau, record=False)
+    R_eq = dd.cur["R"].clone()
+    t0 = time.perf_counter()
+    R_data, lp_data, F_data = dd.collect_configs(tau, (1 << 20) // wl.n_walk)
+    torch.cuda.synchronize()
+    collect_s = time.perf_counter() - t0
+    mlp = B.MLP(0, wl.n_elec, hidden=256, seed=3, mu_max=1.0, s0=0.5 * math.log(tau), s_span=3.0)
+    t0 = time.perf_counter()
+    hist = train_esjd(mlp, ctx, R_data, lp_data, F_data, tau, epochs=3, batch=8192, lr=3e-4, speed_beta=0.1,
+                      target_acc=0.4)
+    torch.cuda.synchronize()
+    train_s = time.perf_counter() - t0
+    with ClockSampler(_gpu_index(0)) as clk:
+        base = measure_chain(ctx, R_eq, n_chain, tau, seed=5, warmup=args.warmup)
+        learned = measure_chain(ctx, R_eq, n_chain, tau, mlp=mlp, seed=6, warmup=args.warmup)
+    line = {"metric": "autocorrelation-corrected samples/s of <E_L>, learned proposal vs drift-diffusion",
+            "value": learned["samples_per_s"], "unit": "samples/s", "n_gpus": 1, "steps": n_chain,
+            "warmup": args.warmup, "ms_per_step": learned["ms_per_step"], "higher_is_better": True,
+            "dtype": "f64+f32x2" if prec == pkg.PRECISION_MIXED else "f64", "data": "synthetic",
+            "config": {"workload": "learned_proposal_100k", "walkers": wl.n_walk, "n_det": int(wl.n_det),
+                       "tau": tau, "drift_limit_a": 1.0, "training_configs": int(R_data.shape[0]),
+                       "mlp": "51-256-256-68 tanh, BF16 weights, FP32 accumulation",
+                       "objective": "generalised speed measure, target acceptance 0.4"},
+            "learned": learned, "drift_diffusion": base,
+            "gain": learned["samples_per_s"] / base["samples_per_s"],
+            "training": {"collect_s": collect_s, "train_s": train_s,
+                         "objective_acceptance_per_epoch": hist},
+            "clocks": clk.summary()}
+    print(json.dumps(line), flush=True)
+    mlp.close()
+
+
 def main():
     p = argparse.ArgumentParser()
     p.add_argument("--gpus", type=int, default=1)
@@ -378,6 +440,8 @@ def main():
         run_reference(args)
     elif args.workload == "batched_uneven_64":
         run_batched(args)
+    elif args.workload == "learned_proposal_100k":
+        run_learned(args)
     else:
         run_ours(args)
 

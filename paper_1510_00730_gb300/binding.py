@@ -99,6 +99,40 @@ def load_library(build_if_missing: bool = True):
                  "mdet_set_tuning", "mdet_autotune", "mdet_batch_evaluate", "mdet_batch_create", "mdet_batch_launch", "mdet_set_fallback",
                  "mdet_get_error_estimates"):
         getattr(L, name).restype = i32
+    # VMC moves and the learned proposal (include/mdet_vmc.h)
+    u32p = C.POINTER(C.c_uint32)
+    L.mdet_philox4x32_10.argtypes = [u32p, u32p, u32p]
+    L.mdet_philox4x32_10.restype = None
+    L.mdet_vmc_propose_drift.argtypes = [i64, i32, vp, vp, C.c_double, C.c_uint64, C.c_uint64, vp, vp, vp]
+    L.mdet_vmc_reverse_drift.argtypes = [i64, i32, vp, vp, vp, C.c_double, vp, vp]
+    L.mdet_vmc_accept.argtypes = [i64, i32, C.c_uint64, C.c_uint64, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp,
+                                  vp, vp, vp, vp, vp, vp]
+    L.mdet_vmc_r2.argtypes = [i64, i32, vp, vp, vp]
+    L.mdet_vmc_select_rows.argtypes = [i64, i32, vp, vp, vp, vp]
+    L.mdet_vmc_limit_drift.argtypes = [i64, i32, vp, C.c_double, C.c_double, vp, vp]
+    L.mdet_mlp_create.argtypes = [C.POINTER(vp), i32, i32, i32, C.c_uint64, C.c_double, C.c_double, C.c_double,
+                                  C.c_double]
+    L.mdet_mlp_destroy.argtypes = [vp]
+    L.mdet_mlp_destroy.restype = None
+    L.mdet_mlp_n_params.argtypes = [vp]
+    L.mdet_mlp_n_params.restype = i64
+    for n in ("mdet_mlp_get_params", "mdet_mlp_set_params", "mdet_mlp_get_grads"):
+        getattr(L, n).argtypes = [vp, vp]
+    L.mdet_mlp_forward.argtypes = [vp, i64, vp, vp, vp]
+    L.mdet_mlp_backward.argtypes = [vp, i64, vp, vp]
+    L.mdet_mlp_zero_grad.argtypes = [vp, vp]
+    L.mdet_mlp_adam.argtypes = [vp, C.c_double, C.c_double, C.c_double, C.c_double, i64, vp]
+    L.mdet_mlp_nll_grad.argtypes = [vp, i64, vp, vp, vp, vp, vp, vp]
+    L.mdet_vmc_propose_mlp.argtypes = [vp, i64, vp, vp, vp, C.c_uint64, C.c_uint64, vp, vp, vp]
+    L.mdet_mlp_esjd_grad.argtypes = [vp, i64, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp, C.c_int, C.c_double,
+                                     C.c_double, vp, vp, vp, vp]
+    L.mdet_vmc_reverse_mlp.argtypes = [vp, i64, vp, vp, vp, vp, vp, vp]
+    for n in ("mdet_vmc_propose_drift", "mdet_vmc_reverse_drift", "mdet_vmc_accept", "mdet_vmc_r2",
+              "mdet_vmc_select_rows", "mdet_vmc_limit_drift",
+              "mdet_mlp_create", "mdet_mlp_get_params", "mdet_mlp_set_params", "mdet_mlp_get_grads",
+              "mdet_mlp_forward", "mdet_mlp_backward", "mdet_mlp_zero_grad", "mdet_mlp_adam", "mdet_mlp_nll_grad",
+              "mdet_vmc_propose_mlp", "mdet_vmc_reverse_mlp", "mdet_mlp_esjd_grad"):
+        getattr(L, n).restype = i32
     _lib = L
     return L
 
@@ -403,3 +437,175 @@ class Batch:
             self.close()
         except Exception:
             pass
+
+
+# ---------------------------------------------------------------------------
+# VMC moves and the learned proposal
+
+def _sp(stream, dev):
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream(dev)
+    return stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream)
+
+
+def _chk(st, what):
+    if st:
+        raise MdetError(st, "%s failed: %s" % (what, load_library().mdet_status_string(st).decode()))
+
+
+def philox4x32_10(ctr, key):
+    """Philox4x32-10 block for a 4-word counter and 2-word key (host)."""
+    L = load_library()
+    c = (C.c_uint32 * 4)(*[int(v) & 0xFFFFFFFF for v in ctr])
+    k = (C.c_uint32 * 2)(*[int(v) & 0xFFFFFFFF for v in key])
+    o = (C.c_uint32 * 4)()
+    L.mdet_philox4x32_10(c, k, o)
+    return [int(v) for v in o]
+
+
+def vmc_propose_drift(R, grad, tau, seed, step, R_new, log_q, stream=None):
+    _chk(load_library().mdet_vmc_propose_drift(R.shape[0], R.shape[1], R.data_ptr(), grad.data_ptr(), float(tau),
+                                               int(seed), int(step), R_new.data_ptr(), log_q.data_ptr(),
+                                               _sp(stream, R.device)), "mdet_vmc_propose_drift")
+
+
+def vmc_reverse_drift(R, R_new, grad_new, tau, log_q, stream=None):
+    _chk(load_library().mdet_vmc_reverse_drift(R.shape[0], R.shape[1], R.data_ptr(), R_new.data_ptr(),
+                                               grad_new.data_ptr(), float(tau), log_q.data_ptr(),
+                                               _sp(stream, R.device)), "mdet_vmc_reverse_drift")
+
+
+def vmc_accept(seed, step, log_q_fwd, log_q_rev, cur, new, accept=None, n_accept=None, stream=None):
+    """cur / new: dicts with R, log_abs_psi, sign, grad, lap, e_local (device tensors)."""
+    R = cur["R"]
+    _chk(load_library().mdet_vmc_accept(
+        R.shape[0], R.shape[1], int(seed), int(step), log_q_fwd.data_ptr(), log_q_rev.data_ptr(), R.data_ptr(),
+        cur["log_abs_psi"].data_ptr(), cur["sign"].data_ptr(), cur["grad"].data_ptr(), cur["lap"].data_ptr(),
+        cur["e_local"].data_ptr(), new["R"].data_ptr(), new["log_abs_psi"].data_ptr(), new["sign"].data_ptr(),
+        new["grad"].data_ptr(), new["lap"].data_ptr(), new["e_local"].data_ptr(),
+        accept.data_ptr() if accept is not None else None, n_accept.data_ptr() if n_accept is not None else None,
+        _sp(stream, R.device)), "mdet_vmc_accept")
+
+
+def vmc_limit_drift(F, tau, a, F_bar, stream=None):
+    """Per-electron drift limiting (Umrigar, Nightingale and Runge); a = 0 copies F."""
+    _chk(load_library().mdet_vmc_limit_drift(F.shape[0], F.shape[1], F.data_ptr(), float(tau), float(a),
+                                             F_bar.data_ptr(), _sp(stream, F.device)), "mdet_vmc_limit_drift")
+
+
+def vmc_select_rows(take, src, dst, stream=None):
+    """dst[w] = src[w] where take[w] != 0 (float32 rows)."""
+    _chk(load_library().mdet_vmc_select_rows(src.shape[0], src.shape[1], take.data_ptr(), src.data_ptr(),
+                                             dst.data_ptr(), _sp(stream, src.device)), "mdet_vmc_select_rows")
+
+
+def vmc_r2(R, r2, stream=None):
+    _chk(load_library().mdet_vmc_r2(R.shape[0], R.shape[1], R.data_ptr(), r2.data_ptr(), _sp(stream, R.device)),
+         "mdet_vmc_r2")
+
+
+class MLP:
+    """The learned proposal's perceptron (3N -> H -> H -> 4N, tanh, BF16 weights, FP32 accumulation)."""
+
+    def __init__(self, device, n_elec, hidden=256, seed=1, mu_max=1.0, s0=-1.5, s_span=2.0, coord_scale=2.0,
+                 langevin=True, zero_head=True):
+        """langevin: moves take the Langevin form (mean R + mu + sigma^2 F, F the
+        drift at R); zero_head: the output layer starts at zero, so that the
+        untrained proposal is the drift-diffusion move with tau = exp(2 s0)
+        (langevin) or an isotropic Gaussian of scale exp(s0)."""
+        self._L = load_library()
+        h = C.c_void_p()
+        _chk(self._L.mdet_mlp_create(C.byref(h), int(device), int(n_elec), int(hidden), int(seed), float(mu_max),
+                                     float(s0), float(s_span), float(coord_scale)), "mdet_mlp_create")
+        self._h = h
+        self.device, self.n_elec, self.hidden = int(device), int(n_elec), int(hidden)
+        self.mu_max, self.s0, self.s_span, self.coord_scale = mu_max, s0, s_span, coord_scale
+        self.n_params = int(self._L.mdet_mlp_n_params(h))
+        self.langevin = bool(langevin)
+        if zero_head:
+            p = self.params()
+            n_in, H, n_out = 3 * self.n_elec, self.hidden, 4 * self.n_elec
+            p[n_in * H + H + H * H + H:] = 0.0
+            self.set_params(p)
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            self._L.mdet_mlp_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def params(self):
+        p = np.empty(self.n_params, np.float32)
+        _chk(self._L.mdet_mlp_get_params(self._h, _ptr(p)), "mdet_mlp_get_params")
+        return p
+
+    def set_params(self, p):
+        p = _c(p, np.float32)
+        _chk(self._L.mdet_mlp_set_params(self._h, _ptr(p)), "mdet_mlp_set_params")
+
+    def grads(self):
+        g = np.empty(self.n_params, np.float32)
+        _chk(self._L.mdet_mlp_get_grads(self._h, _ptr(g)), "mdet_mlp_get_grads")
+        return g
+
+    def forward(self, R, out=None, stream=None):
+        import torch
+        if out is None:
+            out = torch.empty(R.shape[0], 4 * self.n_elec, dtype=torch.float32, device=R.device)
+        _chk(self._L.mdet_mlp_forward(self._h, R.shape[0], R.data_ptr(), out.data_ptr(), _sp(stream, R.device)),
+             "mdet_mlp_forward")
+        return out
+
+    def backward(self, dout, stream=None):
+        _chk(self._L.mdet_mlp_backward(self._h, dout.shape[0], dout.data_ptr(), _sp(stream, dout.device)),
+             "mdet_mlp_backward")
+
+    def zero_grad(self, stream=None, device=None):
+        import torch
+        _chk(self._L.mdet_mlp_zero_grad(self._h, _sp(stream, torch.device("cuda", self.device))), "mdet_mlp_zero_grad")
+
+    def adam(self, lr, t, beta1=0.9, beta2=0.999, eps=1e-8, stream=None):
+        import torch
+        _chk(self._L.mdet_mlp_adam(self._h, float(lr), float(beta1), float(beta2), float(eps), int(t),
+                                   _sp(stream, torch.device("cuda", self.device))), "mdet_mlp_adam")
+
+    def nll_grad(self, R0, R1, out, dout, loss, stream=None):
+        _chk(self._L.mdet_mlp_nll_grad(self._h, R0.shape[0], R0.data_ptr(), R1.data_ptr(), out.data_ptr(),
+                                       dout.data_ptr(), loss.data_ptr(), _sp(stream, R0.device)), "mdet_mlp_nll_grad")
+
+    def esjd_grad(self, R, R_new, out, out_new, log_abs_psi, log_abs_psi_new, sign_new, drift, drift_new,
+                  grad_new, dout, dout_new, objective, jump_len2=0.0, speed_beta=0.0, stream=None):
+        """drift, drift_new: the drift arrays of the forward move and the reverse
+        density (e.g. limited); grad_new: grad Psi / Psi at R_new; objective: two
+        device doubles (J, mean acceptance); speed_beta > 0 selects the speed measure."""
+        lg = self.langevin
+        _chk(self._L.mdet_mlp_esjd_grad(self._h, R.shape[0], R.data_ptr(), R_new.data_ptr(), out.data_ptr(),
+                                        out_new.data_ptr(), log_abs_psi.data_ptr(), log_abs_psi_new.data_ptr(),
+                                        sign_new.data_ptr(), drift.data_ptr() if lg else None,
+                                        drift_new.data_ptr() if lg else None, grad_new.data_ptr(), int(lg),
+                                        float(jump_len2), float(speed_beta), dout.data_ptr(),
+                                        dout_new.data_ptr(), objective.data_ptr(), _sp(stream, R.device)),
+             "mdet_mlp_esjd_grad")
+
+    def propose(self, R, out, seed, step, R_new, log_q, drift=None, stream=None):
+        """drift: grad Psi / Psi at R, required for the Langevin form."""
+        if self.langevin and drift is None:
+            raise ValueError("the Langevin form needs the drift at R")
+        _chk(self._L.mdet_vmc_propose_mlp(self._h, R.shape[0], R.data_ptr(), out.data_ptr(),
+                                          drift.data_ptr() if self.langevin else None, int(seed), int(step),
+                                          R_new.data_ptr(), log_q.data_ptr(), _sp(stream, R.device)),
+             "mdet_vmc_propose_mlp")
+
+    def reverse(self, R, R_new, out_new, log_q, drift_new=None, stream=None):
+        """drift_new: grad Psi / Psi at R_new, required for the Langevin form."""
+        if self.langevin and drift_new is None:
+            raise ValueError("the Langevin form needs the drift at R_new")
+        _chk(self._L.mdet_vmc_reverse_mlp(self._h, R.shape[0], R.data_ptr(), R_new.data_ptr(), out_new.data_ptr(),
+                                          drift_new.data_ptr() if self.langevin else None, log_q.data_ptr(),
+                                          _sp(stream, R.device)), "mdet_vmc_reverse_mlp")
