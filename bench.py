@@ -29,7 +29,7 @@ FP64_PEAK_TFLOPS = 1.25     # nominal dense FP64 of one GB300 (recipe table); se
 CPU_SAMPLE_WALKERS = 96     # bounded oracle sample for the CPU baseline (~10-30 s of CPU work)
 # dram__bytes_read.sum + dram__bytes_write.sum of one k_spmm_wm launch on the 750k workload with
 # 8,192 walkers (ncu capture summarised in profiles/mixed_chlorine_like_750k.md)
-SPMM_TRAFFIC_750K = None
+SPMM_TRAFFIC_750K = 853.5e6
 
 
 def _env_int(k, d):
@@ -227,6 +227,10 @@ def run_ours(args):
         del out
     st = ctxs[primary].stats()
     main = results[primary]
+    # kernels per evaluation: orbitals, reference, ratios, 2 contractions, final per walker chunk,
+    # plus the 5 kernels of the stability fallback when it is enabled
+    fb_tol, fb_cap = ctxs[primary].fallback
+    st_launches = 6 * max(1, ctxs[primary].tuning()["walker_chunks"]) + (5 if fb_tol > 0 else 0)
 
     # end to end through the host-memory C-ABI call: H2D of R and D2H of all outputs per step
     ctx = ctxs[primary]
@@ -278,7 +282,7 @@ def run_ours(args):
             "clocks": main["clocks"],
             "e2e": {"value": W * world / (e2e_ms / 1e3), "unit": UNIT, "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms},
-            "gpu_launches": 6 * args.steps,
+            "gpu_launches": st_launches * args.steps,
             "kernels_ms": kern,
             "fallback_walkers": main["n_fb"],
             "roofline": roofline}
@@ -393,13 +397,15 @@ def run_learned(args):
     collect_s = time.perf_counter() - t0
     mlp = B.MLP(0, wl.n_elec, hidden=256, seed=3, mu_max=1.0, s0=0.5 * math.log(tau), s_span=3.0)
     t0 = time.perf_counter()
-    hist = train_esjd(mlp, ctx, R_data, lp_data, F_data, tau, epochs=3, batch=8192, lr=3e-4, speed_beta=0.1,
-                      target_acc=0.4)
+    hist = train_esjd(mlp, ctx, R_data, lp_data, F_data, tau, epochs=3, batch=8192, lr=1e-4, speed_beta=0.1,
+                      target_acc=0.5)
     torch.cuda.synchronize()
     train_s = time.perf_counter() - t0
     with ClockSampler(_gpu_index(0)) as clk:
-        base = measure_chain(ctx, R_eq, n_chain, tau, seed=5, warmup=args.warmup)
-        learned = measure_chain(ctx, R_eq, n_chain, tau, mlp=mlp, seed=6, warmup=args.warmup)
+        # the plain method: drift-diffusion without drift capping, tau at ~50 % acceptance
+        base = measure_chain(ctx, R_eq, n_chain, tau, seed=5, warmup=args.warmup, drift_a=0.0)
+        limited = measure_chain(ctx, R_eq, n_chain, tau, seed=5, warmup=args.warmup, drift_a=1.0)
+        learned = measure_chain(ctx, R_eq, n_chain, tau, mlp=mlp, seed=6, warmup=args.warmup, drift_a=1.0)
     line = {"metric": "autocorrelation-corrected samples/s of <E_L>, learned proposal vs drift-diffusion",
             "value": learned["samples_per_s"], "unit": "samples/s", "n_gpus": 1, "steps": n_chain,
             "warmup": args.warmup, "ms_per_step": learned["ms_per_step"], "higher_is_better": True,
@@ -408,8 +414,9 @@ def run_learned(args):
                        "tau": tau, "drift_limit_a": 1.0, "training_configs": int(R_data.shape[0]),
                        "mlp": "51-256-256-68 tanh, BF16 weights, FP32 accumulation",
                        "objective": "generalised speed measure, target acceptance 0.4"},
-            "learned": learned, "drift_diffusion": base,
+            "learned": learned, "drift_diffusion": base, "drift_diffusion_limited": limited,
             "gain": learned["samples_per_s"] / base["samples_per_s"],
+            "gain_vs_limited": learned["samples_per_s"] / limited["samples_per_s"],
             "training": {"collect_s": collect_s, "train_s": train_s,
                          "objective_acceptance_per_epoch": hist},
             "clocks": clk.summary()}

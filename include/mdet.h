@@ -184,8 +184,9 @@ mdet_status mdet_get_ratios(mdet_ctx* ctx, int64_t n_walk, double* r_up, double*
  * FP64, about 2^-47 double-float), cond_1(S_ref) = |S_ref|_1 |S_ref^-1|_1 of
  * its reference Slater matrix, and C the cancellation ratio (sum of |terms| /
  * max(|result|, rms over the walker's electrons)) of its gradient and Laplacian
- * sums, with the terms added in quadrature (mdet_get_error_estimates). A walker whose estimate exceeds tol (default 1e-6 for mixed, 1e-8 for
- * FP64 precision), or whose reference is singular, is re-evaluated on the GPU
+ * sums, with the terms added in quadrature (mdet_get_error_estimates). A walker
+ * whose estimate exceeds tol (default 1e-5 for mixed, 1e-6 for FP64
+ * precision), or whose reference is singular, is re-evaluated on the GPU
  * in FP64 by LU of every distinct determinant, its own contraction and
  * epilogue; its status gets MDET_WS_FALLBACK. At most max_walkers walkers per
  * evaluation are re-evaluated (default 64; the scratch grows with it);
@@ -194,6 +195,8 @@ mdet_status mdet_get_ratios(mdet_ctx* ctx, int64_t n_walk, double* r_up, double*
  */
 #define MDET_FALLBACK_MAX_SPIN 17
 mdet_status mdet_set_fallback(mdet_ctx* ctx, double tol, int max_walkers);
+/* The current fallback tolerance and walker cap (host pointers). */
+mdet_status mdet_get_fallback(const mdet_ctx* ctx, double* tol, int* max_walkers);
 
 /*
  * Walker chunking of the mixed-precision evaluation/*

@@ -80,6 +80,7 @@ def load_library(build_if_missing: bool = True):
     L.mdet_set_profiling.argtypes = [vp, i32]
     L.mdet_set_walker_chunks.argtypes = [vp, i32]
     L.mdet_set_fallback.argtypes = [vp, C.c_double, i32]
+    L.mdet_get_fallback.argtypes = [vp, vp, vp]
     L.mdet_get_error_estimates.argtypes = [vp, i64, vp, vp]
     L.mdet_selftest_df32.argtypes = [i32, i64, vp, vp, vp, vp]
     L.mdet_get_tuning.argtypes = [vp, C.POINTER(_Tuning)]
@@ -96,7 +97,7 @@ def load_library(build_if_missing: bool = True):
                  "mdet_evaluate_host", "mdet_get_ratios", "mdet_get_stats", "mdet_get_spin_dets",
                  "mdet_get_ci_matrix", "mdet_omega_sort", "mdet_set_profiling", "mdet_get_profile",
                  "mdet_psi_tilde_noalloc", "mdet_set_walker_chunks", "mdet_selftest_df32", "mdet_get_tuning",
-                 "mdet_set_tuning", "mdet_autotune", "mdet_batch_evaluate", "mdet_batch_create", "mdet_batch_launch", "mdet_set_fallback",
+                 "mdet_set_tuning", "mdet_autotune", "mdet_batch_evaluate", "mdet_batch_create", "mdet_batch_launch", "mdet_set_fallback", "mdet_get_fallback",
                  "mdet_get_error_estimates"):
         getattr(L, name).restype = i32
     # VMC moves and the learned proposal (include/mdet_vmc.h)
@@ -322,6 +323,13 @@ class Context:
     def set_fallback(self, tol, max_walkers=64):
         """Re-evaluate walkers whose estimated table error exceeds tol by full LU (tol <= 0: off)."""
         self._check(self._L.mdet_set_fallback(self._h, float(tol), int(max_walkers)), "mdet_set_fallback")
+
+    @property
+    def fallback(self):
+        """(tolerance, walker cap) of the stability fallback."""
+        tol, cap = C.c_double(), C.c_int()
+        self._check(self._L.mdet_get_fallback(self._h, C.byref(tol), C.byref(cap)), "mdet_get_fallback")
+        return tol.value, cap.value
 
     def error_estimates(self, n_walk):
         """cond_1 of the references [n_walk, 2] and the table error estimates [n_walk, 2] of the last evaluation."""

@@ -773,6 +773,13 @@ mdet_status mdet_set_fallback(mdet_ctx* c, double tol, int max_walkers) {
   return MDET_OK;
 }
 
+mdet_status mdet_get_fallback(const mdet_ctx* c, double* tol, int* max_walkers) {
+  if (!c || !tol || !max_walkers) return MDET_E_ARG;
+  *tol = c->fallback_tol;
+  *max_walkers = c->fallback_cap;
+  return MDET_OK;
+}
+
 mdet_status mdet_set_walker_chunks(mdet_ctx* c, int n_chunks) {
   if (!c || n_chunks < 0) return MDET_E_ARG;
   c->n_chunks_cfg = std::min(n_chunks, (int)mdet_ctx::kMaxChunks);
