@@ -366,6 +366,82 @@ def run_batched(args):
     batch.close()
 
 
+def run_truncation(args):
+    """Synthetic analogue of the paper's truncation table (Table 5) on the
+    750k-determinant expansion: for each threshold eps, norm-based truncation
+    (Sec. 3, eps_up = eps_dn = eps) against truncation by |c_k| that keeps the
+    same number of distinct spin determinants (the paper's measure of cost).
+    For each: products kept, distinct determinants, the retained share of
+    sum c^2 and walker-steps/s of one evaluation of 8,192 walkers (CUDA
+    events, L2 flushed between steps)."""
+    import numpy as np
+    import torch
+
+    import paper_1510_00730_gb300 as pkg
+    from paper_1510_00730_gb300 import synth
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    prec = {"mixed": pkg.PRECISION_MIXED, "fp64": pkg.PRECISION_FP64}[args.precision]
+    wl = synth.chlorine_like_750k()
+    R = torch.from_numpy(wl.R).to(dev)
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    total = float(np.sum(wl.ci_coef ** 2))
+
+    def timed(mask):
+        sub = synth.subset_products(wl, mask)
+        ctx = pkg.Context.from_workload(sub, device=0, precision=prec)
+        out = ctx.alloc_outputs(wl.n_walk)
+        for _ in range(args.warmup):
+            ctx.evaluate(R, out=out)
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+        for s in range(args.steps):
+            flush.fill_(float(s))
+            ev[s][0].record(stream)
+            ctx.evaluate(R, out=out)
+            ev[s][1].record(stream)
+        torch.cuda.synchronize()
+        ms = statistics.mean(a.elapsed_time(b) for a, b in ev)
+        ctx.close()
+        return ms
+
+    # distinct determinants of every |c|-ordered prefix: count first occurrences along the order
+    order = np.argsort(-np.abs(wl.ci_coef), kind="stable")
+    prefix = []
+    for D in (wl.det_up, wl.det_dn):
+        _, ids = np.unique(D, axis=0, return_inverse=True)
+        ids = ids.ravel()[order]
+        first = np.zeros(len(ids), bool)
+        _, pos = np.unique(ids, return_index=True)
+        first[pos] = True
+        prefix.append(np.cumsum(first))
+    rows = []
+    with ClockSampler(_gpu_index(0)) as clk:
+        full_ms = timed(np.ones(len(wl.ci_coef), bool))
+        for eps in (1e-7, 1e-8, 1e-9, 1e-10, 1e-11, 1e-12, 1e-13):
+            keep, _, _, cnt = pkg.truncate_norm(wl.det_up, wl.det_dn, wl.ci_coef, eps, eps)
+            # the longest |c| prefix whose distinct determinants do not exceed the norm truncation's
+            n_c = int(np.searchsorted(prefix[0] + prefix[1], cnt["up"] + cnt["dn"], side="right"))
+            cmask = np.zeros(len(order), bool)
+            cmask[order[:n_c]] = True
+            rows.append({"eps": eps,
+                         "norm": {"products": cnt["products"], "up": cnt["up"], "dn": cnt["dn"],
+                                  "norm_lost": 1.0 - float(np.sum(wl.ci_coef[keep] ** 2)) / total,
+                                  "walker_steps_per_s": wl.n_walk / (timed(keep) / 1e3)},
+                         "coef": {"products": n_c, "up": int(prefix[0][n_c - 1]), "dn": int(prefix[1][n_c - 1]),
+                                  "c_min": float(abs(wl.ci_coef[order[n_c - 1]])),
+                                  "norm_lost": 1.0 - float(np.sum(wl.ci_coef[cmask] ** 2)) / total,
+                                  "walker_steps_per_s": wl.n_walk / (timed(cmask) / 1e3)}})
+    line = {"metric": "walker-steps/s vs truncation threshold, norm-based vs |c| truncation (Table 5 analogue)",
+            "value": wl.n_walk / (full_ms / 1e3), "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": full_ms, "higher_is_better": True,
+            "dtype": "f64+f32x2" if prec == pkg.PRECISION_MIXED else "f64", "data": "synthetic",
+            "config": {"workload": "truncation_750k", "precision": args.precision, "walkers": wl.n_walk,
+                       "n_det": int(len(wl.ci_coef)), "l2": "flushed between timed steps"},
+            "rows": rows, "clocks": clk.summary()}
+    print(json.dumps(line), flush=True)
+
+
 def run_learned(args):
     """The learned Metropolis proposal on the chlorine-like 10^5-determinant
     expansion with 8,192 walkers: a chain of drift-diffusion moves (limited
@@ -449,6 +525,8 @@ def main():
         run_batched(args)
     elif args.workload == "learned_proposal_100k":
         run_learned(args)
+    elif args.workload == "truncation_750k":
+        run_truncation(args)
     else:
         run_ours(args)
 

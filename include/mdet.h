@@ -195,6 +195,31 @@ mdet_status mdet_get_ratios(mdet_ctx* ctx, int64_t n_walk, double* r_up, double*
  */
 #define MDET_FALLBACK_MAX_SPIN 17
 mdet_status mdet_set_fallback(mdet_ctx* ctx, double tol, int max_walkers);
+/*
+ * Norm-based truncation of a CI expansion (Sec. 3). Host call, no context.
+ * The expansion is given as products (det_up[k], det_dn[k], coef[k]), k < n_det,
+ * in the layout of mdet_set_ci_expansion (host pointers). The squared norm
+ * decomposes over the distinct spin determinants:
+ *   sum_k c_k^2 = sum_i N_i^up = sum_j N_j^dn,
+ * where N_i^up is the sum of c_k^2 over the products whose up determinant is
+ * D_i^up, and likewise for down. Every distinct determinant with
+ * N_i^up <= eps_up (N_j^dn <= eps_dn) is removed. All removals use the norms of
+ * the untruncated expansion, and every product that uses a removed determinant
+ * is dropped; the kept coefficients are not renormalised. eps < 0 removes
+ * nothing of that spin.
+ * Outputs, each nullable:
+ *  - keep[k] = 1 for a kept product, else 0;
+ *  - norm_up[k] / norm_dn[k] = the norms of product k's two determinants;
+ *  - counts[5] = {kept products, distinct up determinants in kept products,
+ *    distinct down determinants in kept products, distinct up determinants,
+ *    distinct down determinants}.
+ * Norms are summed with Neumaier compensation in product order.
+ * Errors: MDET_E_ARG for a negative n_det, n_int < 1 or null input arrays.
+ */
+mdet_status mdet_truncate_norm(int64_t n_det, int n_int, const uint64_t* det_up, const uint64_t* det_dn,
+                               const double* coef, double eps_up, double eps_dn, uint8_t* keep, double* norm_up,
+                               double* norm_dn, int64_t* counts);
+
 /* The current fallback tolerance and walker cap (host pointers). */
 mdet_status mdet_get_fallback(const mdet_ctx* ctx, double* tol, int* max_walkers);
 

@@ -76,6 +76,7 @@ def load_library(build_if_missing: bool = True):
     L.mdet_get_spin_dets.argtypes = [vp, i32, vp, vp, vp]
     L.mdet_get_ci_matrix.argtypes = [vp, vp, vp, vp]
     L.mdet_omega_sort.argtypes = [i64, i32, vp, vp]
+    L.mdet_truncate_norm.argtypes = [i64, i32, vp, vp, vp, C.c_double, C.c_double, vp, vp, vp, vp]
     L.mdet_psi_tilde_noalloc.argtypes = [vp, i64, vp, i64, vp, vp]
     L.mdet_set_profiling.argtypes = [vp, i32]
     L.mdet_set_walker_chunks.argtypes = [vp, i32]
@@ -95,7 +96,7 @@ def load_library(build_if_missing: bool = True):
     L.mdet_get_profile.argtypes = [vp, vp]
     for name in ("mdet_create", "mdet_set_system", "mdet_set_orbitals", "mdet_set_ci_expansion", "mdet_evaluate",
                  "mdet_evaluate_host", "mdet_get_ratios", "mdet_get_stats", "mdet_get_spin_dets",
-                 "mdet_get_ci_matrix", "mdet_omega_sort", "mdet_set_profiling", "mdet_get_profile",
+                 "mdet_get_ci_matrix", "mdet_omega_sort", "mdet_truncate_norm", "mdet_set_profiling", "mdet_get_profile",
                  "mdet_psi_tilde_noalloc", "mdet_set_walker_chunks", "mdet_selftest_df32", "mdet_get_tuning",
                  "mdet_set_tuning", "mdet_autotune", "mdet_batch_evaluate", "mdet_batch_create", "mdet_batch_launch", "mdet_set_fallback", "mdet_get_fallback",
                  "mdet_get_error_estimates"):
@@ -144,6 +145,29 @@ def _ptr(a) -> int:
 
 def _c(a, dt):
     return np.ascontiguousarray(a, dtype=dt)
+
+
+def truncate_norm(det_up, det_dn, coef, eps_up, eps_dn):
+    """Norm-based truncation (Sec. 3): remove the distinct spin determinants whose
+    share of the norm is <= eps_sigma (eps < 0: none) and every product using one.
+    Returns (keep [n_det] bool, norm_up [n_det], norm_dn [n_det], counts) with
+    counts = dict(products, up, dn, up_all, dn_all)."""
+    L = load_library()
+    du, dd = _c(det_up, np.uint64), _c(det_dn, np.uint64)
+    if du.ndim == 1:
+        du, dd = du[:, None], dd[:, None]
+    cf = _c(coef, np.float64)
+    n = cf.shape[0]
+    if du.shape != dd.shape or du.shape[0] != n:
+        raise ValueError("det_up, det_dn and coef disagree in length")
+    keep = np.empty(n, np.uint8)
+    nu, nd = np.empty(n), np.empty(n)
+    cnt = np.empty(5, np.int64)
+    st = L.mdet_truncate_norm(n, du.shape[1], _ptr(du), _ptr(dd), _ptr(cf), float(eps_up), float(eps_dn),
+                              _ptr(keep), _ptr(nu), _ptr(nd), _ptr(cnt))
+    if st:
+        raise MdetError(st, "mdet_truncate_norm failed")
+    return keep.astype(bool), nu, nd, dict(zip(("products", "up", "dn", "up_all", "dn_all"), cnt.tolist()))
 
 
 def omega_sort(dets) -> np.ndarray:

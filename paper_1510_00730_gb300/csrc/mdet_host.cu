@@ -620,6 +620,71 @@ mdet_status mdet_set_ci_expansion(mdet_ctx* c, int64_t n_det, int n_int, const u
   return MDET_OK;
 }
 
+mdet_status mdet_truncate_norm(int64_t n_det, int n_int, const uint64_t* det_up, const uint64_t* det_dn,
+                               const double* coef, double eps_up, double eps_dn, uint8_t* keep, double* norm_up,
+                               double* norm_dn, int64_t* counts) {
+  if (n_det < 0 || n_int < 1 || (n_det > 0 && (!det_up || !det_dn || !coef))) return MDET_E_ARG;
+  const uint64_t* in[2] = {det_up, det_dn};
+  const double eps[2] = {eps_up, eps_dn};
+  double* norm_out[2] = {norm_up, norm_dn};
+  std::vector<int64_t> dist_of[2];  // product -> index of its distinct determinant (omega order)
+  std::vector<uint8_t> removed[2];
+  int64_t n_all[2] = {0, 0};
+  for (int sp = 0; sp < 2; sp++) {
+    const uint64_t* D = in[sp];
+    // distinct determinants (Sec. 2.1 sort by the key of Eq. 3), then the norm of each (Sec. 3):
+    // N_i = sum of c_k^2 over the products whose spin-sp determinant is D_i
+    std::vector<int64_t> ord = omega_order(n_det, n_int, D);
+    dist_of[sp].assign(n_det, 0);
+    std::vector<double> sum, comp;
+    for (int64_t q = 0; q < n_det; q++) {
+      if (q == 0 || cmp_det(D + ord[q] * n_int, D + ord[q - 1] * n_int, n_int) != 0) {
+        sum.push_back(0.0);
+        comp.push_back(0.0);
+      }
+      dist_of[sp][ord[q]] = (int64_t)sum.size() - 1;
+    }
+    // Neumaier summation in product order (deterministic whatever the sort did with equal keys)
+    for (int64_t k = 0; k < n_det; k++) {
+      const int64_t i = dist_of[sp][k];
+      const double x = coef[k] * coef[k], t = sum[i] + x;
+      comp[i] += std::fabs(sum[i]) >= std::fabs(x) ? (sum[i] - t) + x : (x - t) + sum[i];
+      sum[i] = t;
+    }
+    n_all[sp] = (int64_t)sum.size();
+    removed[sp].assign(sum.size(), 0);
+    for (size_t i = 0; i < sum.size(); i++) {
+      sum[i] += comp[i];
+      removed[sp][i] = eps[sp] >= 0.0 && sum[i] <= eps[sp];
+    }
+    if (norm_out[sp])
+      for (int64_t k = 0; k < n_det; k++) norm_out[sp][k] = sum[dist_of[sp][k]];
+  }
+  // a product survives when neither of its determinants was removed (all removals use the
+  // norms of the untruncated expansion; no renormalisation)
+  int64_t n_keep = 0;
+  std::vector<uint8_t> used[2] = {std::vector<uint8_t>(n_all[0], 0), std::vector<uint8_t>(n_all[1], 0)};
+  for (int64_t k = 0; k < n_det; k++) {
+    const bool kk = !removed[0][dist_of[0][k]] && !removed[1][dist_of[1][k]];
+    if (keep) keep[k] = kk ? 1 : 0;
+    if (kk) {
+      n_keep++;
+      used[0][dist_of[0][k]] = 1;
+      used[1][dist_of[1][k]] = 1;
+    }
+  }
+  if (counts) {
+    counts[0] = n_keep;
+    for (int sp = 0; sp < 2; sp++) {
+      int64_t u = 0;
+      for (uint8_t x : used[sp]) u += x;
+      counts[1 + sp] = u;
+      counts[3 + sp] = n_all[sp];
+    }
+  }
+  return MDET_OK;
+}
+
 mdet_status mdet_evaluate(mdet_ctx* c, int64_t n_walk, const double* R, double* log_abs_psi, int8_t* sign,
                           double* grad, double* lap, double* e_local, uint32_t* status, void* stream) {
   if (!c) return MDET_E_ARG;

@@ -304,6 +304,15 @@ def batched_uneven(n_exp=64, seed=151000734, walkers=(256, 4096), n_det_range=(1
     return out
 
 
+def subset_products(wl, mask):
+    """The same system with only the products selected by the boolean mask (e.g.
+    a truncation's keep mask); walkers and orbitals are shared."""
+    import dataclasses
+    mask = np.asarray(mask, dtype=bool)
+    return dataclasses.replace(wl, name=wl.name + "_subset", det_up=wl.det_up[mask], det_dn=wl.det_dn[mask],
+                               ci_coef=wl.ci_coef[mask], meta=dict(wl.meta, subset_of=wl.name))
+
+
 WORKLOADS = {
     "oxygen_like_1k": oxygen_like_1k,
     "chlorine_like_100k": chlorine_like_100k,
