@@ -137,6 +137,23 @@ mdet_status mdet_set_ci_expansion(mdet_ctx* ctx, int64_t n_det, int n_int,
                                   const double* coef);
 
 /*
+ * The same expansion and preprocessing with the O(N_det) steps on the GPU:
+ * validation, the sort of each spin list by the key of Eq. 3 (ties broken by
+ * the words from the last to the first, original order among identical
+ * determinants), removal of duplicates, the product -> distinct determinant
+ * map, the reference product and C in column-major and row-major order with
+ * segment pointers. The steps per distinct determinant (excitation records,
+ * degree grouping) run on the host, as in mdet_set_ci_expansion. The resulting
+ * context state is identical to mdet_set_ci_expansion's. det_up, det_dn, coef:
+ * DEVICE arrays of the context's device in the same layout, only read; the
+ * call is synchronous on `stream`. Fails like mdet_set_ci_expansion, also with
+ * MDET_E_INPUT for a non-finite coefficient, and with MDET_E_NODEVICE on a
+ * context without a device.
+ */
+mdet_status mdet_set_ci_expansion_device(mdet_ctx* ctx, int64_t n_det, int n_int, const uint64_t* det_up,
+                                         const uint64_t* det_dn, const double* coef, void* stream);
+
+/*
  * One evaluation of the hot path for n_walk walkers (Sec. 2.2-2.4): orbitals,
  * reference LU per spin, ratio tables, per-determinant ratios and their
  * derivative contributions, the sparse bilinear contraction, and the

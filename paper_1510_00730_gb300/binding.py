@@ -76,6 +76,7 @@ def load_library(build_if_missing: bool = True):
     L.mdet_get_spin_dets.argtypes = [vp, i32, vp, vp, vp]
     L.mdet_get_ci_matrix.argtypes = [vp, vp, vp, vp]
     L.mdet_omega_sort.argtypes = [i64, i32, vp, vp]
+    L.mdet_set_ci_expansion_device.argtypes = [vp, i64, i32, vp, vp, vp, vp]
     L.mdet_truncate_norm.argtypes = [i64, i32, vp, vp, vp, C.c_double, C.c_double, vp, vp, vp, vp]
     L.mdet_psi_tilde_noalloc.argtypes = [vp, i64, vp, i64, vp, vp]
     L.mdet_set_profiling.argtypes = [vp, i32]
@@ -96,7 +97,7 @@ def load_library(build_if_missing: bool = True):
     L.mdet_get_profile.argtypes = [vp, vp]
     for name in ("mdet_create", "mdet_set_system", "mdet_set_orbitals", "mdet_set_ci_expansion", "mdet_evaluate",
                  "mdet_evaluate_host", "mdet_get_ratios", "mdet_get_stats", "mdet_get_spin_dets",
-                 "mdet_get_ci_matrix", "mdet_omega_sort", "mdet_truncate_norm", "mdet_set_profiling", "mdet_get_profile",
+                 "mdet_get_ci_matrix", "mdet_omega_sort", "mdet_truncate_norm", "mdet_set_ci_expansion_device", "mdet_set_profiling", "mdet_get_profile",
                  "mdet_psi_tilde_noalloc", "mdet_set_walker_chunks", "mdet_selftest_df32", "mdet_get_tuning",
                  "mdet_set_tuning", "mdet_autotune", "mdet_batch_evaluate", "mdet_batch_create", "mdet_batch_launch", "mdet_set_fallback", "mdet_get_fallback",
                  "mdet_get_error_estimates"):
@@ -245,17 +246,36 @@ class Context:
         self._check(self._L.mdet_set_orbitals(self._h, l_.shape[0], _ptr(l_), _ptr(c_), _ptr(n_), _ptr(a_), _ptr(k_),
                                               mo.shape[1], _ptr(mo_cm)), "mdet_set_orbitals")
 
-    def set_ci_expansion(self, det_up, det_dn, coef):
+    def set_ci_expansion(self, det_up, det_dn, coef, on_device=False):
+        """The CI expansion and its preprocessing; on_device runs the O(N_det)
+        steps on the GPU (mdet_set_ci_expansion_device; torch tensors on the
+        context's device are used in place, host arrays are copied there)."""
+        if on_device:
+            import torch
+            dev = torch.device("cuda", self.device)
+            def words(a):  # 64-bit words in place; torch has no general uint64, so move them as int64 bits
+                if isinstance(a, torch.Tensor):
+                    return a.to(dev).contiguous()
+                return torch.from_numpy(np.ascontiguousarray(a, np.uint64).view(np.int64)).to(dev)
+
+            du, dd = words(det_up), words(det_dn)
+            cf = torch.as_tensor(coef, dtype=torch.float64, device=dev).contiguous()
+            if du.dim() == 1:
+                du, dd = du[:, None].contiguous(), dd[:, None].contiguous()
+            self._check(self._L.mdet_set_ci_expansion_device(self._h, cf.shape[0], du.shape[1], du.data_ptr(),
+                                                             dd.data_ptr(), cf.data_ptr(), _sp(None, dev)),
+                        "mdet_set_ci_expansion_device")
+            return
         du, dd, cf = _c(det_up, np.uint64), _c(det_dn, np.uint64), _c(coef, np.float64)
         self._check(self._L.mdet_set_ci_expansion(self._h, cf.shape[0], du.shape[1], _ptr(du), _ptr(dd), _ptr(cf)),
                     "mdet_set_ci_expansion")
 
     @classmethod
-    def from_workload(cls, wl, device=0, precision=PRECISION_FP64):
+    def from_workload(cls, wl, device=0, precision=PRECISION_FP64, on_device=False):
         ctx = cls(device, precision)
         ctx.set_system(wl.n_up, wl.n_dn, wl.Z, wl.nuc_xyz)
         ctx.set_orbitals(wl.shell_l, wl.shell_center, wl.shell_nprim, wl.alpha, wl.coef, wl.mo_coef)
-        ctx.set_ci_expansion(wl.det_up, wl.det_dn, wl.ci_coef)
+        ctx.set_ci_expansion(wl.det_up, wl.det_dn, wl.ci_coef, on_device=on_device)
         return ctx
 
     # -- evaluation ---------------------------------------------------------

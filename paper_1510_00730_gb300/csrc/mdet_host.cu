@@ -205,6 +205,66 @@ void free_scratch(mdet_ctx* c) {
 }
 
 // Upload everything the kernels read (called once the expansion is complete).
+// Host step shared by both preprocessing paths. From the distinct determinants
+// of one spin in omega order (udets [nu][n_int]) and the omega index of the
+// reference: excitation degrees relative to the reference, the context order
+// (reference first, then by degree, omega order within a degree), the
+// excitation records with their phases, and ctx_of[omega index] = context index.
+mdet_status spin_tables(mdet_ctx* c, int sp, int n_int, const std::vector<uint64_t>& udets, int64_t iref,
+                        std::vector<int32_t>& ctx_of) {
+  const int64_t nu = (int64_t)(udets.size() / n_int);
+  const uint64_t* ref = udets.data() + iref * n_int;
+  std::vector<int> deg(nu);
+  for (int64_t i = 0; i < nu; i++) {
+    const uint64_t* w = udets.data() + i * n_int;
+    int h = 0;
+    for (int q = 0; q < n_int; q++) h += __builtin_popcountll(ref[q] & ~w[q]);
+    deg[i] = h;
+    if (h > kMaxExc)
+      return fail(c, MDET_E_INPUT, "spin %d determinant is a degree-%d excitation of the reference (max %d)", sp, h,
+                  kMaxExc);
+  }
+  std::vector<int64_t> order;
+  order.reserve(nu);
+  order.push_back(iref);
+  for (int d = 1; d <= kMaxExc; d++)
+    for (int64_t i = 0; i < nu; i++)
+      if (deg[i] == d && i != iref) order.push_back(i);
+  ctx_of.assign(nu, 0);
+  for (int64_t t = 0; t < nu; t++) ctx_of[order[t]] = (int32_t)t;
+  std::vector<int> rocc = decode_occ(ref, n_int);
+  c->ref_occ[sp] = rocc;
+  c->dets[sp].assign((size_t)nu * n_int, 0);
+  c->degree[sp].assign(nu, 0);
+  c->exc[sp].assign(nu, Exc{});
+  for (int64_t t = 0; t < nu; t++) {
+    const uint64_t* w = udets.data() + order[t] * n_int;
+    std::copy(w, w + n_int, c->dets[sp].begin() + t * n_int);
+    Exc e{};
+    std::vector<int> cols = rocc;  // reference columns with holes replaced by particles
+    int k = 0, kp = 0;
+    for (size_t a = 0; a < rocc.size(); a++) {
+      int m = rocc[a];
+      if (!((w[m / 64] >> (m % 64)) & 1ULL)) e.h[k++] = (uint8_t)a;
+    }
+    for (int q = 0; q < n_int; q++) {
+      uint64_t part = w[q] & ~ref[q];
+      while (part) {
+        int b = __builtin_ctzll(part);
+        part &= part - 1;
+        e.p[kp++] = (uint8_t)(64 * q + b);
+      }
+    }
+    if (k != kp) return fail(c, MDET_E_INPUT, "internal: hole/particle count mismatch");
+    for (int a = 0; a < k; a++) cols[e.h[a]] = e.p[a];
+    e.k = (uint8_t)k;
+    e.eps = (int8_t)sort_parity(cols);
+    c->exc[sp][t] = e;
+    c->degree[sp][t] = k;
+  }
+  return MDET_OK;
+}
+
 mdet_status upload_problem(mdet_ctx* c) {
   if (c->device < 0) return MDET_OK;
   CUDA_TRY(c, cudaSetDevice(c->device));
@@ -488,6 +548,8 @@ mdet_status mdet_set_ci_expansion(mdet_ctx* c, int64_t n_det, int n_int, const u
       if (top < 64 && (w[n_int - 1] >> top) != 0)
         return fail(c, MDET_E_INPUT, "product %lld: spin %d determinant occupies an MO >= n_mo", (long long)k, sp);
     }
+  for (int64_t k = 0; k < n_det; k++)
+    if (!std::isfinite(coef[k])) return fail(c, MDET_E_INPUT, "product %lld: coefficient is not finite", (long long)k);
   // reference product: the largest |c_k| (first one on ties)
   int64_t kref = 0;
   for (int64_t k = 1; k < n_det; k++)
@@ -512,61 +574,13 @@ mdet_status mdet_set_ci_expansion(mdet_ctx* c, int64_t n_det, int n_int, const u
       }
       pos[k] = (int32_t)lo;
     }
-    // reference determinant and excitation degrees relative to it
-    const int64_t iref = pos[kref];
-    const uint64_t* ref = D + uniq[iref] * n_int;
-    std::vector<int> deg(nu);
-    for (int64_t i = 0; i < nu; i++) {
-      const uint64_t* w = D + uniq[i] * n_int;
-      int h = 0;
-      for (int q = 0; q < n_int; q++) h += __builtin_popcountll(ref[q] & ~w[q]);
-      deg[i] = h;
-      if (h > kMaxExc)
-        return fail(c, MDET_E_INPUT, "spin %d determinant is a degree-%d excitation of the reference (max %d)", sp,
-                    h, kMaxExc);
-    }
-    // context order: reference first, then by degree, omega order within a degree (stable counting sort)
-    std::vector<int64_t> order;
-    order.reserve(nu);
-    order.push_back(iref);
-    for (int d = 1; d <= kMaxExc; d++)
-      for (int64_t i = 0; i < nu; i++)
-        if (deg[i] == d && i != iref) order.push_back(i);
-    std::vector<int32_t> ctx_of(nu);
-    for (int64_t t = 0; t < nu; t++) ctx_of[order[t]] = (int32_t)t;
+    std::vector<uint64_t> udets((size_t)nu * n_int);
+    for (int64_t i = 0; i < nu; i++) std::copy(D + uniq[i] * n_int, D + (uniq[i] + 1) * n_int, udets.begin() + i * n_int);
+    std::vector<int32_t> ctx_of;
+    mdet_status st = spin_tables(c, sp, n_int, udets, pos[kref], ctx_of);
+    if (st != MDET_OK) return st;
     idx_of[sp].resize(n_det);
     for (int64_t k = 0; k < n_det; k++) idx_of[sp][k] = ctx_of[pos[k]];
-    // excitation records
-    std::vector<int> rocc = decode_occ(ref, n_int);
-    c->ref_occ[sp] = rocc;
-    c->dets[sp].assign((size_t)nu * n_int, 0);
-    c->degree[sp].assign(nu, 0);
-    c->exc[sp].assign(nu, Exc{});
-    for (int64_t t = 0; t < nu; t++) {
-      const uint64_t* w = D + uniq[order[t]] * n_int;
-      std::copy(w, w + n_int, c->dets[sp].begin() + t * n_int);
-      Exc e{};
-      std::vector<int> cols = rocc;  // reference columns with holes replaced by particles
-      int k = 0, kp = 0;
-      for (size_t a = 0; a < rocc.size(); a++) {
-        int m = rocc[a];
-        if (!((w[m / 64] >> (m % 64)) & 1ULL)) e.h[k++] = (uint8_t)a;
-      }
-      for (int q = 0; q < n_int; q++) {
-        uint64_t part = w[q] & ~ref[q];
-        while (part) {
-          int b = __builtin_ctzll(part);
-          part &= part - 1;
-          e.p[kp++] = (uint8_t)(64 * q + b);
-        }
-      }
-      if (k != kp) return fail(c, MDET_E_INPUT, "internal: hole/particle count mismatch");
-      for (int a = 0; a < k; a++) cols[e.h[a]] = e.p[a];
-      e.k = (uint8_t)k;
-      e.eps = (int8_t)sort_parity(cols);
-      c->exc[sp][t] = e;
-      c->degree[sp][t] = k;
-    }
   }
   // C in the paper's column-major order: radix sort of N_up * j + i
   const int64_t nup = (int64_t)c->exc[0].size(), ndn = (int64_t)c->exc[1].size();
@@ -614,6 +628,55 @@ mdet_status mdet_set_ci_expansion(mdet_ctx* c, int64_t n_det, int n_int, const u
   c->n_det = n_det;
   c->n_int = n_int;
   mdet_status s = upload_problem(c);
+  if (s != MDET_OK) return s;
+  c->has_ci = true;
+  c->err.clear();
+  return MDET_OK;
+}
+
+mdet_status mdet_set_ci_expansion_device(mdet_ctx* c, int64_t n_det, int n_int, const uint64_t* det_up,
+                                         const uint64_t* det_dn, const double* coef, void* stream) {
+  if (!c) return MDET_E_ARG;
+  if (!c->has_system || !c->has_orbitals) return fail(c, MDET_E_STATE, "set_system and set_orbitals must come first");
+  if (c->device < 0) return fail(c, MDET_E_NODEVICE, "device preprocessing needs a context with a device");
+  if (n_det < 1 || !det_up || !det_dn || !coef) return fail(c, MDET_E_ARG, "empty expansion or null pointer");
+  if (n_det >= (int64_t)1 << 31) return fail(c, MDET_E_ARG, "n_det must be below 2^31");
+  const int want_int = (c->n_mo + 63) / 64;
+  if (final_smem_bytes_host(c->n_up, c->n_dn, c->n_mo, c->precision == MDET_PRECISION_MIXED) > 227 * 1024)
+    return fail(c, MDET_E_ARG, "(n_up + n_dn) * n_mo too large for the per-walker epilogue (shared memory)");
+  if (n_int != want_int) return fail(c, MDET_E_ARG, "n_int=%d but ceil(n_mo/64)=%d", n_int, want_int);
+  CUDA_TRY(c, cudaSetDevice(c->device));
+  c->has_ci = false;
+  cudaStream_t st = (cudaStream_t)stream;
+  PreDevice* h = nullptr;
+  PreSpin spin[2];
+  std::string msg;
+  mdet_status s = pre_distinct(&h, n_det, n_int, det_up, det_dn, coef, c->n_up, c->n_dn, c->n_mo, st, spin, &msg);
+  if (s != MDET_OK) {
+    pre_free(h);
+    return fail(c, s, "%s", msg.c_str());
+  }
+  std::vector<int32_t> ctx_of[2];
+  for (int sp = 0; sp < 2 && s == MDET_OK; sp++) s = spin_tables(c, sp, n_int, spin[sp].udets, spin[sp].iref, ctx_of[sp]);
+  if (s != MDET_OK) {
+    pre_free(h);
+    return s;
+  }
+  PreC C;
+  s = pre_build_c(h, ctx_of, (int64_t)c->exc[0].size(), (int64_t)c->exc[1].size(), st, &C, &msg);
+  pre_free(h);
+  if (s != MDET_OK) return fail(c, s, "%s", msg.c_str());
+  c->coo_row = std::move(C.csc_row);
+  c->coo_col = std::move(C.csc_col);
+  c->coo_val = std::move(C.csc_val);
+  c->csr_row = std::move(C.csr_row);
+  c->csr_col = std::move(C.csr_col);
+  c->csr_val = std::move(C.csr_val);
+  c->csr_ptr = std::move(C.csr_ptr);
+  c->csc_ptr = std::move(C.csc_ptr);
+  c->n_det = n_det;
+  c->n_int = n_int;
+  s = upload_problem(c);
   if (s != MDET_OK) return s;
   c->has_ci = true;
   c->err.clear();

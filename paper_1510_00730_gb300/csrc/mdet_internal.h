@@ -3,6 +3,9 @@
 #pragma once
 
 #include <cstdint>
+#include <string>
+#include <vector>
+
 #include <cuda_runtime.h>
 
 #include "../../include/mdet.h"
@@ -122,5 +125,34 @@ size_t final_smem_bytes(const DevProblem& P, bool mixed);
 cudaError_t launch_final(const DevProblem& P, const DevScratch& S, int64_t n_walk, const double* R,
                          double* log_abs_psi, int8_t* sign, double* grad, double* lap, double* e_local,
                          uint32_t* status, bool mixed, cudaStream_t st);
+
+// ---- expansion preprocessing on the GPU (mdet_preprocess.cu), Sec. 2.1 ----
+// Results of the O(N_det) steps for one spin: the distinct determinants in the
+// order of the key of Eq. 3 ([nu][n_int]) and the position of the reference.
+struct PreSpin {
+  std::vector<uint64_t> udets;
+  int64_t iref = 0;
+};
+struct PreDevice;  // device buffers kept between the two calls below
+// The C arrays in both orders and their segment pointers, as built on the host.
+struct PreC {
+  std::vector<int32_t> csc_row, csc_col, csr_row, csr_col, csr_ptr, csc_ptr;
+  std::vector<double> csc_val, csr_val;
+};
+// Validates both spin lists (popcount, bits beyond n_mo) and the coefficients
+// (finite), sorts each list by the key of Eq. 3 with ties broken by the words
+// from the last to the first (stable), removes duplicates, maps every product to
+// its distinct determinant and finds the reference product (largest |c|, first
+// on ties). Inputs are device arrays. Returns MDET_OK, MDET_E_INPUT (msg says
+// which product) or MDET_E_CUDA.
+mdet_status pre_distinct(PreDevice** h, int64_t n, int n_int, const uint64_t* det_up, const uint64_t* det_dn,
+                         const double* coef, int n_up, int n_dn, int n_mo, cudaStream_t st, PreSpin out[2],
+                         std::string* msg);
+// From ctx_of (distinct index -> context index) of both spins: C sorted by
+// (column, row) and by (row, column), the duplicate-pair check and the segment
+// pointers, copied to the host.
+mdet_status pre_build_c(PreDevice* h, const std::vector<int32_t> ctx_of[2], int64_t nup, int64_t ndn,
+                        cudaStream_t st, PreC* out, std::string* msg);
+void pre_free(PreDevice* h);
 
 }  // namespace mdet
