@@ -442,6 +442,64 @@ def run_truncation(args):
     print(json.dumps(line), flush=True)
 
 
+def run_sm_chain(args):
+    """The paper's sequential Sherman-Morrison chain (Sec. 2.2) against the
+    table method on the 750k expansion (8,192 walkers, FP64 orbitals of one
+    evaluation): ms per step for the chain (both spins) and for the table
+    method's reference + ratio stages, the chain's N_inv and N_subst per
+    walker-step (Table 3), and the relative difference of the two sets of ratios
+    on 64 sampled walkers."""
+    import numpy as np
+    import torch
+
+    import paper_1510_00730_gb300 as pkg
+    from paper_1510_00730_gb300 import synth
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    wl = synth.chlorine_like_750k()
+    ctx = pkg.Context.from_workload(wl, device=0, precision=pkg.PRECISION_FP64)
+    R = torch.from_numpy(wl.R).to(dev)
+    out = ctx.alloc_outputs(wl.n_walk)
+    ctx.set_profiling(True)
+    stream = torch.cuda.current_stream(dev)
+    stages = []
+    for s in range(args.warmup + args.steps):
+        ctx.evaluate(R, out=out)
+        torch.cuda.synchronize()
+        if s >= args.warmup:
+            stages.append(ctx.profile())
+    table_ms = statistics.mean(p["reference"] + p["ratios"] for p in stages)
+    ev = []
+    with ClockSampler(_gpu_index(0)) as clk:
+        for s in range(args.warmup + args.steps):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            r, n_inv, n_subst = ctx.sm_chain(wl.n_walk)
+            b.record(stream)
+            if s >= args.warmup:
+                ev.append((a, b))
+        torch.cuda.synchronize()
+    chain_ms = statistics.mean(a.elapsed_time(b) for a, b in ev)
+    st = ctx.stats()
+    r_up, r_dn, _, _ = ctx.ratios(wl.n_walk)
+    table = np.concatenate([r_up, r_dn], axis=1)
+    chain = r.cpu().numpy()[:, :wl.n_walk].T
+    idx = np.arange(0, wl.n_walk, wl.n_walk // 64)
+    diff = np.abs(chain[idx] - table[idx]) / np.maximum(np.abs(table[idx]), 1.0)
+    line = {"metric": "ms per step of the determinant ratios: sequential Sherman-Morrison chain vs table method",
+            "value": chain_ms, "unit": "ms", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": chain_ms, "higher_is_better": False, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "sm_chain_750k", "walkers": wl.n_walk, "n_det_up": st["n_det_up"],
+                       "n_det_dn": st["n_det_dn"], "threshold": 1e-3},
+            "table_ms": table_ms, "chain_over_table": chain_ms / table_ms,
+            "n_inv": float(n_inv.double().mean()), "n_subst": float(n_subst.double().mean()),
+            "ratio_difference": {"p50": float(np.median(diff)), "p99": float(np.percentile(diff, 99)),
+                                 "max": float(diff.max())},
+            "clocks": clk.summary()}
+    print(json.dumps(line), flush=True)
+    ctx.close()
+
+
 def run_learned(args):
     """The learned Metropolis proposal on the chlorine-like 10^5-determinant
     expansion with 8,192 walkers: a chain of drift-diffusion moves (limited
@@ -527,6 +585,8 @@ def main():
         run_learned(args)
     elif args.workload == "truncation_750k":
         run_truncation(args)
+    elif args.workload == "sm_chain_750k":
+        run_sm_chain(args)
     else:
         run_ours(args)
 

@@ -137,6 +137,28 @@ mdet_status mdet_set_ci_expansion(mdet_ctx* ctx, int64_t n_det, int n_int,
                                   const double* coef);
 
 /*
+ * The paper's own route to the determinant values (Sec. 2.2), for comparison
+ * with the table method of mdet_evaluate. For every walker and spin the
+ * distinct determinants are visited in the order of the key of Eq. 3. The
+ * first one is inverted in full (Gauss-Jordan, partial pivoting). Each next
+ * one is reached from its predecessor by in-place Sherman-Morrison column
+ * substitutions (Eq. 4), one column at a time, holes and particles paired in
+ * ascending order. A substitution with |ratio| < 1e-3 is deferred and retried
+ * after the others; a round that applies none of the remaining ones cancels the
+ * updates and the determinant is inverted in full. All in FP64, on the orbital
+ * values of the last mdet_evaluate of this context (n_walk at most its walker
+ * count). Outputs (device): r [n_det_up + n_det_dn][ld] walker-minor, the
+ * ratios D_I / D_ref in the context's order (mdet_get_spin_dets) relative to
+ * that evaluation's reference determinants; n_inv, n_subst [n_walk]: full
+ * inversions and applied substitutions over both spins (Table 3's N_inv and
+ * N_subst). Asynchronous on `stream` (waits for the evaluation's stream if it
+ * differs). Errors: MDET_E_STATE without an expansion or for too many walkers,
+ * MDET_E_ARG for null outputs or ld < n_walk.
+ */
+mdet_status mdet_sm_chain(mdet_ctx* ctx, int64_t n_walk, double* r, int64_t ld, int32_t* n_inv, int32_t* n_subst,
+                          void* stream);
+
+/*
  * The same expansion and preprocessing with the O(N_det) steps on the GPU:
  * validation, the sort of each spin list by the key of Eq. 3 (ties broken by
  * the words from the last to the first, original order among identical

@@ -76,6 +76,7 @@ def load_library(build_if_missing: bool = True):
     L.mdet_get_spin_dets.argtypes = [vp, i32, vp, vp, vp]
     L.mdet_get_ci_matrix.argtypes = [vp, vp, vp, vp]
     L.mdet_omega_sort.argtypes = [i64, i32, vp, vp]
+    L.mdet_sm_chain.argtypes = [vp, i64, vp, i64, vp, vp, vp]
     L.mdet_set_ci_expansion_device.argtypes = [vp, i64, i32, vp, vp, vp, vp]
     L.mdet_truncate_norm.argtypes = [i64, i32, vp, vp, vp, C.c_double, C.c_double, vp, vp, vp, vp]
     L.mdet_psi_tilde_noalloc.argtypes = [vp, i64, vp, i64, vp, vp]
@@ -97,7 +98,7 @@ def load_library(build_if_missing: bool = True):
     L.mdet_get_profile.argtypes = [vp, vp]
     for name in ("mdet_create", "mdet_set_system", "mdet_set_orbitals", "mdet_set_ci_expansion", "mdet_evaluate",
                  "mdet_evaluate_host", "mdet_get_ratios", "mdet_get_stats", "mdet_get_spin_dets",
-                 "mdet_get_ci_matrix", "mdet_omega_sort", "mdet_truncate_norm", "mdet_set_ci_expansion_device", "mdet_set_profiling", "mdet_get_profile",
+                 "mdet_get_ci_matrix", "mdet_omega_sort", "mdet_truncate_norm", "mdet_sm_chain", "mdet_set_ci_expansion_device", "mdet_set_profiling", "mdet_get_profile",
                  "mdet_psi_tilde_noalloc", "mdet_set_walker_chunks", "mdet_selftest_df32", "mdet_get_tuning",
                  "mdet_set_tuning", "mdet_autotune", "mdet_batch_evaluate", "mdet_batch_create", "mdet_batch_launch", "mdet_set_fallback", "mdet_get_fallback",
                  "mdet_get_error_estimates"):
@@ -403,6 +404,22 @@ class Context:
                     n_det_up=s.n_det_up, n_det_dn=s.n_det_dn, max_degree=list(s.max_degree),
                     degree_hist=[list(s.degree_hist[0]), list(s.degree_hist[1])],
                     precision=s.precision, device=s.device)
+
+    def sm_chain(self, n_walk, stream=None):
+        """Ratios D_I / D_ref by the paper's sequential Sherman-Morrison chain
+        (mdet_sm_chain) on the orbitals of the last evaluation. Returns device
+        tensors r [n_det_up + n_det_dn][ld] (walker-minor, ld = n_walk rounded up
+        to 256), n_inv [n_walk], n_subst [n_walk]."""
+        import torch
+        dev = torch.device("cuda", self.device)
+        st = self.stats()
+        ld = max(256, (n_walk + 255) // 256 * 256)
+        r = torch.empty((st["n_det_up"] + st["n_det_dn"], ld), dtype=torch.float64, device=dev)
+        n_inv = torch.empty(n_walk, dtype=torch.int32, device=dev)
+        n_subst = torch.empty(n_walk, dtype=torch.int32, device=dev)
+        self._check(self._L.mdet_sm_chain(self._h, n_walk, r.data_ptr(), ld, n_inv.data_ptr(), n_subst.data_ptr(),
+                                          _sp(stream, dev)), "mdet_sm_chain")
+        return r, n_inv, n_subst
 
     def spin_dets(self, spin):
         s = self.stats()

@@ -328,6 +328,38 @@ mdet_status upload_problem(mdet_ctx* c) {
   UP(c->coo_val, P.csc_val);
   UP(c->csr_ptr, P.csr_ptr);
   UP(c->csc_ptr, P.csc_ptr);
+  // the sequential chain of Sec. 2.2: distinct determinants in the order of the key of Eq. 3,
+  // each with the substitutions from its predecessor (holes and particles ascending, paired in order)
+  for (int sp = 0; sp < 2; sp++) {
+    const int64_t nu = (int64_t)c->exc[sp].size();
+    std::vector<int64_t> ord = omega_order(nu, c->n_int, c->dets[sp].data());
+    std::vector<SmStep> steps(nu);
+    std::vector<int> prev;
+    for (int64_t t = 0; t < nu; t++) {
+      SmStep& st = steps[t];
+      st = SmStep{};
+      st.ctx = (int32_t)ord[t];
+      std::vector<int> occ = decode_occ(c->dets[sp].data() + ord[t] * c->n_int, c->n_int);
+      for (size_t a = 0; a < occ.size(); a++) st.occ[a] = (uint8_t)occ[a];
+      std::vector<int> holes, parts;
+      for (int m : prev)
+        if (!std::binary_search(occ.begin(), occ.end(), m)) holes.push_back(m);
+      for (int m : occ)
+        if (!std::binary_search(prev.begin(), prev.end(), m)) parts.push_back(m);
+      if (t == 0 || (int)holes.size() > kSmMaxSub) {
+        st.n_sub = t == 0 ? 0 : (uint8_t)(kSmMaxSub + 1);
+      } else {
+        st.n_sub = (uint8_t)holes.size();
+        for (size_t q = 0; q < holes.size(); q++) {
+          st.hole[q] = (uint8_t)holes[q];
+          st.part[q] = (uint8_t)parts[q];
+        }
+      }
+      prev = occ;
+    }
+    UP(steps, P.sm_steps[sp]);
+    P.sm_n[sp] = (int)nu;
+  }
 #undef UP
   free_scratch(c);  // sizes depend on the problem
   return MDET_OK;
@@ -631,6 +663,24 @@ mdet_status mdet_set_ci_expansion(mdet_ctx* c, int64_t n_det, int n_int, const u
   if (s != MDET_OK) return s;
   c->has_ci = true;
   c->err.clear();
+  return MDET_OK;
+}
+
+mdet_status mdet_sm_chain(mdet_ctx* c, int64_t n_walk, double* r, int64_t ld, int32_t* n_inv, int32_t* n_subst,
+                          void* stream) {
+  if (!c) return MDET_E_ARG;
+  if (c->device < 0) return fail(c, MDET_E_NODEVICE, "the chain runs on the context's device");
+  if (!c->has_ci) return fail(c, MDET_E_STATE, "set_ci_expansion must come first");
+  if (n_walk < 0 || !r || !n_inv || !n_subst || ld < n_walk) return fail(c, MDET_E_ARG, "bad chain arguments");
+  if (n_walk > c->last_walk) return fail(c, MDET_E_STATE, "n_walk exceeds the walkers of the last evaluation");
+  if (n_walk == 0) return MDET_OK;
+  CUDA_TRY(c, cudaSetDevice(c->device));
+  cudaStream_t st = (cudaStream_t)stream;
+  if (c->last_stream != st) CUDA_TRY(c, cudaStreamSynchronize(c->last_stream));
+  CUDA_TRY(c, cudaMemsetAsync(n_inv, 0, n_walk * sizeof(int32_t), st));
+  CUDA_TRY(c, cudaMemsetAsync(n_subst, 0, n_walk * sizeof(int32_t), st));
+  for (int sp = 0; sp < 2; sp++)
+    CUDA_TRY(c, launch_sm_chain(c->P, c->S, sp, c->P.sm_steps[sp], c->P.sm_n[sp], n_walk, r, ld, n_inv, n_subst, st));
   return MDET_OK;
 }
 

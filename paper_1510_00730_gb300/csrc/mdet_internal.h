@@ -37,6 +37,8 @@ struct DevProblem {
   int n_shell, n_ao, n_mo, n_prim;
   int n_det_sp[2];        // distinct determinants per spin
   int64_t nnz;            // products
+  const struct SmStep* sm_steps[2];  // the sequential chain of each spin (mdet_sm_chain)
+  int sm_n[2];
   int spmm_chunk;         // tuning: nonzeros per warp in the contraction
   int mo_ec;              // tuning: electrons per CTA in the orbital kernels (4, 6 or 8)
   double fallback_tol;    // estimated relative error above which a walker is re-evaluated by full LU (<= 0: off)
@@ -154,5 +156,23 @@ mdet_status pre_distinct(PreDevice** h, int64_t n, int n_int, const uint64_t* de
 mdet_status pre_build_c(PreDevice* h, const std::vector<int32_t> ctx_of[2], int64_t nup, int64_t ndn,
                         cudaStream_t st, PreC* out, std::string* msg);
 void pre_free(PreDevice* h);
+
+// ---- the sequential Sherman-Morrison chain (mdet_smchain.cu), Sec. 2.2 ----
+constexpr int kSmMaxSub = 8;  // substitutions between consecutive determinants (2 * MDET_MAX_EXC)
+// One determinant of the chain, in the order of the key of Eq. 3: its context
+// index, the substitutions hole[s] -> part[s] (MO indices, ascending) that turn
+// the previous determinant of the chain into it (n_sub > kSmMaxSub: recompute it
+// from scratch), and its occupied MOs in ascending order.
+struct SmStep {
+  int32_t ctx;
+  uint8_t n_sub;
+  uint8_t hole[kSmMaxSub];
+  uint8_t part[kSmMaxSub];
+  uint8_t occ[kMaxSpin];
+};
+size_t sm_chain_smem_bytes(int n);
+cudaError_t launch_sm_chain(const DevProblem& P, const DevScratch& S, int spin, const SmStep* steps, int n_steps,
+                            int64_t n_walk, double* r, int64_t ld_r, int32_t* n_inv, int32_t* n_subst,
+                            cudaStream_t st);
 
 }  // namespace mdet
