@@ -369,8 +369,9 @@ __global__ void __launch_bounds__(128) k_spmm_wm(const int* __restrict__ seg, co
 // a compensated pair of FP32 shared atomics: the atomic returns the old value,
 // so TwoSum(old, x) recovers the rounding error of the addition it performed,
 // which goes into the low word. Q, Pm and G stay FP64.
-// smem: T[N][M] (FP64), W[N][M] (FP64, or hi/lo FP32 pairs then FP64),
-//       Q[N][M], Tdf[N][M] (MIXED), A blocks, Pm.
+// smem, FP64: T[N][M], W[N][M], Q[N][M], A blocks, Pm.
+// smem, MIXED: W[N][M] (hi/lo FP32 pairs during the scatter, then the FP64 T
+//       for Pm), Q[N][M], A blocks, Pm, Tdf[N][M] (then W in FP64).
 template <bool MIXED>
 __global__ void __launch_bounds__(128) k_final(DevProblem P, DevScratch S, const double* __restrict__ R,
                                                double* __restrict__ log_abs_psi, int8_t* __restrict__ sign,
@@ -380,8 +381,8 @@ __global__ void __launch_bounds__(128) k_final(DevProblem P, DevScratch S, const
   const int nu = P.n_up, nd = P.n_dn, N = nu + nd, M = P.n_mo;
   const int NM = N * M;
   const int64_t w = blockIdx.x, wp = S.wp;
-  double* Ts = sm;                      // [N][M]
-  double* Ws = Ts + NM;                 // [N][M]
+  double* Ts = MIXED ? nullptr : sm;    // [N][M]; MIXED: loaded into the W space after the scatter
+  double* Ws = MIXED ? sm : sm + NM;    // [N][M]
   double* Qs = Ws + NM;                 // [N][M]
   double* As = Qs + NM;                 // [nu*nu + nd*nd]
   double* Pm = As + nu * nu + nd * nd;  // [nu*nu + nd*nd]  Pm[b][i] per spin
@@ -394,24 +395,32 @@ __global__ void __launch_bounds__(128) k_final(DevProblem P, DevScratch S, const
   __shared__ float G2[kMaxSpin * 2][4];
   __shared__ float rmsG[4], estw[2][4];
   for (int t = threadIdx.x; t < NM; t += blockDim.x) {
-    Ts[t] = S.T[(size_t)t * wp + w];
     if (MIXED) {
       Tdf[t] = S.Tdf[(size_t)t * wp + w];
       Whi[t] = 0.0f;
       Wlo[t] = 0.0f;
     } else {
+      Ts[t] = S.T[(size_t)t * wp + w];
       Ws[t] = 0.0;
     }
   }
   for (int t = threadIdx.x; t < nu * nu + nd * nd; t += blockDim.x) As[t] = S.Ainv[w * (nu * nu + nd * nd) + t];
   __syncthreads();
   const int nu_det = P.n_det_sp[0], ntot = nu_det + P.n_det_sp[1];
-  // each thread walks its own contiguous block of determinants, so the lanes
-  // of a warp hold determinants far apart in the (degree, key) order; those
-  // rarely share a (hole, particle) slot, which keeps the shared atomics apart
-  const int per = (ntot + blockDim.x - 1) / blockDim.x;
-  const int t_begin = threadIdx.x * per, t_end = min(ntot, t_begin + per);
-  for (int t = t_begin; t < t_end; t++) {
+  // MIXED: determinant t = (q * stride) mod ntot for q = thread, thread + 128,
+  // ..., with a prime stride that does not divide ntot (a permutation): every
+  // thread gets a mix of excitation degrees, so the double-float cofactor work
+  // (k^2 per determinant) is balanced across the block. FP64: each thread walks
+  // its own contiguous block (sequential loads of records and weights; the
+  // FP64 pipe, not the balance, bounds that variant). Either way the lanes of a
+  // warp hold determinants far apart in the (degree, key) order, which rarely
+  // share a (hole, particle) slot of W.
+  const int64_t stride = (ntot % 7919) ? 7919 : ((ntot % 7927) ? 7927 : 7933);
+  const int tid = threadIdx.x, nth = blockDim.x;
+  const int per = (ntot + nth - 1) / nth;
+  const int n_mine = MIXED ? (ntot - tid + nth - 1) / nth : max(0, min(per, ntot - tid * per));
+  for (int j = 0; j < n_mine; j++) {
+    const int t = MIXED ? (int)(((int64_t)(tid + j * nth) * stride) % ntot) : tid * per + j;
     const int sp = t < nu_det ? 0 : 1;
     const Exc e = P.exc[sp][sp ? t - nu_det : t];
     if (e.k == 0) continue;
@@ -461,6 +470,9 @@ __global__ void __launch_bounds__(128) k_final(DevProblem P, DevScratch S, const
   if (MIXED) {
     for (int t = threadIdx.x; t < NM; t += blockDim.x) Wd[t] = (double)Whi[t] + (double)Wlo[t];
     __syncthreads();
+    // the FP64 table for Pm, into the space of the hi/lo words (Q does not read it)
+    Ts = Ws;
+    for (int t = threadIdx.x; t < NM; t += blockDim.x) Ts[t] = S.T[(size_t)t * wp + w];
   }
   // Q[i][m] = sum_a A[a][i] W[a][m] (per spin block)
   for (int t = threadIdx.x; t < NM; t += blockDim.x) {
@@ -729,7 +741,9 @@ cudaError_t launch_spmm_rows_f64(const DevProblem& P, const double* r_dn, const 
 
 size_t final_smem_bytes(const DevProblem& P, bool mixed) {
   const size_t NM = (size_t)P.n_elec * P.n_mo;
-  return sizeof(double) * (3 * NM + 2 * (size_t)(P.n_up * P.n_up + P.n_dn * P.n_dn)) + (mixed ? 8 * NM : 0);
+  // FP64: T, W, Q; MIXED: W (then T), Q, Tdf (then W); both: A blocks and Pm
+  return sizeof(double) * ((mixed ? 2 : 3) * NM + 2 * (size_t)(P.n_up * P.n_up + P.n_dn * P.n_dn)) +
+         (mixed ? 8 * NM : 0);
 }
 
 cudaError_t launch_final(const DevProblem& P, const DevScratch& S, int64_t n_walk, const double* R,
