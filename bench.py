@@ -25,7 +25,7 @@ sys.path.insert(0, ROOT)
 
 METRIC = "walker-steps/s (Ψ,∇Ψ,∇²Ψ), 17e⁻, N_det=750k: mixed vs FP64 at 1e-5 rel err"
 UNIT = "walker-steps/s"
-FP64_PEAK_TFLOPS = 1.25     # nominal dense FP64 of one GB300 (recipe table); see the design doc
+FP64_PEAK_TFLOPS = 1.25     # nominal dense FP64 rate of one GB300 (no measured FP64 peak is available)
 CPU_SAMPLE_WALKERS = 96     # bounded oracle sample for the CPU baseline (~10-30 s of CPU work)
 # dram__bytes_read.sum + dram__bytes_write.sum of one k_spmm_wm launch on the 750k workload with
 # 8,192 walkers (ncu capture summarised in profiles/mixed_chlorine_like_750k.md)

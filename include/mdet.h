@@ -275,10 +275,13 @@ mdet_status mdet_get_fallback(const mdet_ctx* ctx, double* tol, int* max_walkers
 mdet_status mdet_set_walker_chunks(mdet_ctx* ctx, int n_chunks);
 
 /*
- * Tile shapes of the evaluation kernels (SURVEY-level tuning knobs, no paper
- * counterpart): spmm_chunk nonzeros of C per warp in the contraction (64..8192),
+ * Tile shapes of the evaluation kernels (tuning knobs with no counterpart in
+ * the paper): spmm_chunk nonzeros of C per warp in the contraction (64..8192),
  * mo_ec electrons per thread block in the orbital kernels (4, 6 or 8),
- * walker_chunks as in mdet_set_walker_chunks. best_ms and trials are filled by
+ * walker_chunks as in mdet_set_walker_chunks, spmm_blocks the grid of the
+ * contraction (0: one warp per work item; otherwise at most that many
+ * 128-thread blocks looping over the work items, which leaves room on the SMs
+ * for the kernels of another walker chunk). best_ms and trials are filled by
  * mdet_autotune (the fastest step time seen and the configurations timed).
  */
 typedef struct {
@@ -287,6 +290,7 @@ typedef struct {
   int32_t walker_chunks;
   float best_ms;
   int32_t trials;
+  int32_t spmm_blocks;
 } mdet_tuning;
 
 mdet_status mdet_get_tuning(const mdet_ctx* ctx, mdet_tuning* out);

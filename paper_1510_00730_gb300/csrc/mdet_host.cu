@@ -51,6 +51,7 @@ struct mdet_ctx {
   int fallback_cap = 64;
   std::vector<int32_t> csr_ptr, csc_ptr;
   int spmm_chunk = 512;  // tile shapes (mdet_set_tuning / mdet_autotune)
+  int spmm_blocks = 0;
   int mo_ec = 6;
   mdet_tuning last_tune{};
   cudaStream_t cs[kMaxChunks] = {};
@@ -276,6 +277,7 @@ mdet_status upload_problem(mdet_ctx* c) {
   P.n_det_sp[1] = (int)c->exc[1].size();
   P.nnz = c->n_det;
   P.spmm_chunk = c->spmm_chunk;
+  P.spmm_blocks = c->spmm_blocks;
   P.mo_ec = c->mo_ec;
   P.fallback_tol = c->fallback_tol;
   P.fallback_cap = c->fallback_cap;
@@ -1004,6 +1006,7 @@ mdet_status mdet_get_tuning(const mdet_ctx* c, mdet_tuning* out) {
   out->spmm_chunk = c->spmm_chunk;
   out->mo_ec = c->mo_ec;
   out->walker_chunks = c->n_chunks_cfg;
+  out->spmm_blocks = c->spmm_blocks;
   return MDET_OK;
 }
 
@@ -1012,6 +1015,9 @@ mdet_status mdet_set_tuning(mdet_ctx* c, const mdet_tuning* t) {
   if (t->spmm_chunk < 64 || t->spmm_chunk > 8192) return fail(c, MDET_E_ARG, "spmm_chunk outside 64..8192");
   if (t->mo_ec != 4 && t->mo_ec != 6 && t->mo_ec != 8) return fail(c, MDET_E_ARG, "mo_ec must be 4, 6 or 8");
   if (t->walker_chunks < 0) return fail(c, MDET_E_ARG, "walker_chunks < 0");
+  if (t->spmm_blocks < 0) return fail(c, MDET_E_ARG, "spmm_blocks < 0");
+  c->spmm_blocks = t->spmm_blocks;
+  c->P.spmm_blocks = t->spmm_blocks;
   c->spmm_chunk = t->spmm_chunk;
   c->mo_ec = t->mo_ec;
   c->n_chunks_cfg = std::min(t->walker_chunks, (int)mdet_ctx::kMaxChunks);

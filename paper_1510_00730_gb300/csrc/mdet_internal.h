@@ -40,6 +40,7 @@ struct DevProblem {
   const struct SmStep* sm_steps[2];  // the sequential chain of each spin (mdet_sm_chain)
   int sm_n[2];
   int spmm_chunk;         // tuning: nonzeros per warp in the contraction
+  int spmm_blocks;        // tuning: grid of the contraction (0: one warp per work item)
   int mo_ec;              // tuning: electrons per CTA in the orbital kernels (4, 6 or 8)
   double fallback_tol;    // estimated relative error above which a walker is re-evaluated by full LU (<= 0: off)
   int fallback_cap;       // walkers re-evaluated per evaluation at most

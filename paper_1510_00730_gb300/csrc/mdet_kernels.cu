@@ -692,8 +692,10 @@ cudaError_t launch_contract_f64(const DevProblem& P, const DevScratch& S, int64_
   const int64_t n_chunks = (P.nnz + chunk - 1) / chunk;
   const int64_t n_groups = (n_walk + 255) / 256;
   const int64_t items = n_chunks * n_groups;
-  // one work item per warp (full occupancy hides the L2 latency of the gathers)
-  const int64_t blocks = (items + 3) / 4;
+  // one work item per warp (full occupancy hides the L2 latency of the gathers), or a
+  // persistent grid of spmm_blocks blocks looping over the items
+  int64_t blocks = (items + 3) / 4;
+  if (P.spmm_blocks > 0) blocks = std::min<int64_t>(blocks, P.spmm_blocks);
   (void)n_sm;
   const int64_t ndt = (int64_t)P.n_det_sp[0] + P.n_det_sp[1];
   const double* r_up = S.r;
