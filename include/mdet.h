@@ -281,8 +281,13 @@ mdet_status mdet_set_walker_chunks(mdet_ctx* ctx, int n_chunks);
  * walker_chunks as in mdet_set_walker_chunks, spmm_blocks the grid of the
  * contraction (0: one warp per work item; otherwise at most that many
  * 128-thread blocks looping over the work items, which leaves room on the SMs
- * for the kernels of another walker chunk). best_ms and trials are filled by
- * mdet_autotune (the fastest step time seen and the configurations timed).
+ * for the kernels of another walker chunk), mo_impl the mixed-precision
+ * orbital product (1, the default: the compensated FP32 dot product on the
+ * CUDA cores, accurate relative to each term; 0: BF16 tensor cores on exact
+ * digit products, accurate to about 2^-55 of the row and column maxima).
+ * Defaults: spmm_chunk 512, mo_ec 4, walker_chunks 0, spmm_blocks 0, mo_impl 1.
+ * best_ms and trials are filled by mdet_autotune (the fastest step time seen
+ * and the configurations timed).
  */
 typedef struct {
   int32_t spmm_chunk;
@@ -291,6 +296,7 @@ typedef struct {
   float best_ms;
   int32_t trials;
   int32_t spmm_blocks;
+  int32_t mo_impl;
 } mdet_tuning;
 
 mdet_status mdet_get_tuning(const mdet_ctx* ctx, mdet_tuning* out);

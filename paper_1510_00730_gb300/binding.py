@@ -34,7 +34,7 @@ class MdetError(RuntimeError):
 
 class _Tuning(C.Structure):
     _fields_ = [("spmm_chunk", C.c_int32), ("mo_ec", C.c_int32), ("walker_chunks", C.c_int32),
-                ("best_ms", C.c_float), ("trials", C.c_int32), ("spmm_blocks", C.c_int32)]
+                ("best_ms", C.c_float), ("trials", C.c_int32), ("spmm_blocks", C.c_int32), ("mo_impl", C.c_int32)]
 
 
 class _Stats(C.Structure):
@@ -351,10 +351,10 @@ class Context:
         t = _Tuning()
         self._check(self._L.mdet_get_tuning(self._h, C.byref(t)), "mdet_get_tuning")
         return dict(spmm_chunk=t.spmm_chunk, mo_ec=t.mo_ec, walker_chunks=t.walker_chunks, best_ms=t.best_ms,
-                    trials=t.trials, spmm_blocks=t.spmm_blocks)
+                    trials=t.trials, spmm_blocks=t.spmm_blocks, mo_impl=t.mo_impl)
 
-    def set_tuning(self, spmm_chunk=512, mo_ec=6, walker_chunks=0, spmm_blocks=0):
-        t = _Tuning(spmm_chunk, mo_ec, walker_chunks, 0.0, 0, spmm_blocks)
+    def set_tuning(self, spmm_chunk=512, mo_ec=4, walker_chunks=0, spmm_blocks=0, mo_impl=1):
+        t = _Tuning(spmm_chunk, mo_ec, walker_chunks, 0.0, 0, spmm_blocks, mo_impl)
         self._check(self._L.mdet_set_tuning(self._h, C.byref(t)), "mdet_set_tuning")
 
     def autotune(self, R, budget_ms=200.0):
@@ -363,7 +363,7 @@ class Context:
         self._check(self._L.mdet_autotune(self._h, R.shape[0], R.data_ptr(), float(budget_ms), C.byref(t)),
                     "mdet_autotune")
         return dict(spmm_chunk=t.spmm_chunk, mo_ec=t.mo_ec, walker_chunks=t.walker_chunks, best_ms=t.best_ms,
-                    trials=t.trials, spmm_blocks=t.spmm_blocks)
+                    trials=t.trials, spmm_blocks=t.spmm_blocks, mo_impl=t.mo_impl)
 
     def set_fallback(self, tol, max_walkers=64):
         """Re-evaluate walkers whose estimated table error exceeds tol by full LU (tol <= 0: off)."""

@@ -52,7 +52,8 @@ struct mdet_ctx {
   std::vector<int32_t> csr_ptr, csc_ptr;
   int spmm_chunk = 512;  // tile shapes (mdet_set_tuning / mdet_autotune)
   int spmm_blocks = 0;
-  int mo_ec = 6;
+  int mo_impl = 1;  // the compensated CUDA-core product (faster here than the tensor-core digits)
+  int mo_ec = 4;
   mdet_tuning last_tune{};
   cudaStream_t cs[kMaxChunks] = {};
   cudaEvent_t fork = nullptr, joined[kMaxChunks] = {}, contracted[kMaxChunks] = {};
@@ -279,6 +280,7 @@ mdet_status upload_problem(mdet_ctx* c) {
   P.spmm_chunk = c->spmm_chunk;
   P.spmm_blocks = c->spmm_blocks;
   P.mo_ec = c->mo_ec;
+  P.mo_impl = c->mo_impl;
   P.fallback_tol = c->fallback_tol;
   P.fallback_cap = c->fallback_cap;
   mdet_status s;
@@ -304,6 +306,37 @@ mdet_status upload_problem(mdet_ctx* c) {
   UP(B, P.B);
   UP(Bh, P.B_hi);
   UP(Bl, P.B_lo);
+  // digits of B for the tensor-core orbital product: column m as 2^f_m sum_j g_j 2^(-8 j),
+  // j = 1..7, integer digits (|g_1| <= 256, |g_j| <= 128) stored as BF16, [j][m][k] K-contiguous
+  {
+    const int kDigits = 7;
+    P.tc_kp = (c->n_ao + 15) / 16 * 16;
+    P.tc_mp = (c->n_mo + 7) / 8 * 8;
+    const int half = P.tc_kp / 2;  // shared row stride in 4-byte words must be 4 mod 8 (conflict-free A fragments)
+    P.tc_sx = P.tc_kp + 2 * ((4 - half % 8 + 8) % 8);
+    std::vector<uint16_t> dig((size_t)kDigits * P.tc_mp * P.tc_kp, 0);
+    std::vector<int> fexp(c->n_mo, 0);
+    for (int m = 0; m < c->n_mo; m++) {
+      double mx = 0.0;
+      for (int mu = 0; mu < c->n_ao; mu++) mx = std::max(mx, std::fabs(B[(size_t)mu * c->n_mo + m]));
+      const int f = mx > 0.0 ? std::ilogb(mx) + 1 : 0;
+      fexp[m] = f;
+      for (int mu = 0; mu < c->n_ao; mu++) {
+        double v = std::ldexp(B[(size_t)mu * c->n_mo + m], -f);
+        for (int j = 0; j < kDigits; j++) {
+          v *= 256.0;
+          const double d = std::nearbyint(v);
+          v -= d;
+          const float fd = (float)d;
+          uint32_t bits;
+          std::memcpy(&bits, &fd, 4);
+          dig[((size_t)j * P.tc_mp + m) * P.tc_kp + mu] = (uint16_t)(bits >> 16);
+        }
+      }
+    }
+    UP(dig, P.B_dig);
+    UP(fexp, P.B_exp);
+  }
   auto split = [](const std::vector<double>& v) {
     std::vector<float2> o(v.size());
     for (size_t i = 0; i < v.size(); i++) {
@@ -1007,6 +1040,7 @@ mdet_status mdet_get_tuning(const mdet_ctx* c, mdet_tuning* out) {
   out->mo_ec = c->mo_ec;
   out->walker_chunks = c->n_chunks_cfg;
   out->spmm_blocks = c->spmm_blocks;
+  out->mo_impl = c->mo_impl;
   return MDET_OK;
 }
 
@@ -1016,6 +1050,9 @@ mdet_status mdet_set_tuning(mdet_ctx* c, const mdet_tuning* t) {
   if (t->mo_ec != 4 && t->mo_ec != 6 && t->mo_ec != 8) return fail(c, MDET_E_ARG, "mo_ec must be 4, 6 or 8");
   if (t->walker_chunks < 0) return fail(c, MDET_E_ARG, "walker_chunks < 0");
   if (t->spmm_blocks < 0) return fail(c, MDET_E_ARG, "spmm_blocks < 0");
+  if (t->mo_impl != 0 && t->mo_impl != 1) return fail(c, MDET_E_ARG, "mo_impl must be 0 or 1");
+  c->mo_impl = t->mo_impl;
+  c->P.mo_impl = t->mo_impl;
   c->spmm_blocks = t->spmm_blocks;
   c->P.spmm_blocks = t->spmm_blocks;
   c->spmm_chunk = t->spmm_chunk;

@@ -42,6 +42,10 @@ struct DevProblem {
   int spmm_chunk;         // tuning: nonzeros per warp in the contraction
   int spmm_blocks;        // tuning: grid of the contraction (0: one warp per work item)
   int mo_ec;              // tuning: electrons per CTA in the orbital kernels (4, 6 or 8)
+  int mo_impl;            // tuning: mixed orbitals on the tensor cores (0) or the compensated FP32 dot product (1)
+  const uint16_t* B_dig;  // [7][tc_mp][tc_kp] BF16 digits of the MO coefficients (column-scaled)
+  const int* B_exp;       // [n_mo] column exponents of B_dig
+  int tc_kp, tc_mp, tc_sx;  // K padded to 16, M padded to 8, shared row stride of the AO digits
   double fallback_tol;    // estimated relative error above which a walker is re-evaluated by full LU (<= 0: off)
   int fallback_cap;       // walkers re-evaluated per evaluation at most
   const double* Z;        // [n_nuc]
