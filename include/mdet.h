@@ -285,7 +285,8 @@ mdet_status mdet_set_walker_chunks(mdet_ctx* ctx, int n_chunks);
  * orbital product (1, the default: the compensated FP32 dot product on the
  * CUDA cores, accurate relative to each term; 0: BF16 tensor cores on exact
  * digit products, accurate to about 2^-55 of the row and column maxima).
- * Defaults: spmm_chunk 512, mo_ec 4, walker_chunks 0, spmm_blocks 0, mo_impl 1.
+ * Defaults: spmm_chunk 512, mo_ec 4 (mixed) or 6 (FP64), walker_chunks 0,
+ * spmm_blocks 0, mo_impl 1.
  * best_ms and trials are filled by mdet_autotune (the fastest step time seen
  * and the configurations timed).
  */

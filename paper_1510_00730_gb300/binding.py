@@ -353,7 +353,10 @@ class Context:
         return dict(spmm_chunk=t.spmm_chunk, mo_ec=t.mo_ec, walker_chunks=t.walker_chunks, best_ms=t.best_ms,
                     trials=t.trials, spmm_blocks=t.spmm_blocks, mo_impl=t.mo_impl)
 
-    def set_tuning(self, spmm_chunk=512, mo_ec=4, walker_chunks=0, spmm_blocks=0, mo_impl=1):
+    def set_tuning(self, spmm_chunk=512, mo_ec=None, walker_chunks=0, spmm_blocks=0, mo_impl=1):
+        """Tile shapes (mdet_set_tuning); mo_ec None keeps the context's current value."""
+        if mo_ec is None:
+            mo_ec = self.tuning()["mo_ec"]
         t = _Tuning(spmm_chunk, mo_ec, walker_chunks, 0.0, 0, spmm_blocks, mo_impl)
         self._check(self._L.mdet_set_tuning(self._h, C.byref(t)), "mdet_set_tuning")
 

@@ -9,7 +9,7 @@
 //                Gauss-Jordan inversion with partial pivoting of the Slater
 //                matrix, log|D|, sign and (d_{i mu} D)/D = sum_a d_mu phi_{o_a}(r_i) (S^-1)_{a i}
 //   k_fb_scale   per flagged walker: common scale of its determinant values
-//   k_fb_rows    (rows, walker) blocks: v = C d_dn, u = C^T d_up, Psi, gradient
+//   k_fb_rows    (rows, walker) blocks, a warp per row: v = C d_dn, u = C^T d_up, Psi, gradient
 //                and Laplacian sums, reduced per block then with atomics
 //   k_fb_out     per flagged walker: potential energy and outputs
 #include <cfloat>
@@ -189,24 +189,32 @@ __global__ void __launch_bounds__(256) k_fb_rows(DevProblem P, DevScratch S) {
   __shared__ double G[1 + 4 * 2 * kFbMax];  // Psi, then G
   for (int q = threadIdx.x; q < 1 + 4 * N; q += blockDim.x) G[q] = 0.0;
   __syncthreads();
-  const int t = blockIdx.x * blockDim.x + threadIdx.x;
-  if (t < nu_det) {
+  // one warp per distinct determinant: its row (up) or column (down) of C, whose length
+  // varies by orders of magnitude, is split over the lanes and reduced with shuffles
+  const int lane = threadIdx.x & 31;
+  const int t = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  if (t < ntot) {
+    const bool up = t < nu_det;
     double v = 0.0;
-    for (int k = P.csr_ptr[t]; k < P.csr_ptr[t + 1]; k++) v = fma(P.csr_val[k], dv[nu_det + P.csr_col[k]], v);
+    if (up) {
+      for (int k = P.csr_ptr[t] + lane; k < P.csr_ptr[t + 1]; k += 32)
+        v = fma(P.csr_val[k], dv[nu_det + P.csr_col[k]], v);
+    } else {
+      const int J = t - nu_det;
+      for (int k = P.csc_ptr[J] + lane; k < P.csc_ptr[J + 1]; k += 32) v = fma(P.csc_val[k], dv[P.csc_row[k]], v);
+    }
+#pragma unroll
+    for (int off = 16; off; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
     const double* r = rec + (size_t)t * stride;
     const double vd = v * r[0];
     if (vd != 0.0) {
-      atomicAdd(&G[0], vd);
-      for (int q = 0; q < 4 * nu; q++) atomicAdd(&G[1 + q], vd * r[2 + q]);
+      if (up) {
+        if (lane == 0) atomicAdd(&G[0], vd);
+        for (int q = lane; q < 4 * nu; q += 32) atomicAdd(&G[1 + q], vd * r[2 + q]);
+      } else {
+        for (int q = lane; q < 4 * nd; q += 32) atomicAdd(&G[1 + 4 * nu + q], vd * r[2 + q]);
+      }
     }
-  } else if (t < ntot) {
-    const int J = t - nu_det;
-    double u = 0.0;
-    for (int k = P.csc_ptr[J]; k < P.csc_ptr[J + 1]; k++) u = fma(P.csc_val[k], dv[P.csc_row[k]], u);
-    const double* r = rec + (size_t)t * stride;
-    const double ud = u * r[0];
-    if (ud != 0.0)
-      for (int q = 0; q < 4 * nd; q++) atomicAdd(&G[1 + 4 * nu + q], ud * r[2 + q]);
   }
   __syncthreads();
   for (int q = threadIdx.x; q < 1 + 4 * N; q += blockDim.x)
@@ -299,7 +307,7 @@ cudaError_t launch_fallback(const DevProblem& P, const DevScratch& S, int64_t n_
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   k_fb_scale<<<P.fallback_cap, 256, 0, st>>>(P, S);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  dim3 g2((ntot + 255) / 256, P.fallback_cap);
+  dim3 g2((ntot + 7) / 8, P.fallback_cap);  // 8 warps per block, one per distinct determinant
   k_fb_rows<<<g2, 256, 0, st>>>(P, S);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   k_fb_out<<<P.fallback_cap, 64, 0, st>>>(P, S, R, log_abs_psi, sign, grad, lap, e_local, status);

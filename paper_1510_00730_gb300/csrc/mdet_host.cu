@@ -488,6 +488,7 @@ mdet_status mdet_create(mdet_ctx** out, int device, int precision) {
   c->device = device;
   c->precision = precision;
   c->fallback_tol = precision == MDET_PRECISION_MIXED ? 1e-5 : 1e-6;
+  c->mo_ec = precision == MDET_PRECISION_MIXED ? 4 : 6;  // measured best electron block of each orbital kernel
   if (device >= 0) {
     int n = 0;
     if (cudaGetDeviceCount(&n) != cudaSuccess || device >= n) {
