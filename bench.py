@@ -29,7 +29,7 @@ FP64_PEAK_TFLOPS = 1.25     # nominal dense FP64 rate of one GB300 (no measured 
 CPU_SAMPLE_WALKERS = 96     # bounded oracle sample for the CPU baseline (~10-30 s of CPU work)
 # dram__bytes_read.sum + dram__bytes_write.sum of one k_spmm_wm launch on the 750k workload with
 # 8,192 walkers (ncu capture summarised in profiles/mixed_chlorine_like_750k.md)
-SPMM_TRAFFIC_750K = 853.5e6
+SPMM_TRAFFIC_750K = 852.5e6
 
 
 def _env_int(k, d):

@@ -9,9 +9,10 @@
 //                Gauss-Jordan inversion with partial pivoting of the Slater
 //                matrix, log|D|, sign and (d_{i mu} D)/D = sum_a d_mu phi_{o_a}(r_i) (S^-1)_{a i}
 //   k_fb_scale   per flagged walker: common scale of its determinant values
-//   k_fb_rows    (rows, walker) blocks, a warp per row: v = C d_dn, u = C^T d_up, Psi, gradient
+//   k_fb_rows    fixed grid over (walker, 64 rows) items, a warp per row: v = C d_dn, u = C^T d_up, Psi, gradient
 //                and Laplacian sums, reduced per block then with atomics
 //   k_fb_out     per flagged walker: potential energy and outputs
+#include <algorithm>
 #include <cfloat>
 #include <cmath>
 
@@ -176,49 +177,55 @@ __global__ void __launch_bounds__(256) k_fb_scale(DevProblem P, DevScratch S) {
 // grid (ceil(ntot / 256), count slots): one thread per up row (v = C d_dn,
 // Psi and the up-electron sums) or down column (u = C^T d_up, the
 // down-electron sums); block sums in shared memory, then one atomic per value.
+constexpr int kFbRowsPerItem = 64;  // distinct determinants per work item of k_fb_rows (8 warps x 8)
+
 __global__ void __launch_bounds__(256) k_fb_rows(DevProblem P, DevScratch S) {
-  const int slot = blockIdx.y;
   const int count = min(S.fb_list[0], P.fallback_cap);
-  if (slot >= count) return;
   const int nu = P.n_up, nd = P.n_dn, N = nu + nd, nmax = max(nu, nd);
   const int nu_det = P.n_det_sp[0], ntot = nu_det + P.n_det_sp[1];
   const int stride = 2 + 4 * nmax;
-  const double* rec = S.fb + (size_t)slot * ntot * stride;
-  const double* dv = S.fb + (size_t)P.fallback_cap * ntot * stride + (size_t)slot * ntot;
-  double* acc = S.fb_acc + (size_t)slot * (3 + 4 * 2 * kFbMax);
+  const int n_rg = (ntot + kFbRowsPerItem - 1) / kFbRowsPerItem;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   __shared__ double G[1 + 4 * 2 * kFbMax];  // Psi, then G
-  for (int q = threadIdx.x; q < 1 + 4 * N; q += blockDim.x) G[q] = 0.0;
-  __syncthreads();
-  // one warp per distinct determinant: its row (up) or column (down) of C, whose length
-  // varies by orders of magnitude, is split over the lanes and reduced with shuffles
-  const int lane = threadIdx.x & 31;
-  const int t = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-  if (t < ntot) {
-    const bool up = t < nu_det;
-    double v = 0.0;
-    if (up) {
-      for (int k = P.csr_ptr[t] + lane; k < P.csr_ptr[t + 1]; k += 32)
-        v = fma(P.csr_val[k], dv[nu_det + P.csr_col[k]], v);
-    } else {
-      const int J = t - nu_det;
-      for (int k = P.csc_ptr[J] + lane; k < P.csc_ptr[J + 1]; k += 32) v = fma(P.csc_val[k], dv[P.csc_row[k]], v);
-    }
-#pragma unroll
-    for (int off = 16; off; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
-    const double* r = rec + (size_t)t * stride;
-    const double vd = v * r[0];
-    if (vd != 0.0) {
+  // work items (flagged walker, group of 64 distinct determinants) over a fixed grid: a batch
+  // without flagged walkers costs one small launch
+  for (int64_t item = blockIdx.x; item < (int64_t)count * n_rg; item += gridDim.x) {
+    const int slot = (int)(item / n_rg), rg = (int)(item - (int64_t)slot * n_rg);
+    const double* rec = S.fb + (size_t)slot * ntot * stride;
+    const double* dv = S.fb + (size_t)P.fallback_cap * ntot * stride + (size_t)slot * ntot;
+    for (int q = threadIdx.x; q < 1 + 4 * N; q += blockDim.x) G[q] = 0.0;
+    __syncthreads();
+    // one warp per distinct determinant: its row (up) or column (down) of C, whose length
+    // varies by orders of magnitude, is split over the lanes and reduced with shuffles
+    for (int t = rg * kFbRowsPerItem + warp; t < min(ntot, (rg + 1) * kFbRowsPerItem); t += blockDim.x >> 5) {
+      const bool up = t < nu_det;
+      double v = 0.0;
       if (up) {
-        if (lane == 0) atomicAdd(&G[0], vd);
-        for (int q = lane; q < 4 * nu; q += 32) atomicAdd(&G[1 + q], vd * r[2 + q]);
+        for (int k = P.csr_ptr[t] + lane; k < P.csr_ptr[t + 1]; k += 32)
+          v = fma(P.csr_val[k], dv[nu_det + P.csr_col[k]], v);
       } else {
-        for (int q = lane; q < 4 * nd; q += 32) atomicAdd(&G[1 + 4 * nu + q], vd * r[2 + q]);
+        const int J = t - nu_det;
+        for (int k = P.csc_ptr[J] + lane; k < P.csc_ptr[J + 1]; k += 32) v = fma(P.csc_val[k], dv[P.csc_row[k]], v);
+      }
+#pragma unroll
+      for (int off = 16; off; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+      const double* r = rec + (size_t)t * stride;
+      const double vd = v * r[0];
+      if (vd != 0.0) {
+        if (up) {
+          if (lane == 0) atomicAdd(&G[0], vd);
+          for (int q = lane; q < 4 * nu; q += 32) atomicAdd(&G[1 + q], vd * r[2 + q]);
+        } else {
+          for (int q = lane; q < 4 * nd; q += 32) atomicAdd(&G[1 + 4 * nu + q], vd * r[2 + q]);
+        }
       }
     }
+    __syncthreads();
+    double* acc = S.fb_acc + (size_t)slot * (3 + 4 * 2 * kFbMax);
+    for (int q = threadIdx.x; q < 1 + 4 * N; q += blockDim.x)
+      if (G[q] != 0.0) atomicAdd(&acc[2 + q], G[q]);
+    __syncthreads();
   }
-  __syncthreads();
-  for (int q = threadIdx.x; q < 1 + 4 * N; q += blockDim.x)
-    if (G[q] != 0.0) atomicAdd(&acc[2 + q], G[q]);
 }
 
 // Per flagged walker: potential energy and the outputs.
@@ -307,8 +314,14 @@ cudaError_t launch_fallback(const DevProblem& P, const DevScratch& S, int64_t n_
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   k_fb_scale<<<P.fallback_cap, 256, 0, st>>>(P, S);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  dim3 g2((ntot + 7) / 8, P.fallback_cap);  // 8 warps per block, one per distinct determinant
-  k_fb_rows<<<g2, 256, 0, st>>>(P, S);
+  static int n_sm = 0;
+  if (!n_sm) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n_sm <= 0) n_sm = 132;
+  }
+  const int64_t items = (int64_t)P.fallback_cap * ((ntot + kFbRowsPerItem - 1) / kFbRowsPerItem);
+  k_fb_rows<<<(unsigned)std::min<int64_t>(items, 4 * n_sm), 256, 0, st>>>(P, S);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   k_fb_out<<<P.fallback_cap, 64, 0, st>>>(P, S, R, log_abs_psi, sign, grad, lap, e_local, status);
   return cudaGetLastError();
