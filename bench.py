@@ -133,7 +133,8 @@ def run_reference(args):
     line = {"impl": "reference", "metric": METRIC, "value": val, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": per * 1e3, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": args.workload, "walkers_per_step": n, "n_det": wl.n_det},
+            "config": {"workload": args.workload, "walkers_per_gpu": wl.n_walk, "n_det": int(wl.n_det),
+                       "n_elec": wl.n_elec, "sampled_walkers_per_step": n},
             "cpu_baseline": {"value": val, "unit": UNIT, "cores": cores, "kind": "oracle",
                              "sample": "%d walkers per step of the %d-walker workload" % (n, wl.n_walk)},
             "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
