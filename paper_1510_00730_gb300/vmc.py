@@ -149,6 +149,59 @@ class VMC:
         return torch.cat(R0), torch.cat(R1)
 
 
+_CKPT_MAGIC = b"MDETVMC1"
+
+
+def save_checkpoint(path, vmc, mlp=None):
+    """Write the chain state as one flat little-endian binary: the magic
+    MDETVMC1, then int64 walkers, electrons, seed, step, parameter count
+    (0 without a network), float64 drift_a, drift_tau (NaN when unset), the
+    positions [W][N][3] float64 and the network's FP32 master parameters. The
+    random numbers are counter-based (Philox keyed by seed and step), so seed
+    and step are the whole generator state."""
+    import struct
+    R = vmc.cur["R"].detach().cpu().numpy().astype("<f8")
+    params = mlp.params().astype("<f4") if mlp is not None else np.zeros(0, "<f4")
+    tau = float("nan") if vmc.drift_tau is None else float(vmc.drift_tau)
+    with open(path, "wb") as f:
+        f.write(_CKPT_MAGIC)
+        f.write(struct.pack("<5q2d", vmc.W, vmc.N, vmc.seed, vmc.step_count, params.size, vmc.drift_a, tau))
+        f.write(R.tobytes())
+        f.write(params.tobytes())
+
+
+def read_checkpoint(path):
+    """The fields written by save_checkpoint, as a dict (host arrays)."""
+    import struct
+    with open(path, "rb") as f:
+        if f.read(8) != _CKPT_MAGIC:
+            raise ValueError("not a chain checkpoint: " + str(path))
+        W, N, seed, step, n_par, drift_a, tau = struct.unpack("<5q2d", f.read(56))
+        R = np.frombuffer(f.read(W * N * 3 * 8), dtype="<f8").reshape(W, N, 3).copy()
+        params = np.frombuffer(f.read(n_par * 4), dtype="<f4").copy()
+        if R.size != W * N * 3 or params.size != n_par:
+            raise ValueError("truncated chain checkpoint: " + str(path))
+    return dict(W=W, N=N, seed=seed, step=step, R=R, params=params, drift_a=drift_a,
+                drift_tau=None if tau != tau else tau)
+
+
+def resume_checkpoint(path, ctx, mlp=None):
+    """A VMC chain on ctx continuing from the checkpoint: positions, seed, step
+    and drift settings restored, the wavefunction re-evaluated at the positions,
+    and the network's parameters loaded into mlp when given."""
+    ck = read_checkpoint(path)
+    if ck["N"] != ctx.n_up + ctx.n_dn:
+        raise ValueError("checkpoint has %d electrons, the context %d" % (ck["N"], ctx.n_up + ctx.n_dn))
+    v = VMC(ctx, ck["R"], seed=ck["seed"], drift_a=ck["drift_a"], drift_tau=ck["drift_tau"])
+    v.step_count = ck["step"]
+    if mlp is not None:
+        if ck["params"].size != mlp.n_params:
+            raise ValueError("checkpoint network has %d parameters, the given one %d" % (ck["params"].size,
+                                                                                       mlp.n_params))
+        mlp.set_params(ck["params"])
+    return v
+
+
 def train_proposal(mlp, R0, R1, epochs=4, batch=8192, lr=1e-3, seed=0, log=None):
     """Maximum-likelihood fit of the perceptron's Gaussian move to observed
     moves R0 -> R1 (Adam on minibatches; the loss is the mean negative

@@ -264,3 +264,35 @@ def test_learned_proposal_gain_over_drift_diffusion(capsys):
     assert learned["acceptance"] > 0.05 and np.isfinite(gain) and gain > 0
     m.close()
     ctx.close()
+
+
+def test_chain_resumes_from_checkpoint(tmp_path):
+    """A chain resumed from its checkpoint continues the uninterrupted chain: the
+    same counter-based random numbers and the same network, so the positions
+    after further learned and drift-diffusion steps agree to rounding."""
+    from paper_1510_00730_gb300.vmc import VMC, resume_checkpoint, save_checkpoint
+    wl = synth.tiny(n_walk=256)
+    ctx = pkg.Context.from_workload(wl, device=0, precision=pkg.PRECISION_FP64)
+    tau = 0.1
+    m = B.MLP(0, wl.n_elec, hidden=32, seed=4, mu_max=1.0, s0=0.5 * math.log(tau), s_span=2.0, zero_head=False)
+    a = VMC(ctx, wl.R, seed=41, drift_tau=tau)
+    a.run(20, tau=tau, mlp=m, mix_drift=0.3, record=False)
+    p = tmp_path / "chain.bin"
+    save_checkpoint(p, a, m)
+    m2 = B.MLP(0, wl.n_elec, hidden=32, seed=99, mu_max=1.0, s0=0.5 * math.log(tau), s_span=2.0)
+    b = resume_checkpoint(p, ctx, m2)
+    assert b.step_count == a.step_count and np.array_equal(m2.params(), m.params())
+    for k in range(10):
+        if k % 3 == 2:
+            a.step_drift(tau)
+            b.step_drift(tau)
+        else:
+            a.step_mlp(m)
+            b.step_mlp(m2)
+    torch.cuda.synchronize()
+    ra, rb = a.cur["R"].cpu().numpy(), b.cur["R"].cpu().numpy()
+    same = np.abs(ra - rb).max(axis=(1, 2)) <= 1e-10
+    assert same.mean() >= 0.99, same.mean()  # an acceptance test within rounding of its threshold may flip
+    m.close()
+    m2.close()
+    ctx.close()

@@ -165,3 +165,35 @@ def test_speed_measure_gradient_closed_form_when_always_accepted():
     np.testing.assert_allclose(d0[:, 3 * n_elec:], -3 * beta * span * (1 - ts ** 2) / B, rtol=1e-6)
     np.testing.assert_allclose(d1, 0.0, atol=1e-9)
     assert abs(J - beta * 3 * (s0 + span * ts).sum(1).mean()) < 1e-12
+
+
+def test_checkpoint_round_trip(tmp_path):
+    """The flat chain checkpoint reads back exactly; a wrong magic or a truncated file is refused."""
+    import pytest
+    import torch
+    from types import SimpleNamespace
+
+    from paper_1510_00730_gb300.vmc import read_checkpoint, save_checkpoint
+    rng = np.random.default_rng(9)
+    R = rng.normal(size=(5, 3, 3))
+    vmc = SimpleNamespace(W=5, N=3, seed=123456789012, step_count=77, drift_a=1.0, drift_tau=3e-5,
+                          cur={"R": torch.from_numpy(R)})
+    params = rng.normal(size=41).astype(np.float32)
+    mlp = SimpleNamespace(params=lambda: params)
+    p = tmp_path / "chain.bin"
+    save_checkpoint(p, vmc, mlp)
+    ck = read_checkpoint(p)
+    assert (ck["W"], ck["N"], ck["seed"], ck["step"], ck["drift_a"], ck["drift_tau"]) == (5, 3, 123456789012, 77,
+                                                                                        1.0, 3e-5)
+    assert np.array_equal(ck["R"], R) and np.array_equal(ck["params"], params)
+    vmc.drift_tau = None
+    save_checkpoint(p, vmc)
+    ck = read_checkpoint(p)
+    assert ck["drift_tau"] is None and ck["params"].size == 0
+    data = p.read_bytes()
+    (tmp_path / "short.bin").write_bytes(data[:-8])
+    with pytest.raises(ValueError):
+        read_checkpoint(tmp_path / "short.bin")
+    (tmp_path / "bad.bin").write_bytes(b"NOTACKPT" + data[8:])
+    with pytest.raises(ValueError):
+        read_checkpoint(tmp_path / "bad.bin")
