@@ -263,3 +263,34 @@ def test_mixed_tensor_core_orbitals(name, ec):
     ref = oracle.evaluate(wl, R=wl.R[idx])
     rep = compare({k: v[idx] for k, v in got.items()}, ref, **TOL[pkg.PRECISION_MIXED])
     assert rep["ok"], rep
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("prec", PRECISIONS)
+def test_exchange_antisymmetry_full_size(cl750, prec):
+    """A property that holds at any size, checked on every walker of the
+    full-size workload in the bench's launch configuration: exchanging two
+    same-spin electrons (an up pair and a down pair) flips the sign of Psi,
+    keeps log|Psi| and permutes the gradients and Laplacians (Eq. 1: each spin
+    factor is a determinant)."""
+    wl = cl750[0] if isinstance(cl750, tuple) else cl750
+    ctx = pkg.Context.from_workload(wl, device=0, precision=prec)
+    a = _gpu_eval(ctx, wl.R)
+    for i, j in ((0, 3), (wl.n_up + 1, wl.n_up + 6)):
+        Rs = wl.R.copy()
+        Rs[:, [i, j]] = Rs[:, [j, i]]
+        b = _gpu_eval(ctx, Rs)
+        perm = np.arange(wl.n_elec)
+        perm[[i, j]] = perm[[j, i]]
+        ok = (a["status"] & (pkg.WS_REF_SINGULAR | pkg.WS_PSI_ZERO | pkg.WS_NONFINITE)) == 0
+        assert ok.mean() > 0.99
+        assert np.all(b["sign"][ok] == -a["sign"][ok])
+        d_log = np.abs(b["log_abs_psi"] - a["log_abs_psi"])[ok]
+        gs = np.sqrt(np.mean(a["grad"] ** 2, axis=(1, 2)))[:, None, None]
+        d_grad = (np.abs(b["grad"] - a["grad"][:, perm]) / np.maximum(np.abs(a["grad"][:, perm]), gs)).max(axis=(1, 2))[ok]
+        ls = np.sqrt(np.mean(a["lap"] ** 2, axis=1))[:, None]
+        d_lap = (np.abs(b["lap"] - a["lap"][:, perm]) / np.maximum(np.abs(a["lap"][:, perm]), ls)).max(axis=1)[ok]
+        tol = 1e-9 if prec == pkg.PRECISION_FP64 else 1e-7
+        for name, d in (("log", d_log), ("grad", d_grad), ("lap", d_lap)):
+            assert np.percentile(d, 99) <= tol, (name, np.percentile(d, 99), d.max())
+            assert d.max() <= 1e3 * tol, (name, d.max())
