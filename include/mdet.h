@@ -284,9 +284,12 @@ mdet_status mdet_set_walker_chunks(mdet_ctx* ctx, int n_chunks);
  * for the kernels of another walker chunk), mo_impl the mixed-precision
  * orbital product (1, the default: the compensated FP32 dot product on the
  * CUDA cores, accurate relative to each term; 0: BF16 tensor cores on exact
- * digit products, accurate to about 2^-55 of the row and column maxima).
+ * digit products, accurate to about 2^-55 of the row and column maxima),
+ * contract_impl the CI contraction of the mixed path (0, the default: FP64;
+ * 1: double-float pairs on the FP32 pipe with a compensated dot product, an
+ * option outside the FP64 contraction of the method's precision plan).
  * Defaults: spmm_chunk 512, mo_ec 4 (mixed) or 6 (FP64), walker_chunks 0,
- * spmm_blocks 0, mo_impl 1.
+ * spmm_blocks 0, mo_impl 1, contract_impl 0.
  * best_ms and trials are filled by mdet_autotune (the fastest step time seen
  * and the configurations timed).
  */
@@ -298,6 +301,7 @@ typedef struct {
   int32_t trials;
   int32_t spmm_blocks;
   int32_t mo_impl;
+  int32_t contract_impl;
 } mdet_tuning;
 
 mdet_status mdet_get_tuning(const mdet_ctx* ctx, mdet_tuning* out);

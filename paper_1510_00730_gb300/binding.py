@@ -34,7 +34,8 @@ class MdetError(RuntimeError):
 
 class _Tuning(C.Structure):
     _fields_ = [("spmm_chunk", C.c_int32), ("mo_ec", C.c_int32), ("walker_chunks", C.c_int32),
-                ("best_ms", C.c_float), ("trials", C.c_int32), ("spmm_blocks", C.c_int32), ("mo_impl", C.c_int32)]
+                ("best_ms", C.c_float), ("trials", C.c_int32), ("spmm_blocks", C.c_int32), ("mo_impl", C.c_int32),
+                ("contract_impl", C.c_int32)]
 
 
 class _Stats(C.Structure):
@@ -351,13 +352,14 @@ class Context:
         t = _Tuning()
         self._check(self._L.mdet_get_tuning(self._h, C.byref(t)), "mdet_get_tuning")
         return dict(spmm_chunk=t.spmm_chunk, mo_ec=t.mo_ec, walker_chunks=t.walker_chunks, best_ms=t.best_ms,
-                    trials=t.trials, spmm_blocks=t.spmm_blocks, mo_impl=t.mo_impl)
+                    trials=t.trials, spmm_blocks=t.spmm_blocks, mo_impl=t.mo_impl,
+                    contract_impl=t.contract_impl)
 
-    def set_tuning(self, spmm_chunk=512, mo_ec=None, walker_chunks=0, spmm_blocks=0, mo_impl=1):
-        """Tile shapes (mdet_set_tuning); mo_ec None keeps the context's current value."""
+    def set_tuning(self, spmm_chunk=512, mo_ec=None, walker_chunks=0, spmm_blocks=0, mo_impl=1, contract_impl=0):
+        """Tile shapes and kernel choices (mdet_set_tuning); mo_ec None keeps the context's current value."""
         if mo_ec is None:
             mo_ec = self.tuning()["mo_ec"]
-        t = _Tuning(spmm_chunk, mo_ec, walker_chunks, 0.0, 0, spmm_blocks, mo_impl)
+        t = _Tuning(spmm_chunk, mo_ec, walker_chunks, 0.0, 0, spmm_blocks, mo_impl, contract_impl)
         self._check(self._L.mdet_set_tuning(self._h, C.byref(t)), "mdet_set_tuning")
 
     def autotune(self, R, budget_ms=200.0):
@@ -366,7 +368,8 @@ class Context:
         self._check(self._L.mdet_autotune(self._h, R.shape[0], R.data_ptr(), float(budget_ms), C.byref(t)),
                     "mdet_autotune")
         return dict(spmm_chunk=t.spmm_chunk, mo_ec=t.mo_ec, walker_chunks=t.walker_chunks, best_ms=t.best_ms,
-                    trials=t.trials, spmm_blocks=t.spmm_blocks, mo_impl=t.mo_impl)
+                    trials=t.trials, spmm_blocks=t.spmm_blocks, mo_impl=t.mo_impl,
+                    contract_impl=t.contract_impl)
 
     def set_fallback(self, tol, max_walkers=64):
         """Re-evaluate walkers whose estimated table error exceeds tol by full LU (tol <= 0: off)."""

@@ -54,6 +54,7 @@ struct mdet_ctx {
   int spmm_blocks = 0;
   int mo_impl = 1;  // the compensated CUDA-core product (faster here than the tensor-core digits)
   int mo_ec = 4;
+  int contract_impl = 0;  // FP64 contraction (the double-float one is an option of the mixed path)
   mdet_tuning last_tune{};
   cudaStream_t cs[kMaxChunks] = {};
   cudaEvent_t fork = nullptr, joined[kMaxChunks] = {}, contracted[kMaxChunks] = {};
@@ -199,14 +200,13 @@ void free_problem(mdet_ctx* c) {
 
 void free_scratch(mdet_ctx* c) {
   DevScratch& S = c->S;
-  void* ptrs[] = {S.phi, S.Ainv, S.ld0, S.sg0, S.g, S.kap, S.est, S.T, S.Tdf, S.r, S.vu, S.psit, S.wstat,
+  void* ptrs[] = {S.phi, S.Ainv, S.ld0, S.sg0, S.g, S.kap, S.est, S.T, S.Tdf, S.r, S.rdf, S.vu, S.psit, S.wstat,
                   S.fb, S.fb_list, S.fb_acc, S.R_stage, S.out_stage};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   S = DevScratch{};
 }
 
-// Upload everything the kernels read (called once the expansion is complete).
 // Host step shared by both preprocessing paths. From the distinct determinants
 // of one spin in omega order (udets [nu][n_int]) and the omega index of the
 // reference: excitation degrees relative to the reference, the context order
@@ -267,6 +267,7 @@ mdet_status spin_tables(mdet_ctx* c, int sp, int n_int, const std::vector<uint64
   return MDET_OK;
 }
 
+// Upload everything the kernels read (called once the expansion is complete).
 mdet_status upload_problem(mdet_ctx* c) {
   if (c->device < 0) return MDET_OK;
   CUDA_TRY(c, cudaSetDevice(c->device));
@@ -281,6 +282,7 @@ mdet_status upload_problem(mdet_ctx* c) {
   P.spmm_blocks = c->spmm_blocks;
   P.mo_ec = c->mo_ec;
   P.mo_impl = c->mo_impl;
+  P.contract_impl = c->contract_impl;
   P.fallback_tol = c->fallback_tol;
   P.fallback_cap = c->fallback_cap;
   mdet_status s;
@@ -363,6 +365,11 @@ mdet_status upload_problem(mdet_ctx* c) {
   UP(c->coo_val, P.csc_val);
   UP(c->csr_ptr, P.csr_ptr);
   UP(c->csc_ptr, P.csc_ptr);
+  {  // C as double-float pairs for the optional double-float contraction
+    std::vector<float2> a = split(c->csr_val), b = split(c->coo_val);
+    UP(a, P.csr_val_df);
+    UP(b, P.csc_val_df);
+  }
   // the sequential chain of Sec. 2.2: distinct determinants in the order of the key of Eq. 3,
   // each with the substitutions from its predecessor (holes and particles ascending, paired in order)
   for (int sp = 0; sp < 2; sp++) {
@@ -434,6 +441,10 @@ mdet_status ensure_scratch(mdet_ctx* c, int64_t n_walk) {
     CUDA_TRY(c, cudaMemset(S.Tdf, 0, sizeof(float2) * N * M * wp));
   }
   if ((s = dalloc(c, &S.r, (size_t)ndt * wp))) return s;
+  if (c->precision == MDET_PRECISION_MIXED && c->contract_impl == 1) {
+    if ((s = dalloc(c, &S.rdf, (size_t)ndt * wp))) return s;
+    CUDA_TRY(c, cudaMemset(S.rdf, 0, sizeof(float2) * ndt * wp));
+  }
   if ((s = dalloc(c, &S.vu, (size_t)ndt * wp))) return s;  // walker-major [wp][ndt]
   if ((s = dalloc(c, &S.psit, (size_t)wp))) return s;
   if ((s = dalloc(c, &S.wstat, (size_t)W))) return s;
@@ -1042,6 +1053,7 @@ mdet_status mdet_get_tuning(const mdet_ctx* c, mdet_tuning* out) {
   out->walker_chunks = c->n_chunks_cfg;
   out->spmm_blocks = c->spmm_blocks;
   out->mo_impl = c->mo_impl;
+  out->contract_impl = c->contract_impl;
   return MDET_OK;
 }
 
@@ -1052,6 +1064,12 @@ mdet_status mdet_set_tuning(mdet_ctx* c, const mdet_tuning* t) {
   if (t->walker_chunks < 0) return fail(c, MDET_E_ARG, "walker_chunks < 0");
   if (t->spmm_blocks < 0) return fail(c, MDET_E_ARG, "spmm_blocks < 0");
   if (t->mo_impl != 0 && t->mo_impl != 1) return fail(c, MDET_E_ARG, "mo_impl must be 0 or 1");
+  if (t->contract_impl != 0 && t->contract_impl != 1) return fail(c, MDET_E_ARG, "contract_impl must be 0 or 1");
+  if (t->contract_impl != c->contract_impl) {
+    c->contract_impl = t->contract_impl;
+    c->P.contract_impl = t->contract_impl;
+    free_scratch(c);  // the double-float ratio pairs are allocated with the scratch
+  }
   c->mo_impl = t->mo_impl;
   c->P.mo_impl = t->mo_impl;
   c->spmm_blocks = t->spmm_blocks;

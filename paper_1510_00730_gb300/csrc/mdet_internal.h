@@ -41,6 +41,9 @@ struct DevProblem {
   int sm_n[2];
   int spmm_chunk;         // tuning: nonzeros per warp in the contraction
   int spmm_blocks;        // tuning: grid of the contraction (0: one warp per work item)
+  int contract_impl;      // tuning: contraction in FP64 (0) or double-float on the FP32 pipe (1, mixed only)
+  const float2* csr_val_df;  // C values as double-float pairs, row-major and column-major orders
+  const float2* csc_val_df;
   int mo_ec;              // tuning: electrons per CTA in the orbital kernels (4, 6 or 8)
   int mo_impl;            // tuning: mixed orbitals on the tensor cores (0) or the compensated FP32 dot product (1)
   const uint16_t* B_dig;  // [7][tc_mp][tc_kp] BF16 digits of the MO coefficients (column-scaled)
@@ -90,6 +93,7 @@ struct DevScratch {
   double* T = nullptr;    // [n_up + n_dn][n_mo][wp] walker-minor ratio tables (up block then down block)
   float2* Tdf = nullptr;  // same as double-float pairs (hi, lo), mixed path only
   double* r = nullptr;    // [n_det_up + n_det_dn][wp] ratios D_I / D_ref, walker-minor
+  float2* rdf = nullptr;  // same as double-float pairs (mixed path with the double-float contraction only)
   double* vu = nullptr;   // walker-major [wp][n_det_up + n_det_dn]: v = C r_dn (up) then u = C^T r_up (down)
   double* psit = nullptr; // [wp] Psi / (D_ref_up D_ref_dn)
   uint32_t* wstat = nullptr;  // [W] status bits

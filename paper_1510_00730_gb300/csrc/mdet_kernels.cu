@@ -360,6 +360,74 @@ __global__ void __launch_bounds__(128) k_spmm_wm(const int* __restrict__ seg, co
   }
 }
 
+// The same segmented product with the ratios and C as double-float pairs on
+// the FP32 pipe (an option of the mixed path; the default contraction is the
+// FP64 kernel above): per walker the compensated dot product of Ogita, Rump and
+// Oishi (TwoProd of the leading words, TwoSum into the running sum, cross terms
+// and all rounding errors into a second word), about 13 FP32 instructions per
+// nonzero instead of one FP64 FMA at 1/54 of the FP32 rate. Segment sums are
+// converted to FP64 at the flush.
+__global__ void __launch_bounds__(128) k_spmm_df(const int* __restrict__ seg, const int* __restrict__ gidx,
+                                                 const float2* __restrict__ val, int64_t nnz, int chunk,
+                                                 int64_t n_chunks, int64_t n_groups,
+                                                 const float2* __restrict__ x, int64_t wp,
+                                                 double* __restrict__ y, int64_t ldy, int seg_off,
+                                                 const double* __restrict__ rdot, double* __restrict__ psit) {
+  const int lane = threadIdx.x & 31;
+  const int64_t nwarps = (int64_t)gridDim.x * (blockDim.x >> 5);
+  for (int64_t item = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); item < n_chunks * n_groups;
+       item += nwarps) {
+    const int64_t ch = item % n_chunks, grp = item / n_chunks;
+    const int64_t k0 = ch * chunk, k1 = min(k0 + (int64_t)chunk, nnz);
+    const int64_t wb = grp * 256 + lane * 8;
+    float s[8], e[8];
+#pragma unroll
+    for (int j = 0; j < 8; j++) s[j] = e[j] = 0.0f;
+    int cur = __ldg(seg + k0);
+    auto flush = [&](int sg) {
+      const double* rp = rdot ? rdot + (size_t)sg * wp + wb : nullptr;
+#pragma unroll
+      for (int j = 0; j < 8; j++) {
+        const double v = (double)s[j] + (double)e[j];
+        atomicAdd(y + (wb + j) * ldy + seg_off + sg, v);
+        if (rp) atomicAdd(psit + wb + j, rp[j] * v);
+      }
+    };
+    for (int64_t k = k0; k < k1; k++) {
+      const int sg = __ldg(seg + k);
+      if (sg != cur) {
+        flush(cur);
+        cur = sg;
+#pragma unroll
+        for (int j = 0; j < 8; j++) s[j] = e[j] = 0.0f;
+      }
+      const float2 c = __ldg(val + k);
+      const float4* xp = reinterpret_cast<const float4*>(x + (size_t)__ldg(gidx + k) * wp + wb);
+      float xs[16];
+#pragma unroll
+      for (int q = 0; q < 4; q++) {
+        const float4 v = __ldg(xp + q);
+        xs[4 * q] = v.x;
+        xs[4 * q + 1] = v.y;
+        xs[4 * q + 2] = v.z;
+        xs[4 * q + 3] = v.w;
+      }
+#pragma unroll
+      for (int j = 0; j < 8; j++) {
+        const float xh = xs[2 * j], xl = xs[2 * j + 1];
+        const float p = __fmul_rn(c.x, xh);
+        const float pe = __fmaf_rn(c.x, xh, -p);
+        const float cross = __fmaf_rn(c.x, xl, __fmul_rn(c.y, xh));
+        float t, err;
+        two_sum(s[j], p, t, err);
+        s[j] = t;
+        e[j] = __fadd_rn(e[j], __fadd_rn(err, __fadd_rn(pe, cross)));
+      }
+    }
+    flush(cur);
+  }
+}
+
 // ---------------------------------------------------------------------------
 // K6: per walker: W scatter over every determinant, Q = A^T W, Pm = T Q^T,
 // G_{i mu} = g Psi~ + sum_m d_mu phi[i][m] Q[i][m] - sum_b d_mu phi[i][o_b] Pm[b][i],
@@ -700,6 +768,17 @@ cudaError_t launch_contract_f64(const DevProblem& P, const DevScratch& S, int64_
   const int64_t ndt = (int64_t)P.n_det_sp[0] + P.n_det_sp[1];
   const double* r_up = S.r;
   const double* r_dn = S.r + (size_t)P.n_det_sp[0] * S.wp;
+  if (P.contract_impl == 1 && S.rdf && P.csr_val_df) {  // double-float option of the mixed path
+    const float2* x_up = S.rdf;
+    const float2* x_dn = S.rdf + (size_t)P.n_det_sp[0] * S.wp;
+    k_spmm_df<<<(unsigned)blocks, 128, 0, st>>>(P.csr_row, P.csr_col, P.csr_val_df, P.nnz, chunk, n_chunks,
+                                                 n_groups, x_dn, S.wp, S.vu, ndt, 0, r_up, S.psit);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    k_spmm_df<<<(unsigned)blocks, 128, 0, st>>>(P.csc_col, P.csc_row, P.csc_val_df, P.nnz, chunk, n_chunks,
+                                                 n_groups, x_up, S.wp, S.vu, ndt, P.n_det_sp[0], nullptr, nullptr);
+    return cudaGetLastError();
+  }
   // v = C r_dn (rows = up determinants) with Psi~ = r_up . v
   k_spmm_wm<<<(unsigned)blocks, 128, 0, st>>>(P.csr_row, P.csr_col, P.csr_val, P.nnz, chunk, n_chunks, n_groups,
                                                r_dn, S.wp, S.vu, ndt, 0, r_up, S.psit);
@@ -728,6 +807,7 @@ DevScratch scratch_view(const DevScratch& S, const DevProblem& P, int64_t off) {
   V.T = S.T + off;  // walker-minor: a column offset with the same stride
   if (S.Tdf) V.Tdf = S.Tdf + off;
   V.r = S.r + off;
+  if (S.rdf) V.rdf = S.rdf + off;
   V.psit = S.psit + off;
   return V;
 }

@@ -294,3 +294,28 @@ def test_exchange_antisymmetry_full_size(cl750, prec):
         for name, d in (("log", d_log), ("grad", d_grad), ("lap", d_lap)):
             assert np.percentile(d, 99) <= tol, (name, np.percentile(d, 99), d.max())
             assert d.max() <= 1e3 * tol, (name, d.max())
+
+
+@pytest.mark.parametrize("name", ["oxygen_like_1k", "chlorine_like_100k"])
+def test_mixed_double_float_contraction(name):
+    """The optional double-float contraction of the mixed path (contract_impl = 1)
+    against the oracle; the 10^5 expansion on 32 sampled walkers."""
+    wl = synth.WORKLOADS[name]()
+    ctx = pkg.Context.from_workload(wl, device=0, precision=pkg.PRECISION_MIXED)
+    ctx.set_tuning(contract_impl=1)
+    assert ctx.tuning()["contract_impl"] == 1
+    got = _gpu_eval(ctx, wl.R)
+    idx = np.arange(wl.n_walk) if wl.n_walk <= 64 else np.random.default_rng(3).choice(wl.n_walk, 32, replace=False)
+    ref = oracle.evaluate(wl, R=wl.R[idx])
+    rep = compare({k: v[idx] for k, v in got.items()}, ref, **TOL[pkg.PRECISION_MIXED])
+    assert rep["ok"], rep
+
+
+@pytest.mark.slow
+def test_mixed_double_float_contraction_full_size(cl750):
+    wl, idx, ref = cl750
+    ctx = pkg.Context.from_workload(wl, device=0, precision=pkg.PRECISION_MIXED)
+    ctx.set_tuning(contract_impl=1)
+    got = _gpu_eval(ctx, wl.R)
+    rep = compare({k: v[idx] for k, v in got.items()}, ref, **TOL[pkg.PRECISION_MIXED])
+    assert rep["ok"], rep
