@@ -416,7 +416,7 @@ mdet_status mdet_selftest_df32(int device, int64_t n, const double* x, double* y
  */
 mdet_status mdet_get_error_estimates(mdet_ctx* ctx, int64_t n_walk, double* cond1, double* est);
 
-/* Sizes and excitation statistics (host only; works without a device). *//* Sizes and excitation statistics (host only; works without a device). */
+/* Sizes and excitation statistics (host only; works without a device). */
 mdet_status mdet_get_stats(const mdet_ctx* ctx, mdet_stats* out);
 
 /*

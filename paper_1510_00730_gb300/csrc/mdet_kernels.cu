@@ -5,7 +5,10 @@
 //                    single-determinant derivatives g (Sec. 2.2; Sec. 5 Table method)
 //   k_ratio_f64      D_I / D_ref = eps_I det T[h_I, p_I] for every distinct
 //                    spin determinant (k x k, k <= 4)
-//   k_spmm_f64       v = C r_dn (plus Psi~ = r_up . v) and u = C^T r_up (Sec. 2.4)
+//   k_spmm_wm        v = C r_dn (plus Psi~ = r_up . v) and u = C^T r_up (Sec. 2.4),
+//                    8 walkers per lane, walker-major output (k_spmm_df: the
+//                    double-float option of the mixed path; k_spmm_f64: the
+//                    walker-minor form used by the allocation-free entry point)
 //   k_final          derivative aggregation and the per-walker epilogue (Eqs. 5-8)
 // k_ref and k_final take a MIXED flag: the mixed-precision variants (and the
 // mixed orbital and ratio kernels of mdet_kernels_mixed.cu) run the
