@@ -303,12 +303,8 @@ cudaError_t launch_fallback(const DevProblem& P, const DevScratch& S, int64_t n_
   const int nmax = P.n_up > P.n_dn ? P.n_up : P.n_dn;
   const int ntot = P.n_det_sp[0] + P.n_det_sp[1];
   const size_t smem = sizeof(double) * 64 * nmax * nmax;
-  static size_t attr_bytes = 0;
-  if (smem > attr_bytes) {
-    if ((e = cudaFuncSetAttribute(k_fb_dets, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess)
-      return e;
-    attr_bytes = smem;
-  }
+  static SmemOptIn opt;
+  if ((e = opt.ensure(k_fb_dets, smem)) != cudaSuccess) return e;
   dim3 g1((ntot + 63) / 64, P.fallback_cap);
   k_fb_dets<<<g1, 64, smem, st>>>(P, S);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;

@@ -2,6 +2,7 @@
 // Not part of the public ABI.
 #pragma once
 
+#include <atomic>
 #include <cstdint>
 #include <string>
 #include <vector>
@@ -16,6 +17,28 @@ constexpr int kMaxSpin = MDET_MAX_SPIN_ELEC;
 constexpr int kMaxExc = MDET_MAX_EXC;
 constexpr int kMaxL = MDET_MAX_L;
 constexpr int kWalkerPad = 256;  // walker-minor arrays are padded to a multiple of this
+
+// Dynamic shared memory a kernel has been opted into, per device (a function
+// attribute belongs to each device's context). Concurrent callers at worst
+// repeat the attribute call.
+struct SmemOptIn {
+  static constexpr int kMaxDevices = 64;
+  std::atomic<size_t> bytes[kMaxDevices] = {};
+  template <class K>
+  cudaError_t ensure(K kernel, size_t need) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev >= 0 && dev < kMaxDevices && need <= bytes[dev].load()) return cudaSuccess;
+    e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)need);
+    if (e == cudaSuccess && dev >= 0 && dev < kMaxDevices) {
+      size_t cur = bytes[dev].load();
+      while (cur < need && !bytes[dev].compare_exchange_weak(cur, need)) {
+      }
+    }
+    return e;
+  }
+};
 
 // Excitation of one distinct spin determinant relative to the reference of its
 // spin: columns h[0..k) of the reference Slater matrix (hole positions, in the

@@ -707,12 +707,9 @@ template <int EC>
 static cudaError_t launch_mo_f64_ec(const DevProblem& P, const DevScratch& S, int64_t n_walk, const double* R,
                                    cudaStream_t st) {
   const size_t smem = sizeof(double) * 5 * EC * P.n_ao;
-  static size_t attr_bytes = 0;  // dynamic shared memory opted in so far (static arrays come on top)
-  if (smem > attr_bytes) {
-    cudaError_t e = cudaFuncSetAttribute(k_mo_f64<EC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    attr_bytes = smem;
-  }
+  static SmemOptIn opt;  // dynamic shared memory (static arrays come on top)
+  cudaError_t e = opt.ensure(k_mo_f64<EC>, smem);
+  if (e != cudaSuccess) return e;
   dim3 grid((unsigned)n_walk, (P.n_elec + EC - 1) / EC);
   k_mo_f64<EC><<<grid, 128, smem, st>>>(P, S.phi, R);
   return cudaGetLastError();
@@ -836,12 +833,9 @@ cudaError_t launch_final(const DevProblem& P, const DevScratch& S, int64_t n_wal
                          uint32_t* status, bool mixed, cudaStream_t st) {
   const size_t smem = final_smem_bytes(P, mixed);
   auto kern = mixed ? k_final<true> : k_final<false>;
-  static size_t attr_bytes[2] = {0, 0};  // dynamic shared memory opted in so far (static arrays come on top)
-  if (smem > attr_bytes[mixed]) {
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    attr_bytes[mixed] = smem;
-  }
+  static SmemOptIn opt[2];  // dynamic shared memory per variant (static arrays come on top)
+  cudaError_t e = opt[mixed].ensure(kern, smem);
+  if (e != cudaSuccess) return e;
   kern<<<(unsigned)n_walk, 128, smem, st>>>(P, S, R, log_abs_psi, sign, grad, lap, e_local, status);
   return cudaGetLastError();
 }

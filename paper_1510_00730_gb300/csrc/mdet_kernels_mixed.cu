@@ -306,12 +306,9 @@ template <int EC>
 static cudaError_t launch_mo_mixed_ec(const DevProblem& P, const DevScratch& S, int64_t n_walk, const double* R,
                                      cudaStream_t st) {
   const size_t smem = sizeof(float) * 2 * 5 * EC * P.n_ao;
-  static size_t attr_bytes = 0;  // dynamic shared memory opted in so far (static arrays come on top)
-  if (smem > attr_bytes) {
-    cudaError_t e = cudaFuncSetAttribute(k_mo_mixed<EC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    attr_bytes = smem;
-  }
+  static SmemOptIn opt;  // dynamic shared memory (static arrays come on top)
+  cudaError_t e = opt.ensure(k_mo_mixed<EC>, smem);
+  if (e != cudaSuccess) return e;
   dim3 grid((unsigned)n_walk, (P.n_elec + EC - 1) / EC);
   k_mo_mixed<EC><<<grid, 128, smem, st>>>(P, S.phi, R);
   return cudaGetLastError();
@@ -326,12 +323,9 @@ template <int EC>
 static cudaError_t launch_mo_tc_ec(const DevProblem& P, const DevScratch& S, int64_t n_walk, const double* R,
                                    cudaStream_t st) {
   const size_t smem = mo_tc_smem_bytes(P, EC);
-  static size_t attr_bytes = 0;
-  if (smem > attr_bytes) {
-    cudaError_t e = cudaFuncSetAttribute(k_mo_tc<EC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    attr_bytes = smem;
-  }
+  static SmemOptIn opt;
+  cudaError_t e = opt.ensure(k_mo_tc<EC>, smem);
+  if (e != cudaSuccess) return e;
   dim3 grid((unsigned)n_walk, (P.n_elec + EC - 1) / EC);
   k_mo_tc<EC><<<grid, 128, smem, st>>>(P, S.phi, R);
   return cudaGetLastError();
