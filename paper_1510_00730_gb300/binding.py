@@ -142,6 +142,28 @@ def load_library(build_if_missing: bool = True):
     return L
 
 
+def _need(t, name, shape, dtype, device):
+    """t must be a contiguous CUDA tensor of exactly this shape and dtype on
+    `device`: the kernels read and write that many elements, so any other
+    buffer would be an out-of-bounds access. Raises ValueError otherwise."""
+    import torch
+    ok = (isinstance(t, torch.Tensor) and t.is_cuda and t.device == device and t.dtype == dtype
+          and t.is_contiguous() and tuple(t.shape) == tuple(shape))
+    if not ok:
+        got = ("%s %s on %s%s" % (tuple(t.shape), t.dtype, t.device, "" if t.is_contiguous() else ", strided")
+               if isinstance(t, torch.Tensor) else type(t).__name__)
+        raise ValueError("%s must be a contiguous %s tensor of shape %s on %s (got %s)" % (name, dtype, tuple(shape),
+                                                                                         device, got))
+    return t
+
+
+def _need_np(a, name, shape, dtype):
+    """The host counterpart of _need for numpy output arrays."""
+    if not (isinstance(a, np.ndarray) and a.dtype == dtype and a.shape == tuple(shape) and a.flags.c_contiguous):
+        raise ValueError("%s must be a C-contiguous %s array of shape %s" % (name, np.dtype(dtype), tuple(shape)))
+    return a
+
+
 def _ptr(a) -> int:
     return a.ctypes.data if a is not None else None
 
@@ -297,11 +319,16 @@ class Context:
         Returns (and fills) a dict of device tensors; asynchronous on `stream`
         (default: torch's current stream)."""
         import torch
-        if not (R.is_cuda and R.dtype == torch.float64 and R.is_contiguous()):
-            raise ValueError("R must be a contiguous CUDA float64 tensor")
-        n_walk = R.shape[0]
+        dev = torch.device("cuda", self.device)
+        N = self.n_up + self.n_dn
+        n_walk = R.shape[0] if isinstance(R, torch.Tensor) and R.dim() == 3 else -1
+        _need(R, "R", (n_walk, N, 3), torch.float64, dev)
         if out is None:
             out = self.alloc_outputs(n_walk)
+        for k, shape, dt in (("log_abs_psi", (n_walk,), torch.float64), ("sign", (n_walk,), torch.int8),
+                             ("grad", (n_walk, N, 3), torch.float64), ("lap", (n_walk, N), torch.float64),
+                             ("e_local", (n_walk,), torch.float64), ("status", (n_walk,), torch.int32)):
+            _need(out[k], "out['%s']" % k, shape, dt, dev)
         if stream is None:
             stream = torch.cuda.current_stream(R.device)
         sp = stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream)
@@ -313,11 +340,19 @@ class Context:
     def evaluate_host(self, R, out=None):
         """Host-memory evaluation (copies inside the call); returns numpy arrays."""
         R = _c(R, np.float64)
-        n_walk = R.shape[0]
         N = self.n_up + self.n_dn
+        if R.ndim != 3 or R.shape[1:] != (N, 3):
+            raise ValueError("R must have shape [n_walk, %d, 3]" % N)
+        n_walk = R.shape[0]
         if out is None:
             out = dict(log_abs_psi=np.empty(n_walk), sign=np.empty(n_walk, np.int8), grad=np.empty((n_walk, N, 3)),
                        lap=np.empty((n_walk, N)), e_local=np.empty(n_walk), status=np.empty(n_walk, np.uint32))
+        for k, shape, dt in (("log_abs_psi", (n_walk,), np.float64), ("sign", (n_walk,), np.int8),
+                             ("grad", (n_walk, N, 3), np.float64), ("lap", (n_walk, N), np.float64),
+                             ("e_local", (n_walk,), np.float64)):
+            _need_np(out[k], "out['%s']" % k, shape, dt)
+        if out["status"].shape != (n_walk,) or out["status"].dtype.itemsize != 4:
+            raise ValueError("out['status'] must be a 32-bit array of shape (%d,)" % n_walk)
         self._check(self._L.mdet_evaluate_host(self._h, n_walk, _ptr(R), _ptr(out["log_abs_psi"]), _ptr(out["sign"]),
                                                _ptr(out["grad"]), _ptr(out["lap"]), _ptr(out["e_local"]),
                                                _ptr(out["status"])), "mdet_evaluate_host")
@@ -539,13 +574,30 @@ def philox4x32_10(ctr, key):
     return [int(v) for v in o]
 
 
+def _walkers(R):
+    import torch
+    if not (isinstance(R, torch.Tensor) and R.dim() == 3 and R.shape[2] == 3):
+        raise ValueError("R must be a [n_walk, n_elec, 3] tensor")
+    return R.shape[0], R.shape[1], R.device
+
+
 def vmc_propose_drift(R, grad, tau, seed, step, R_new, log_q, stream=None):
+    import torch
+    W, N, dev = _walkers(R)
+    for t, n in ((R, "R"), (grad, "grad"), (R_new, "R_new")):
+        _need(t, n, (W, N, 3), torch.float64, dev)
+    _need(log_q, "log_q", (W,), torch.float64, dev)
     _chk(load_library().mdet_vmc_propose_drift(R.shape[0], R.shape[1], R.data_ptr(), grad.data_ptr(), float(tau),
                                                int(seed), int(step), R_new.data_ptr(), log_q.data_ptr(),
                                                _sp(stream, R.device)), "mdet_vmc_propose_drift")
 
 
 def vmc_reverse_drift(R, R_new, grad_new, tau, log_q, stream=None):
+    import torch
+    W, N, dev = _walkers(R)
+    for t, n in ((R, "R"), (R_new, "R_new"), (grad_new, "grad_new")):
+        _need(t, n, (W, N, 3), torch.float64, dev)
+    _need(log_q, "log_q", (W,), torch.float64, dev)
     _chk(load_library().mdet_vmc_reverse_drift(R.shape[0], R.shape[1], R.data_ptr(), R_new.data_ptr(),
                                                grad_new.data_ptr(), float(tau), log_q.data_ptr(),
                                                _sp(stream, R.device)), "mdet_vmc_reverse_drift")
@@ -553,7 +605,22 @@ def vmc_reverse_drift(R, R_new, grad_new, tau, log_q, stream=None):
 
 def vmc_accept(seed, step, log_q_fwd, log_q_rev, cur, new, accept=None, n_accept=None, stream=None):
     """cur / new: dicts with R, log_abs_psi, sign, grad, lap, e_local (device tensors)."""
+    import torch
     R = cur["R"]
+    W, N, dev = _walkers(R)
+    for d, tag in ((cur, "cur"), (new, "new")):
+        _need(d["R"], tag + "['R']", (W, N, 3), torch.float64, dev)
+        _need(d["grad"], tag + "['grad']", (W, N, 3), torch.float64, dev)
+        _need(d["lap"], tag + "['lap']", (W, N), torch.float64, dev)
+        _need(d["sign"], tag + "['sign']", (W,), torch.int8, dev)
+        for k in ("log_abs_psi", "e_local"):
+            _need(d[k], "%s['%s']" % (tag, k), (W,), torch.float64, dev)
+    for t, n in ((log_q_fwd, "log_q_fwd"), (log_q_rev, "log_q_rev")):
+        _need(t, n, (W,), torch.float64, dev)
+    if accept is not None:
+        _need(accept, "accept", (W,), torch.int32, dev)
+    if n_accept is not None:
+        _need(n_accept, "n_accept", (1,), torch.int32, dev)
     _chk(load_library().mdet_vmc_accept(
         R.shape[0], R.shape[1], int(seed), int(step), log_q_fwd.data_ptr(), log_q_rev.data_ptr(), R.data_ptr(),
         cur["log_abs_psi"].data_ptr(), cur["sign"].data_ptr(), cur["grad"].data_ptr(), cur["lap"].data_ptr(),
@@ -565,17 +632,31 @@ def vmc_accept(seed, step, log_q_fwd, log_q_rev, cur, new, accept=None, n_accept
 
 def vmc_limit_drift(F, tau, a, F_bar, stream=None):
     """Per-electron drift limiting (Umrigar, Nightingale and Runge); a = 0 copies F."""
+    import torch
+    W, N, dev = _walkers(F)
+    _need(F, "F", (W, N, 3), torch.float64, dev)
+    _need(F_bar, "F_bar", (W, N, 3), torch.float64, dev)
     _chk(load_library().mdet_vmc_limit_drift(F.shape[0], F.shape[1], F.data_ptr(), float(tau), float(a),
                                              F_bar.data_ptr(), _sp(stream, F.device)), "mdet_vmc_limit_drift")
 
 
 def vmc_select_rows(take, src, dst, stream=None):
     """dst[w] = src[w] where take[w] != 0 (float32 rows)."""
+    import torch
+    if not (isinstance(src, torch.Tensor) and src.dim() == 2):
+        raise ValueError("src must be a [n_walk, width] tensor")
+    _need(src, "src", tuple(src.shape), torch.float32, src.device)
+    _need(dst, "dst", tuple(src.shape), torch.float32, src.device)
+    _need(take, "take", (src.shape[0],), torch.int32, src.device)
     _chk(load_library().mdet_vmc_select_rows(src.shape[0], src.shape[1], take.data_ptr(), src.data_ptr(),
                                              dst.data_ptr(), _sp(stream, src.device)), "mdet_vmc_select_rows")
 
 
 def vmc_r2(R, r2, stream=None):
+    import torch
+    W, N, dev = _walkers(R)
+    _need(R, "R", (W, N, 3), torch.float64, dev)
+    _need(r2, "r2", (W,), torch.float64, dev)
     _chk(load_library().mdet_vmc_r2(R.shape[0], R.shape[1], R.data_ptr(), r2.data_ptr(), _sp(stream, R.device)),
          "mdet_vmc_r2")
 
@@ -629,19 +710,41 @@ class MLP:
         _chk(self._L.mdet_mlp_get_grads(self._h, _ptr(g)), "mdet_mlp_get_grads")
         return g
 
+    def _pos(self, R, name="R"):
+        """(n_walk, device) of a position tensor [n_walk, n_elec, 3] float64 on this network's device."""
+        import torch
+        dev = torch.device("cuda", self.device)
+        n = R.shape[0] if isinstance(R, torch.Tensor) and R.dim() == 3 else -1
+        _need(R, name, (n, self.n_elec, 3), torch.float64, dev)
+        return n, dev
+
+    def _outs(self, n, dev, **tensors):
+        import torch
+        for name, t in tensors.items():
+            _need(t, name, (n, 4 * self.n_elec), torch.float32, dev)
+
     def forward(self, R, out=None, stream=None):
         import torch
+        n, dev = self._pos(R)
         if out is None:
-            out = torch.empty(R.shape[0], 4 * self.n_elec, dtype=torch.float32, device=R.device)
-        _chk(self._L.mdet_mlp_forward(self._h, R.shape[0], R.data_ptr(), out.data_ptr(), _sp(stream, R.device)),
+            out = torch.empty(n, 4 * self.n_elec, dtype=torch.float32, device=dev)
+        self._outs(n, dev, out=out)
+        _chk(self._L.mdet_mlp_forward(self._h, n, R.data_ptr(), out.data_ptr(), _sp(stream, dev)),
              "mdet_mlp_forward")
+        self._last_n = n
         return out
 
     def backward(self, dout, stream=None):
-        _chk(self._L.mdet_mlp_backward(self._h, dout.shape[0], dout.data_ptr(), _sp(stream, dout.device)),
-             "mdet_mlp_backward")
+        """Backward pass of the last forward (dout has its walker count)."""
+        import torch
+        dev = torch.device("cuda", self.device)
+        n = getattr(self, "_last_n", None)
+        if n is None:
+            raise ValueError("backward needs a forward pass first")
+        self._outs(n, dev, dout=dout)
+        _chk(self._L.mdet_mlp_backward(self._h, n, dout.data_ptr(), _sp(stream, dev)), "mdet_mlp_backward")
 
-    def zero_grad(self, stream=None, device=None):
+    def zero_grad(self, stream=None):
         import torch
         _chk(self._L.mdet_mlp_zero_grad(self._h, _sp(stream, torch.device("cuda", self.device))), "mdet_mlp_zero_grad")
 
@@ -651,6 +754,11 @@ class MLP:
                                    _sp(stream, torch.device("cuda", self.device))), "mdet_mlp_adam")
 
     def nll_grad(self, R0, R1, out, dout, loss, stream=None):
+        import torch
+        n, dev = self._pos(R0, "R0")
+        _need(R1, "R1", (n, self.n_elec, 3), torch.float64, dev)
+        self._outs(n, dev, out=out, dout=dout)
+        _need(loss, "loss", (1,), torch.float64, dev)
         _chk(self._L.mdet_mlp_nll_grad(self._h, R0.shape[0], R0.data_ptr(), R1.data_ptr(), out.data_ptr(),
                                        dout.data_ptr(), loss.data_ptr(), _sp(stream, R0.device)), "mdet_mlp_nll_grad")
 
@@ -659,7 +767,17 @@ class MLP:
         """drift, drift_new: the drift arrays of the forward move and the reverse
         density (e.g. limited); grad_new: grad Psi / Psi at R_new; objective: two
         device doubles (J, mean acceptance); speed_beta > 0 selects the speed measure."""
+        import torch
         lg = self.langevin
+        n, dev = self._pos(R)
+        for t, name in ((R_new, "R_new"), (grad_new, "grad_new")) + (((drift, "drift"), (drift_new, "drift_new"))
+                                                                   if lg else ()):
+            _need(t, name, (n, self.n_elec, 3), torch.float64, dev)
+        self._outs(n, dev, out=out, out_new=out_new, dout=dout, dout_new=dout_new)
+        _need(log_abs_psi, "log_abs_psi", (n,), torch.float64, dev)
+        _need(log_abs_psi_new, "log_abs_psi_new", (n,), torch.float64, dev)
+        _need(sign_new, "sign_new", (n,), torch.int8, dev)
+        _need(objective, "objective", (2,), torch.float64, dev)
         _chk(self._L.mdet_mlp_esjd_grad(self._h, R.shape[0], R.data_ptr(), R_new.data_ptr(), out.data_ptr(),
                                         out_new.data_ptr(), log_abs_psi.data_ptr(), log_abs_psi_new.data_ptr(),
                                         sign_new.data_ptr(), drift.data_ptr() if lg else None,
@@ -670,8 +788,15 @@ class MLP:
 
     def propose(self, R, out, seed, step, R_new, log_q, drift=None, stream=None):
         """drift: grad Psi / Psi at R, required for the Langevin form."""
+        import torch
         if self.langevin and drift is None:
             raise ValueError("the Langevin form needs the drift at R")
+        n, dev = self._pos(R)
+        _need(R_new, "R_new", (n, self.n_elec, 3), torch.float64, dev)
+        if self.langevin:
+            _need(drift, "drift", (n, self.n_elec, 3), torch.float64, dev)
+        self._outs(n, dev, out=out)
+        _need(log_q, "log_q", (n,), torch.float64, dev)
         _chk(self._L.mdet_vmc_propose_mlp(self._h, R.shape[0], R.data_ptr(), out.data_ptr(),
                                           drift.data_ptr() if self.langevin else None, int(seed), int(step),
                                           R_new.data_ptr(), log_q.data_ptr(), _sp(stream, R.device)),
@@ -679,8 +804,15 @@ class MLP:
 
     def reverse(self, R, R_new, out_new, log_q, drift_new=None, stream=None):
         """drift_new: grad Psi / Psi at R_new, required for the Langevin form."""
+        import torch
         if self.langevin and drift_new is None:
             raise ValueError("the Langevin form needs the drift at R_new")
+        n, dev = self._pos(R)
+        _need(R_new, "R_new", (n, self.n_elec, 3), torch.float64, dev)
+        if self.langevin:
+            _need(drift_new, "drift_new", (n, self.n_elec, 3), torch.float64, dev)
+        self._outs(n, dev, out_new=out_new)
+        _need(log_q, "log_q", (n,), torch.float64, dev)
         _chk(self._L.mdet_vmc_reverse_mlp(self._h, R.shape[0], R.data_ptr(), R_new.data_ptr(), out_new.data_ptr(),
                                           drift_new.data_ptr() if self.langevin else None, log_q.data_ptr(),
                                           _sp(stream, R.device)), "mdet_vmc_reverse_mlp")

@@ -319,3 +319,27 @@ def test_mixed_double_float_contraction_full_size(cl750):
     got = _gpu_eval(ctx, wl.R)
     rep = compare({k: v[idx] for k, v in got.items()}, ref, **TOL[pkg.PRECISION_MIXED])
     assert rep["ok"], rep
+
+
+def test_binding_refuses_mismatched_buffers(o1k):
+    """Buffers of the wrong shape, dtype, layout or device are refused before any
+    kernel runs (the kernels would otherwise read or write out of bounds)."""
+    wl, _ = o1k
+    ctx = pkg.Context.from_workload(wl, device=0, precision=pkg.PRECISION_FP64)
+    R = torch.from_numpy(wl.R).to("cuda:0")
+    with pytest.raises(ValueError):
+        ctx.evaluate(R.float())
+    with pytest.raises(ValueError):
+        ctx.evaluate(R[:, :4])
+    with pytest.raises(ValueError):
+        ctx.evaluate(R.cpu())
+    with pytest.raises(ValueError):
+        ctx.evaluate(R.transpose(0, 1).contiguous().transpose(0, 1))
+    out = ctx.alloc_outputs(wl.n_walk - 1)
+    with pytest.raises(ValueError):
+        ctx.evaluate(R, out=out)
+    with pytest.raises(ValueError):
+        ctx.evaluate_host(wl.R, out=dict(log_abs_psi=np.empty(3)))
+    good = ctx.evaluate(R)
+    torch.cuda.synchronize()
+    assert np.all(np.isfinite(good["log_abs_psi"].cpu().numpy()))
