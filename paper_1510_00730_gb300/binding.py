@@ -375,8 +375,13 @@ class Context:
         [n_det_up + n_det_dn, ld]) into psi_tilde (CUDA float64, [n_walk]),
         using the library's static scratch instead of any device allocation."""
         import torch
+        dev = torch.device("cuda", self.device)
+        st = self.stats()
+        n_walk = psi_tilde.shape[0] if isinstance(psi_tilde, torch.Tensor) and psi_tilde.dim() == 1 else -1
+        _need(psi_tilde, "psi_tilde", (n_walk,), torch.float64, dev)
+        _need(r, "r", (st["n_det_up"] + st["n_det_dn"], int(ld)), torch.float64, dev)
         if stream is None:
-            stream = torch.cuda.current_stream(psi_tilde.device)
+            stream = torch.cuda.current_stream(dev)
         sp = stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream)
         self._check(self._L.mdet_psi_tilde_noalloc(self._h, psi_tilde.shape[0], r.data_ptr(), int(ld),
                                                    psi_tilde.data_ptr(), sp), "mdet_psi_tilde_noalloc")

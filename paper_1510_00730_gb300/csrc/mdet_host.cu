@@ -469,6 +469,9 @@ const DevProblem* ctx_problem(const mdet_ctx* c, int* device) {
   if (device) *device = c->device;
   return &c->P;
 }
+void ctx_set_error(mdet_ctx* c, const char* msg) {
+  if (c) c->err = msg;
+}
 }  // namespace mdet
 
 extern "C" {

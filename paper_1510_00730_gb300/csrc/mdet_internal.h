@@ -153,6 +153,8 @@ cudaError_t launch_fallback(const DevProblem& P, const DevScratch& S, int64_t n_
                             uint32_t* status, cudaStream_t st);
 // Device index and uploaded problem of a context (null when it has none).
 const DevProblem* ctx_problem(const mdet_ctx* ctx, int* device);
+// Record the message that mdet_last_error returns for this context.
+void ctx_set_error(mdet_ctx* ctx, const char* msg);
 cudaError_t launch_selftest_df(int64_t n, const double* x, double* y_df, double* y_ref, double* prod_df,
                                cudaStream_t st);
 size_t final_smem_bytes(const DevProblem& P, bool mixed);

@@ -7,6 +7,7 @@
 // all of the GPU's memory, or a host runtime that forbids allocation after
 // start-up. Such a caller passes its own input and output buffers and gets the
 // work done in this library's static scratch.
+#include <cstdio>
 #include <mutex>
 
 #include "mdet_internal.h"
@@ -52,7 +53,15 @@ extern "C" mdet_status mdet_psi_tilde_noalloc(mdet_ctx* ctx, int64_t n_walk, con
   if (n_walk == 0) return MDET_OK;
   if (!r || !psi_tilde || ld < n_walk || ld % 128 != 0 || ((uintptr_t)r & 15) != 0) return MDET_E_ARG;
   const int64_t need = ((int64_t)P->n_det_sp[0] + 1) * ld;
-  if (need > (int64_t)MDET_NOALLOC_SCRATCH_DOUBLES) return MDET_E_ARG;  // beyond the static scratch
+  if (need > (int64_t)MDET_NOALLOC_SCRATCH_DOUBLES) {  // beyond the static scratch
+    char msg[200];
+    snprintf(msg, sizeof msg,
+             "(n_det_up + 1) * ld = %lld doubles exceeds the static scratch of %u doubles; use a smaller ld "
+             "(fewer walkers per call) or mdet_evaluate",
+             (long long)need, MDET_NOALLOC_SCRATCH_DOUBLES);
+    ctx_set_error(ctx, msg);
+    return MDET_E_ARG;
+  }
   if (cudaSetDevice(device) != cudaSuccess) return MDET_E_CUDA;
   double* scratch = nullptr;
   if (scratch_address(device, &scratch) != cudaSuccess) return MDET_E_CUDA;

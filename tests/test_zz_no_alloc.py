@@ -58,8 +58,8 @@ def test_noalloc_rejects_sizes_beyond_scratch():
     n_up = ctx.stats()["n_det_up"]
     ld = (pkg.Context.NOALLOC_SCRATCH_DOUBLES // (n_up + 1) // 128 + 1) * 128   # one tile too many
     dev = torch.device("cuda", 0)
-    r = torch.zeros(8, dtype=torch.float64, device=dev)
+    r = torch.zeros((n_up + ctx.stats()["n_det_dn"], ld), dtype=torch.float64, device=dev)
     psi_t = torch.zeros(ld, dtype=torch.float64, device=dev)
-    with pytest.raises(pkg.MdetError) as ei:
+    with pytest.raises(pkg.MdetError, match="static scratch") as ei:
         ctx.psi_tilde_noalloc(r, ld, psi_t)
     assert ei.value.status == 1   # MDET_E_ARG, rejected before any GPU work
