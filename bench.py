@@ -27,9 +27,10 @@ METRIC = "walker-steps/s (Ψ,∇Ψ,∇²Ψ), 17e⁻, N_det=750k: mixed vs FP64 a
 UNIT = "walker-steps/s"
 FP64_PEAK_TFLOPS = 1.25     # nominal dense FP64 rate of one GB300 (no measured FP64 peak is available)
 CPU_SAMPLE_WALKERS = 96     # bounded oracle sample for the CPU baseline (~10-30 s of CPU work)
-# dram__bytes_read.sum + dram__bytes_write.sum of one k_spmm_wm launch on the 750k workload with
-# 8,192 walkers (ncu capture summarised in profiles/mixed_chlorine_like_750k.md)
-SPMM_TRAFFIC_750K = 852.5e6
+# dram__bytes_read.sum + dram__bytes_write.sum of the average k_spmm_wm launch on the 750k workload
+# with 8,192 walkers, by the number of walker chunks (ncu captures summarised in
+# profiles/mixed_chlorine_like_750k.md); null for a chunking that was not captured
+SPMM_TRAFFIC_750K = {3: 227.6e6}
 
 
 def _env_int(k, d):
@@ -229,18 +230,31 @@ def run_ours(args):
 
     results = {}
     ctxs = {}
+
+    def timed(name, ctx, clock_index=None):
+        out = ctx.alloc_outputs(W)
+        step_ms, kern, clocks = _time_steps(ctx, Rdev, out, flush, stream, args.steps, args.warmup, dist,
+                                            clock_index)
+        n_fb = int(((out["status"] & pkg.WS_FALLBACK) != 0).sum().item())
+        ms = _max_over_ranks(statistics.mean(step_ms), dist, dev)
+        results[name] = dict(ms=ms, value=whole_job_value(W, world, ms), kern=kern, clocks=clocks, n_fb=n_fb,
+                             chunks=ctx.last_chunks, fallback_tol=ctx.fallback[0])
+
     for pname in [primary] + others:
         ctx = pkg.Context.from_workload(wl, device=local, precision=prec_of[pname])
         if args.chunks is not None:
             ctx.set_walker_chunks(args.chunks)
         ctxs[pname] = ctx
-        out = ctx.alloc_outputs(W)
-        step_ms, kern, clocks = _time_steps(ctx, Rdev, out, flush, stream, args.steps, args.warmup, dist,
-                                            _gpu_index(local) if pname == primary else None)
-        n_fb = int(((out["status"] & pkg.WS_FALLBACK) != 0).sum().item())
-        ms = _max_over_ranks(statistics.mean(step_ms), dist, dev)
-        results[pname] = dict(ms=ms, value=whole_job_value(W, world, ms), kern=kern, clocks=clocks, n_fb=n_fb)
-        del out
+        if pname == primary:
+            timed(pname, ctx, _gpu_index(local))
+            continue
+        # the other precision at the primary's accuracy target (the metric compares the two paths
+        # at the same relative error), then at its own default target
+        own_tol, own_cap = ctx.fallback
+        ctx.set_fallback(ctxs[primary].fallback[0], own_cap)
+        timed(pname, ctx)
+        ctx.set_fallback(own_tol, own_cap)
+        timed(pname + "_default_fallback", ctx)
     # the mixed path with its optional double-float contraction (outside the FP64 contraction of the
     # method's precision plan; reported beside the headline, never as it)
     df_contract = None
@@ -255,10 +269,11 @@ def run_ours(args):
         del out
     st = ctxs[primary].stats()
     main = results[primary]
+    main_chunks = main["chunks"]
     # kernels per evaluation: orbitals, reference, ratios, 2 contractions, final per walker chunk,
     # plus the 5 kernels of the stability fallback when it is enabled
     fb_tol, fb_cap = ctxs[primary].fallback
-    st_launches = 6 * max(1, ctxs[primary].tuning()["walker_chunks"]) + (5 if fb_tol > 0 else 0)
+    st_launches = 6 * main_chunks + (5 if fb_tol > 0 else 0)
 
     # end to end through the host-memory C-ABI call: H2D of R and D2H of all outputs per step
     ctx = ctxs[primary]
@@ -284,14 +299,15 @@ def run_ours(args):
     d2h = W * (8 + 1 + 3 * N * 8 + N * 8 + 8 + 4)
 
     # roofline of the dominant kernel: the FP64 sparse contraction k_spmm_wm, 2 launches per
-    # step (v = C r_dn, u = C^T r_up), each 2 FLOP per nonzero per walker
+    # step and walker chunk (v = C r_dn, u = C^T r_up), each 2 FLOP per nonzero per walker;
+    # the average launch covers W / chunks walkers
     kern = main["kern"]
-    flops_launch = 2.0 * st["n_det"] * W
-    launch_ms = kern["contract"] / 2
+    flops_launch = 2.0 * st["n_det"] * W / main_chunks
+    launch_ms = kern["contract"] / (2 * main_chunks)
     achieved = flops_launch / (launch_ms / 1e3) / 1e12
     traffic = args.traffic
     if traffic is None and args.workload == "chlorine_like_750k" and W == 8192:
-        traffic = SPMM_TRAFFIC_750K
+        traffic = SPMM_TRAFFIC_750K.get(main_chunks)
     roofline = {"kernel": "k_spmm_wm", "bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS,
                 "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS, "traffic": traffic,
                 "traffic_unit": "bytes per launch (ncu dram read + write)",
@@ -306,7 +322,7 @@ def run_ours(args):
                        "n_det": st["n_det"], "n_det_up": st["n_det_up"], "n_det_dn": st["n_det_dn"],
                        "n_elec": N, "n_ao": st["n_ao"], "n_mo": st["n_mo"],
                        "l2": "flushed between timed steps (512 MB write outside the events)",
-                       "parallelism": "dp%d (walkers)" % world},
+                       "walker_chunks": main_chunks, "parallelism": "dp%d (walkers)" % world},
             "clocks": main["clocks"],
             "e2e": {"value": whole_job_value(W, world, e2e_ms), "unit": UNIT, "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms},
@@ -316,9 +332,12 @@ def run_ours(args):
             "roofline": roofline}
     if df_contract is not None:
         line["mixed_df_contraction"] = df_contract
+    line["fallback_tol"] = main["fallback_tol"]
     for pname in others:
-        line[pname] = {"value": results[pname]["value"], "ms_per_step": results[pname]["ms"],
-                       "kernels_ms": results[pname]["kern"], "fallback_walkers": results[pname]["n_fb"]}
+        for name in (pname, pname + "_default_fallback"):
+            line[name] = {"value": results[name]["value"], "ms_per_step": results[name]["ms"],
+                          "kernels_ms": results[name]["kern"], "fallback_walkers": results[name]["n_fb"],
+                          "fallback_tol": results[name]["fallback_tol"]}
 
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         from tests.parity import walker_quantiles

@@ -218,18 +218,21 @@ mdet_status mdet_get_ratios(mdet_ctx* ctx, int64_t n_walk, double* r_up, double*
 
 /*
  * Stability control (the paper's O(N^3) fallback of Sec. 2.2, adapted to the
- * ratio table). The table result of a walker carries relative errors of about
- * u cond_1(S_ref) C, with u the unit roundoff of the table arithmetic (2^-53
- * FP64, about 2^-47 double-float), cond_1(S_ref) = |S_ref|_1 |S_ref^-1|_1 of
- * its reference Slater matrix, and C the cancellation ratio (sum of |terms| /
- * max(|result|, rms over the walker's electrons)) of its gradient and Laplacian
- * sums, with the terms added in quadrature (mdet_get_error_estimates). A walker
- * whose estimate exceeds tol (default 1e-5 for mixed, 1e-6 for FP64
- * precision), or whose reference is singular, is re-evaluated on the GPU
- * in FP64 by LU of every distinct determinant, its own contraction and
- * epilogue; its status gets MDET_WS_FALLBACK. At most max_walkers walkers per
- * evaluation are re-evaluated (default 64; the scratch grows with it);
- * further ones keep the table result and MDET_WS_REF_ILLCOND. tol <= 0
+ * ratio table). Every determinant ratio of the table carries a relative error
+ * of about u cond_1(S_ref), with u the unit roundoff of the table arithmetic
+ * (2^-53 FP64, about 2^-47 double-float) and cond_1(S_ref) = |S_ref|_1
+ * |S_ref^-1|_1 of the walker's reference Slater matrix. The estimate of the
+ * walker's relative error is u cond_1(S_ref) C kappa_Psi: C the cancellation
+ * ratio of its gradient and Laplacian sums (sum of |terms| / max(|result|, rms
+ * over the walker's electrons)), kappa_Psi = sum_ij |c_ij D_up,i D_dn,j| / |Psi|
+ * the conditioning of the CI sum (mdet_get_error_estimates: the l1 form and a
+ * form with the terms added in quadrature). A walker whose l1 estimate exceeds
+ * tol (default 1e-5 for mixed, 1e-8 for FP64 precision: the accuracy target of
+ * each path), or whose reference is singular, is re-evaluated on the GPU in FP64
+ * by LU of every distinct determinant, its own contraction and epilogue; its
+ * status gets MDET_WS_FALLBACK. At most max_walkers walkers per evaluation are
+ * re-evaluated (default 256 for mixed, 512 for FP64; the scratch grows with
+ * it); further ones keep the table result and MDET_WS_REF_ILLCOND. tol <= 0
  * disables the fallback. Supported for n_up, n_dn <= MDET_FALLBACK_MAX_SPIN.
  */
 #define MDET_FALLBACK_MAX_SPIN 17
@@ -263,25 +266,33 @@ mdet_status mdet_truncate_norm(int64_t n_det, int n_int, const uint64_t* det_up,
 mdet_status mdet_get_fallback(const mdet_ctx* ctx, double* tol, int* max_walkers);
 
 /*
- * Walker chunking of the mixed-precision evaluation/*
  * Walker chunking of the mixed-precision evaluation: a batch is cut into
- * n_chunks chunks (multiples of 256 walkers) evaluated on the context's own
- * streams, forked from and joined back to the caller's stream, so the FP32-pipe
- * stages of one chunk overlap the FP64 contraction of another (the FP64
- * contractions themselves run one after another). 0 selects the default (1,
- * no overlap), 1 disables the overlap. Values above 4 are clamped. The FP64 path always
- * runs as one chunk on the caller's stream.
+ * n_chunks chunks (multiples of 256 walkers) pipelined over two streams of the
+ * context, forked from and joined back to the caller's stream. One stream runs
+ * the FP32-pipe stages in order (orbitals, reference tables and ratios of each
+ * chunk; the epilogue of each chunk once it is contracted), the other, of
+ * higher priority, the FP64 contractions one after another on a persistent grid
+ * that leaves part of every SM free. So the contraction of chunk k overlaps the
+ * orbitals and tables of chunk k+1 and the epilogue of chunk k-1. 0 selects the
+ * automatic choice (3 chunks with the FP64 contraction, at least 100,000
+ * products and 3,072 walkers; otherwise 1), 1 disables the overlap. Values
+ * above 8 are clamped, and so are values above the number of 256-walker tiles.
+ * The FP64 path always runs as one chunk on the caller's stream.
  */
 mdet_status mdet_set_walker_chunks(mdet_ctx* ctx, int n_chunks);
+
+/* Walker chunks the last mdet_evaluate of this context was cut into (0 before
+ * the first evaluation). */
+mdet_status mdet_get_last_chunks(const mdet_ctx* ctx, int32_t* n_chunks);
 
 /*
  * Tile shapes of the evaluation kernels (tuning knobs with no counterpart in
  * the paper): spmm_chunk nonzeros of C per warp in the contraction (64..8192),
  * mo_ec electrons per thread block in the orbital kernels (4, 6 or 8),
- * walker_chunks as in mdet_set_walker_chunks, spmm_blocks the grid of the
- * contraction (0: one warp per work item; otherwise at most that many
- * 128-thread blocks looping over the work items, which leaves room on the SMs
- * for the kernels of another walker chunk), mo_impl the mixed-precision
+ * walker_chunks as in mdet_set_walker_chunks, spmm_blocks the grid of the FP64
+ * contraction (0: one warp per work item with one chunk, 4 blocks per SM with
+ * several; otherwise a persistent grid of at most that many 128-thread blocks
+ * whose warps draw work items from a counter), mo_impl the mixed-precision
  * orbital product (1, the default: the compensated FP32 dot product on the
  * CUDA cores, accurate relative to each term; 0: BF16 tensor cores on exact
  * digit products, accurate to about 2^-55 of the row and column maxima),
@@ -312,7 +323,7 @@ mdet_status mdet_set_tuning(mdet_ctx* ctx, const mdet_tuning* in);
  * pointer, [n_walk][n_up+n_dn][3]) with CUDA events on the context's stream and
  * picks the tile shapes by coordinate descent over spmm_chunk in
  * {256, 512, 1024, 2048}, mo_ec in {4, 6, 8} and (mixed precision)
- * walker_chunks in {1, 2, 4}, stopping when budget_ms of GPU time is spent.
+ * walker_chunks in {1, 2, 3, 4}, stopping when budget_ms of GPU time is spent.
  * The winner is stored in the context and returned in *out (may be null).
  * Allocates temporary output buffers; synchronous.
  */
@@ -349,14 +360,12 @@ mdet_status mdet_batch_launch(mdet_batch* b, void* stream);
 void mdet_batch_destroy(mdet_batch* b);
 
 /*
- * Stage timing./*
- * Stage timing./*
- * Stage timing. With profiling on, every mdet_evaluate records CUDA events on
- * its stream around each stage; mdet_get_profile waits for the last one and
- * writes the durations in milliseconds of the last evaluation, in the order
- * MDET_STAGE_* below (ms: [MDET_N_STAGES]), summed over walker chunks (with
- * chunks the stages of different chunks overlap, so the sum can exceed the
- * step time). Off by default.
+ * Stage timing. With profiling on, every mdet_evaluate records a CUDA event
+ * before and after each stage on the stream that runs it; mdet_get_profile
+ * waits for the last one and writes the durations in milliseconds of the last
+ * evaluation, in the order MDET_STAGE_* below (ms: [MDET_N_STAGES]), summed
+ * over walker chunks (with chunks the stages of different chunks overlap, so
+ * the sum can exceed the step time). Off by default.
  */
 enum {
   MDET_STAGE_ORBITALS = 0,  /* AO values and AO->MO product (Sec. 2) */
@@ -409,10 +418,11 @@ mdet_status mdet_selftest_df32(int device, int64_t n, const double* x, double* y
  * Diagnostics of the last evaluation (host copies, synchronises its stream):
  * cond1 [n_walk][2], cond_1 of the reference Slater matrix of each spin;
  * est [n_walk][2], the first-order error estimates of the walker's table
- * result: u cond_1 times the cancellation ratio of its derivative sums with
- * the terms summed in magnitude (est[w][0], a worst case) and in quadrature
- * (est[w][1], the one mdet_set_fallback compares with its tolerance). Either
- * pointer may be null. Meaningful when the fallback is enabled.
+ * result: u cond_1 times the cancellation ratio of its derivative sums times
+ * the conditioning of its CI sum, with the terms summed in magnitude
+ * (est[w][0], the one mdet_set_fallback compares with its tolerance) and in
+ * quadrature (est[w][1]). Either pointer may be null. Meaningful when the
+ * fallback is enabled.
  */
 mdet_status mdet_get_error_estimates(mdet_ctx* ctx, int64_t n_walk, double* cond1, double* est);
 

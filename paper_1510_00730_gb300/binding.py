@@ -83,6 +83,7 @@ def load_library(build_if_missing: bool = True):
     L.mdet_psi_tilde_noalloc.argtypes = [vp, i64, vp, i64, vp, vp]
     L.mdet_set_profiling.argtypes = [vp, i32]
     L.mdet_set_walker_chunks.argtypes = [vp, i32]
+    L.mdet_get_last_chunks.argtypes = [vp, vp]
     L.mdet_set_fallback.argtypes = [vp, C.c_double, i32]
     L.mdet_get_fallback.argtypes = [vp, vp, vp]
     L.mdet_get_error_estimates.argtypes = [vp, i64, vp, vp]
@@ -100,7 +101,7 @@ def load_library(build_if_missing: bool = True):
     for name in ("mdet_create", "mdet_set_system", "mdet_set_orbitals", "mdet_set_ci_expansion", "mdet_evaluate",
                  "mdet_evaluate_host", "mdet_get_ratios", "mdet_get_stats", "mdet_get_spin_dets",
                  "mdet_get_ci_matrix", "mdet_omega_sort", "mdet_truncate_norm", "mdet_sm_chain", "mdet_set_ci_expansion_device", "mdet_set_profiling", "mdet_get_profile",
-                 "mdet_psi_tilde_noalloc", "mdet_set_walker_chunks", "mdet_selftest_df32", "mdet_get_tuning",
+                 "mdet_psi_tilde_noalloc", "mdet_set_walker_chunks", "mdet_get_last_chunks", "mdet_selftest_df32", "mdet_get_tuning",
                  "mdet_set_tuning", "mdet_autotune", "mdet_batch_evaluate", "mdet_batch_create", "mdet_batch_launch", "mdet_set_fallback", "mdet_get_fallback",
                  "mdet_get_error_estimates"):
         getattr(L, name).restype = i32
@@ -430,8 +431,15 @@ class Context:
         return c1, est
 
     def set_walker_chunks(self, n_chunks):
-        """Mixed precision: evaluate a batch in n_chunks overlapping chunks (0 = default, 1 = none)."""
+        """Mixed precision: pipeline a batch in n_chunks walker chunks (0 = automatic, 1 = none)."""
         self._check(self._L.mdet_set_walker_chunks(self._h, int(n_chunks)), "mdet_set_walker_chunks")
+
+    @property
+    def last_chunks(self):
+        """Walker chunks of the last evaluation (mdet_get_last_chunks; 0 before the first)."""
+        n = C.c_int32(0)
+        self._check(self._L.mdet_get_last_chunks(self._h, C.byref(n)), "mdet_get_last_chunks")
+        return int(n.value)
 
     def set_profiling(self, enable=True):
         self._check(self._L.mdet_set_profiling(self._h, int(bool(enable))), "mdet_set_profiling")

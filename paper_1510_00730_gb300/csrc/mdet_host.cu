@@ -43,12 +43,14 @@ struct mdet_ctx {
   cudaStream_t own_stream = nullptr;
   cudaStream_t last_stream = nullptr;
   int64_t last_walk = 0;
-  // walker chunks evaluated on their own streams (mixed precision): the FP32-pipe
-  // stages of one chunk overlap the FP64 contraction of another
-  static constexpr int kMaxChunks = 4;
+  // walker chunks (mixed precision), software-pipelined over two streams: the
+  // FP32-pipe stages of the chunks run in order on fstream, the FP64 contractions on
+  // the higher-priority stream cstream, so one chunk's contraction overlaps the
+  // orbitals, tables and ratios of the next chunk and the epilogue of the previous one
+  static constexpr int kMaxChunks = 8;
   int n_chunks_cfg = 0;  // 0: automatic
   double fallback_tol = 0.0;  // set from the precision in mdet_create
-  int fallback_cap = 64;
+  int fallback_cap = 256;  // set from the precision in mdet_create
   std::vector<int32_t> csr_ptr, csc_ptr;
   int spmm_chunk = 512;  // tile shapes (mdet_set_tuning / mdet_autotune)
   int spmm_blocks = 0;
@@ -56,13 +58,17 @@ struct mdet_ctx {
   int mo_ec = 4;
   int contract_impl = 0;  // FP64 contraction (the double-float one is an option of the mixed path)
   mdet_tuning last_tune{};
-  cudaStream_t cs[kMaxChunks] = {};
-  cudaEvent_t fork = nullptr, joined[kMaxChunks] = {}, contracted[kMaxChunks] = {};
+  cudaStream_t fstream = nullptr, cstream = nullptr;
+  int n_sm = 0;
+  cudaEvent_t fork = nullptr, joined = nullptr, contracted[kMaxChunks] = {}, prepared[kMaxChunks] = {};
   // stage timing
   bool profiling = false;
   bool have_profile = false;
   int prof_chunks = 0;
-  cudaEvent_t ev[kMaxChunks][MDET_N_STAGES + 1] = {};
+  // per chunk: the start and end of every stage (stages of one chunk may run on
+  // different streams, after waits)
+  static constexpr int kEvPerChunk = 2 * MDET_N_STAGES;
+  cudaEvent_t ev[kMaxChunks][kEvPerChunk] = {};
 };
 
 namespace {
@@ -200,8 +206,8 @@ void free_problem(mdet_ctx* c) {
 
 void free_scratch(mdet_ctx* c) {
   DevScratch& S = c->S;
-  void* ptrs[] = {S.phi, S.Ainv, S.ld0, S.sg0, S.g, S.kap, S.est, S.T, S.Tdf, S.r, S.rdf, S.vu, S.psit, S.wstat,
-                  S.fb, S.fb_list, S.fb_acc, S.R_stage, S.out_stage};
+  void* ptrs[] = {S.phi, S.Ainv, S.ld0, S.sg0, S.g, S.kap, S.est, S.T, S.Tdf, S.r, S.rdf, S.vu, S.psit, S.psia, S.wstat,
+                  S.fb, S.fb_list, S.fb_acc, S.queue, S.R_stage, S.out_stage};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   S = DevScratch{};
@@ -447,7 +453,9 @@ mdet_status ensure_scratch(mdet_ctx* c, int64_t n_walk) {
   }
   if ((s = dalloc(c, &S.vu, (size_t)ndt * wp))) return s;  // walker-major [wp][ndt]
   if ((s = dalloc(c, &S.psit, (size_t)wp))) return s;
+  if ((s = dalloc(c, &S.psia, (size_t)wp))) return s;
   if ((s = dalloc(c, &S.wstat, (size_t)W))) return s;
+  if ((s = dalloc(c, &S.queue, (size_t)2 * mdet_ctx::kMaxChunks))) return s;
   if (P.fallback_tol > 0.0 && P.n_up <= MDET_FALLBACK_MAX_SPIN) {
     const int64_t nmax = std::max(P.n_up, P.n_dn);
     if ((s = dalloc(c, &S.fb, (size_t)P.fallback_cap * ndt * (3 + 4 * nmax)))) return s;
@@ -459,6 +467,15 @@ mdet_status ensure_scratch(mdet_ctx* c, int64_t n_walk) {
   S.cap_walk = W;
   S.wp = wp;
   return MDET_OK;
+}
+
+// Walker chunks of a mixed-precision evaluation when none are configured: three
+// when the FP64 contraction is long enough to hide the FP32-pipe stages of the
+// other chunks (at least 100,000 products and 4 walker tiles per chunk), else one.
+int auto_chunks(const mdet_ctx* c, int64_t n_walk) {
+  const int64_t tiles = (n_walk + kWalkerPad - 1) / kWalkerPad;
+  return (c->precision == MDET_PRECISION_MIXED && c->contract_impl == 0 && c->P.nnz >= 100000 && tiles >= 12) ? 3
+                                                                                                                : 1;
 }
 
 }  // namespace
@@ -501,7 +518,9 @@ mdet_status mdet_create(mdet_ctx** out, int device, int precision) {
   if (!c) return MDET_E_OOM;
   c->device = device;
   c->precision = precision;
-  c->fallback_tol = precision == MDET_PRECISION_MIXED ? 1e-5 : 1e-6;
+  // the accuracy targets of the two paths: 1e-5 (mixed) and 1e-8 (FP64) relative
+  c->fallback_tol = precision == MDET_PRECISION_MIXED ? 1e-5 : 1e-8;
+  c->fallback_cap = precision == MDET_PRECISION_MIXED ? 256 : 512;
   c->mo_ec = precision == MDET_PRECISION_MIXED ? 4 : 6;  // measured best electron block of each orbital kernel
   if (device >= 0) {
     int n = 0;
@@ -512,10 +531,15 @@ mdet_status mdet_create(mdet_ctx** out, int device, int precision) {
     bool ok = cudaSetDevice(device) == cudaSuccess &&
               cudaStreamCreateWithFlags(&c->own_stream, cudaStreamNonBlocking) == cudaSuccess &&
               cudaEventCreateWithFlags(&c->fork, cudaEventDisableTiming) == cudaSuccess;
+    int lo = 0, hi = 0;
+    ok = ok && cudaDeviceGetStreamPriorityRange(&lo, &hi) == cudaSuccess &&
+         cudaStreamCreateWithPriority(&c->cstream, cudaStreamNonBlocking, hi) == cudaSuccess &&
+         cudaStreamCreateWithFlags(&c->fstream, cudaStreamNonBlocking) == cudaSuccess &&
+         cudaEventCreateWithFlags(&c->joined, cudaEventDisableTiming) == cudaSuccess &&
+         cudaDeviceGetAttribute(&c->n_sm, cudaDevAttrMultiProcessorCount, device) == cudaSuccess;
     for (int i = 0; ok && i < mdet_ctx::kMaxChunks; i++)
-      ok = cudaStreamCreateWithFlags(&c->cs[i], cudaStreamNonBlocking) == cudaSuccess &&
-           cudaEventCreateWithFlags(&c->joined[i], cudaEventDisableTiming) == cudaSuccess &&
-           cudaEventCreateWithFlags(&c->contracted[i], cudaEventDisableTiming) == cudaSuccess;
+      ok = cudaEventCreateWithFlags(&c->contracted[i], cudaEventDisableTiming) == cudaSuccess &&
+           cudaEventCreateWithFlags(&c->prepared[i], cudaEventDisableTiming) == cudaSuccess;
     if (!ok) {
       delete c;
       return MDET_E_CUDA;
@@ -533,12 +557,14 @@ void mdet_destroy(mdet_ctx* c) {
     free_scratch(c);
     free_problem(c);
     for (int k = 0; k < mdet_ctx::kMaxChunks; k++) {
-      for (int i = 0; i <= MDET_N_STAGES; i++)
+      for (int i = 0; i < mdet_ctx::kEvPerChunk; i++)
         if (c->ev[k][i]) cudaEventDestroy(c->ev[k][i]);
-      if (c->cs[k]) cudaStreamDestroy(c->cs[k]);
-      if (c->joined[k]) cudaEventDestroy(c->joined[k]);
       if (c->contracted[k]) cudaEventDestroy(c->contracted[k]);
+      if (c->prepared[k]) cudaEventDestroy(c->prepared[k]);
     }
+    if (c->cstream) cudaStreamDestroy(c->cstream);
+    if (c->fstream) cudaStreamDestroy(c->fstream);
+    if (c->joined) cudaEventDestroy(c->joined);
     if (c->fork) cudaEventDestroy(c->fork);
     if (c->own_stream) cudaStreamDestroy(c->own_stream);
   }
@@ -864,52 +890,82 @@ mdet_status mdet_evaluate(mdet_ctx* c, int64_t n_walk, const double* R, double* 
   const DevProblem& P = c->P;
   const bool mixed = c->precision == MDET_PRECISION_MIXED;
   const bool prof = c->profiling;
-  // chunking: mixed precision splits large batches so chunks overlap on separate streams
+  // chunking: mixed precision splits large batches into a two-stream pipeline
   int nch = 1;
+  const int64_t tiles = (n_walk + kWalkerPad - 1) / kWalkerPad;
   if (mixed) {
-    const int64_t tiles = (n_walk + kWalkerPad - 1) / kWalkerPad;
-    nch = c->n_chunks_cfg > 0 ? c->n_chunks_cfg : 1;
+    nch = c->n_chunks_cfg > 0 ? c->n_chunks_cfg : auto_chunks(c, n_walk);
     nch = (int)std::min<int64_t>(std::min<int64_t>(nch, tiles), mdet_ctx::kMaxChunks);
   }
-  const int64_t tiles = (n_walk + kWalkerPad - 1) / kWalkerPad;
   if (prof)
     for (int k = 0; k < nch; k++)
-      for (int i = 0; i <= MDET_N_STAGES; i++)
+      for (int i = 0; i < mdet_ctx::kEvPerChunk; i++)
         if (!c->ev[k][i]) CUDA_TRY(c, cudaEventCreate(&c->ev[k][i]));
-  if (nch > 1) CUDA_TRY(c, cudaEventRecord(c->fork, st));
   const int64_t N = P.n_elec;
-  for (int k = 0; k < nch; k++) {
+  auto chunk_range = [&](int k, int64_t* off, int64_t* n) {
     const int64_t t0 = tiles * k / nch, t1 = tiles * (k + 1) / nch;
-    const int64_t off = t0 * kWalkerPad;
-    const int64_t n = std::min<int64_t>(t1 * kWalkerPad, n_walk) - off;
-    cudaStream_t ks = nch > 1 ? c->cs[k] : st;
-    if (nch > 1) CUDA_TRY(c, cudaStreamWaitEvent(ks, c->fork, 0));
+    *off = t0 * kWalkerPad;
+    *n = std::min<int64_t>(t1 * kWalkerPad, n_walk) - *off;
+  };
+  // stage i (MDET_STAGE_*) of chunk k on stream ks, bracketed by its two profiling events
+  auto stage = [&](int k, int i, cudaStream_t ks, int persistent) -> mdet_status {
+    int64_t off, n;
+    chunk_range(k, &off, &n);
     const DevScratch S = scratch_view(c->S, P, off);
-#define STAGE_EVENT(i) \
-  if (prof) CUDA_TRY(c, cudaEventRecord(c->ev[k][i], ks))
     const double* Rk = R + off * N * 3;
-    STAGE_EVENT(0);
-    CUDA_TRY(c, mixed ? launch_mo_mixed(P, S, n, Rk, ks) : launch_mo_f64(P, S, n, Rk, ks));
-    STAGE_EVENT(1);
-    CUDA_TRY(c, launch_ref_tables(P, S, n, mixed, ks));
-    STAGE_EVENT(2);
-    CUDA_TRY(c, mixed ? launch_ratios_mixed(P, S, n, ks) : launch_ratios_f64(P, S, n, ks));
-    STAGE_EVENT(3);
-    CUDA_TRY(c, launch_zero_f64(P, S, n, ks));
-    // the FP64 contractions of successive chunks run one after another
-    if (nch > 1 && k > 0) CUDA_TRY(c, cudaStreamWaitEvent(ks, c->contracted[k - 1], 0));
-    STAGE_EVENT(4);
-    CUDA_TRY(c, launch_contract_f64(P, S, n, ks));
-    STAGE_EVENT(5);
-    if (nch > 1) CUDA_TRY(c, cudaEventRecord(c->contracted[k], ks));
-    CUDA_TRY(c, launch_final(P, S, n, Rk, log_abs_psi + off, sign + off, grad + off * N * 3, lap + off * N,
-                             e_local ? e_local + off : nullptr, status ? status + off : nullptr, mixed, ks));
-    STAGE_EVENT(6);
-#undef STAGE_EVENT
-    if (nch > 1) {
-      CUDA_TRY(c, cudaEventRecord(c->joined[k], ks));
-      CUDA_TRY(c, cudaStreamWaitEvent(st, c->joined[k], 0));
+    if (prof) CUDA_TRY(c, cudaEventRecord(c->ev[k][2 * i], ks));
+    switch (i) {
+      case MDET_STAGE_ORBITALS:
+        CUDA_TRY(c, mixed ? launch_mo_mixed(P, S, n, Rk, ks) : launch_mo_f64(P, S, n, Rk, ks));
+        break;
+      case MDET_STAGE_REFERENCE: CUDA_TRY(c, launch_ref_tables(P, S, n, mixed, ks)); break;
+      case MDET_STAGE_RATIOS:
+        CUDA_TRY(c, mixed ? launch_ratios_mixed(P, S, n, ks) : launch_ratios_f64(P, S, n, ks));
+        break;
+      case MDET_STAGE_ZERO: CUDA_TRY(c, launch_zero_f64(P, S, n, ks)); break;
+      case MDET_STAGE_CONTRACT: CUDA_TRY(c, launch_contract_f64(P, S, n, ks, c->S.queue + 2 * k, persistent)); break;
+      default:
+        CUDA_TRY(c, launch_final(P, S, n, Rk, log_abs_psi + off, sign + off, grad + off * N * 3, lap + off * N,
+                                 e_local ? e_local + off : nullptr, status ? status + off : nullptr, mixed, ks));
     }
+    if (prof) CUDA_TRY(c, cudaEventRecord(c->ev[k][2 * i + 1], ks));
+    return MDET_OK;
+  };
+  mdet_status ms;
+  if (nch == 1) {
+    for (int i = 0; i < MDET_N_STAGES; i++)
+      if ((ms = stage(0, i, st, 0)) != MDET_OK) return ms;
+  } else {
+    // fs (FP32-pipe stages, in this order): orbitals, reference and ratios of chunk 0,
+    // those of chunk 1, the epilogue of chunk 0 (after its contraction), chunk 2, the
+    // epilogue of chunk 1, ... ; xs (higher priority): the contraction of each chunk once
+    // its ratios are ready. The contraction runs on a persistent grid of 4 blocks per SM
+    // (unless spmm_blocks says otherwise) that leaves the rest of every SM to fs.
+    cudaStream_t fs = c->fstream, xs = c->cstream;
+    const int persistent = 4 * std::max(c->n_sm, 1);
+    CUDA_TRY(c, cudaEventRecord(c->fork, st));
+    CUDA_TRY(c, cudaStreamWaitEvent(fs, c->fork, 0));
+    CUDA_TRY(c, cudaStreamWaitEvent(xs, c->fork, 0));
+    auto enqueue = [&](int k) -> mdet_status {
+      mdet_status m;
+      for (int i = MDET_STAGE_ORBITALS; i < MDET_STAGE_ZERO; i++)
+        if ((m = stage(k, i, fs, 0)) != MDET_OK) return m;
+      CUDA_TRY(c, cudaEventRecord(c->prepared[k], fs));
+      CUDA_TRY(c, cudaStreamWaitEvent(xs, c->prepared[k], 0));
+      for (int i = MDET_STAGE_ZERO; i <= MDET_STAGE_CONTRACT; i++)
+        if ((m = stage(k, i, xs, persistent)) != MDET_OK) return m;
+      CUDA_TRY(c, cudaEventRecord(c->contracted[k], xs));
+      return MDET_OK;
+    };
+    if ((ms = enqueue(0)) != MDET_OK) return ms;
+    for (int k = 0; k < nch; k++) {
+      if (k + 1 < nch && (ms = enqueue(k + 1)) != MDET_OK) return ms;
+      CUDA_TRY(c, cudaStreamWaitEvent(fs, c->contracted[k], 0));
+      if ((ms = stage(k, MDET_STAGE_FINAL, fs, 0)) != MDET_OK) return ms;
+    }
+    // every contraction precedes contracted[nch - 1], which fs has waited for
+    CUDA_TRY(c, cudaEventRecord(c->joined, fs));
+    CUDA_TRY(c, cudaStreamWaitEvent(st, c->joined, 0));
   }
   c->prof_chunks = nch;
   // stability fallback over the whole batch, after every chunk has finished
@@ -1014,6 +1070,12 @@ mdet_status mdet_set_walker_chunks(mdet_ctx* c, int n_chunks) {
   return MDET_OK;
 }
 
+mdet_status mdet_get_last_chunks(const mdet_ctx* c, int32_t* n_chunks) {
+  if (!c || !n_chunks) return MDET_E_ARG;
+  *n_chunks = c->last_walk > 0 ? c->prof_chunks : 0;
+  return MDET_OK;
+}
+
 mdet_status mdet_set_profiling(mdet_ctx* c, int enable) {
   if (!c) return MDET_E_ARG;
   if (c->device < 0) return fail(c, MDET_E_NODEVICE, "context has no device");
@@ -1029,10 +1091,10 @@ mdet_status mdet_get_profile(mdet_ctx* c, float* ms) {
   CUDA_TRY(c, cudaSetDevice(c->device));
   for (int i = 0; i < MDET_N_STAGES; i++) ms[i] = 0.0f;
   for (int k = 0; k < c->prof_chunks; k++) {
-    CUDA_TRY(c, cudaEventSynchronize(c->ev[k][MDET_N_STAGES]));
+    CUDA_TRY(c, cudaEventSynchronize(c->ev[k][2 * MDET_STAGE_FINAL + 1]));
     for (int i = 0; i < MDET_N_STAGES; i++) {
       float t = 0.0f;
-      CUDA_TRY(c, cudaEventElapsedTime(&t, c->ev[k][i], c->ev[k][i + 1]));
+      CUDA_TRY(c, cudaEventElapsedTime(&t, c->ev[k][2 * i], c->ev[k][2 * i + 1]));
       ms[i] += t;
     }
   }
@@ -1125,14 +1187,14 @@ mdet_status mdet_autotune(mdet_ctx* c, int64_t n_walk, const double* R, double b
   };
   mdet_tuning cur{};
   mdet_get_tuning(c, &cur);
-  if (cur.walker_chunks == 0) cur.walker_chunks = 1;
+  if (cur.walker_chunks == 0) cur.walker_chunks = auto_chunks(c, n_walk);
   float best = 0.0f;
   s = timed(cur, &best);
   const bool mixed = c->precision == MDET_PRECISION_MIXED;
-  const int chunks[] = {256, 512, 1024, 2048}, ecs[] = {4, 6, 8}, wcs[] = {1, 2, 4};
+  const int chunks[] = {256, 512, 1024, 2048}, ecs[] = {4, 6, 8}, wcs[] = {1, 2, 3, 4};
   for (int param = 0; param < 3 && s == MDET_OK; param++) {
     const int* vals = param == 0 ? chunks : (param == 1 ? ecs : wcs);
-    const int nv = param == 0 ? 4 : 3;
+    const int nv = param == 1 ? 3 : 4;
     if (param == 2 && !mixed) break;
     for (int q = 0; q < nv && s == MDET_OK && spent < budget_ms; q++) {
       mdet_tuning t = cur;

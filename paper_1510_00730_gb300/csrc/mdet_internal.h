@@ -119,10 +119,12 @@ struct DevScratch {
   float2* rdf = nullptr;  // same as double-float pairs (mixed path with the double-float contraction only)
   double* vu = nullptr;   // walker-major [wp][n_det_up + n_det_dn]: v = C r_dn (up) then u = C^T r_up (down)
   double* psit = nullptr; // [wp] Psi / (D_ref_up D_ref_dn)
+  float* psia = nullptr;  // [wp] sum_ij |c_ij| |r_up,i| |r_dn,j| (FP32), the magnitude sum behind psit
   uint32_t* wstat = nullptr;  // [W] status bits
   double* fb = nullptr;       // fallback: [cap][n_det_up + n_det_dn][2 + 4 max(n_up, n_dn)], then [cap][ndt] values
   int* fb_list = nullptr;     // fallback: [1 + cap] count, then walker indices
   double* fb_acc = nullptr;   // fallback: [cap][3 + 8 MDET_FALLBACK_MAX_SPIN] scales, Psi, G
+  unsigned long long* queue = nullptr;  // [2 * walker chunks] work counters of persistent contractions
   double* R_stage = nullptr;  // host-API staging buffers
   double* out_stage = nullptr;
 };
@@ -139,8 +141,11 @@ cudaError_t launch_ratios_f64(const DevProblem& P, const DevScratch& S, int64_t 
 cudaError_t launch_ratios_mixed(const DevProblem& P, const DevScratch& S, int64_t n_walk,
                                 cudaStream_t st);
 cudaError_t launch_zero_f64(const DevProblem& P, const DevScratch& S, int64_t n_walk, cudaStream_t st);
+// queue: two zeroed-per-launch work counters for a persistent contraction grid of
+// spmm_blocks blocks, or of persistent_blocks when spmm_blocks is 0 (null or 0:
+// one warp per work item).
 cudaError_t launch_contract_f64(const DevProblem& P, const DevScratch& S, int64_t n_walk,
-                                cudaStream_t st);
+                                cudaStream_t st, unsigned long long* queue = nullptr, int persistent_blocks = 0);
 // A view of the scratch for walkers [off, off + n): walker-major arrays move by
 // whole walkers, walker-minor arrays by columns (off must be a multiple of kWalkerPad).
 DevScratch scratch_view(const DevScratch& S, const DevProblem& P, int64_t off);

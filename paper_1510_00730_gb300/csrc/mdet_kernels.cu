@@ -306,29 +306,56 @@ __global__ void __launch_bounds__(256) k_spmm_f64(const int* __restrict__ seg, c
   flush(cur);
 }
 
+// |x| as an FP32 value, taken from the high word of the FP64 number (its
+// exponent and 20 leading mantissa bits, so within 2^-20 relative), clamped to
+// [0, FLT_MAX]: integer operations only, no FP64-to-FP32 conversion, for the
+// magnitude sums of the error estimate.
+__device__ __forceinline__ float abs_f32_of(double x) {
+  int t = (__double2hiint(x) & 0x7fffffff) - (896 << 20);  // rebias the exponent from 1023 to 127
+  t = min(max(t, 0), 0x0fefffff);
+  return __int_as_float(t << 3);
+}
+
 // ---------------------------------------------------------------------------
 // K5 (form used by mdet_evaluate): the same segmented product with 8 walkers
 // per lane (256 per warp). Work items are (chunk of nonzeros, group of 256
 // walkers), chunks fastest so that warps in flight share the same walker
-// columns of x in L2; the loop also serves a persistent launch with fewer
-// blocks. Output y is walker-major: y[w * ldy + seg_off + seg], the layout the
-// epilogue reads.
+// columns of x in L2. Output y is walker-major: y[w * ldy + seg_off + seg], the
+// layout the epilogue reads.
+// QUEUE false: one item per warp of a full grid. QUEUE true: a persistent grid
+// whose warps take the next item from the counter *queue (zeroed before the
+// launch), so blocks that become resident late, while kernels of other streams
+// hold part of the SMs, simply take fewer items.
+// ABS (with rdot): psia[w] += |rdot[seg][w]| * sum |c| |x| in FP32, so that
+// psia = sum_ij |c_ij| |r_up,i| |r_dn,j|, the magnitude sum behind Psi~ (its
+// ratio to |Psi~| is the conditioning of the CI sum, used by the error estimate).
+template <bool QUEUE, bool ABS>
 __global__ void __launch_bounds__(128) k_spmm_wm(const int* __restrict__ seg, const int* __restrict__ gidx,
                                                  const double* __restrict__ val, int64_t nnz, int chunk,
                                                  int64_t n_chunks, int64_t n_groups,
                                                  const double* __restrict__ x, int64_t wp,
                                                  double* __restrict__ y, int64_t ldy, int seg_off,
-                                                 const double* __restrict__ rdot, double* __restrict__ psit) {
+                                                 const double* __restrict__ rdot, double* __restrict__ psit,
+                                                 float* __restrict__ psia, unsigned long long* __restrict__ queue) {
   const int lane = threadIdx.x & 31;
-  const int64_t nwarps = (int64_t)gridDim.x * (blockDim.x >> 5);
-  for (int64_t item = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); item < n_chunks * n_groups;
-       item += nwarps) {
+  const int64_t n_items = n_chunks * n_groups;
+  auto next_item = [&]() -> int64_t {
+    unsigned long long t = 0;
+    if (lane == 0) t = atomicAdd(queue, 1ULL);
+    return (int64_t)__shfl_sync(0xffffffffu, t, 0);
+  };
+  const int64_t first = QUEUE ? next_item() : (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  for (int64_t item = first; item < n_items; item = QUEUE ? next_item() : n_items) {
     const int64_t ch = item % n_chunks, grp = item / n_chunks;
     const int64_t k0 = ch * chunk, k1 = min(k0 + (int64_t)chunk, nnz);
     const int64_t wb = grp * 256 + lane * 8;
     double a[8];
+    float aa[8];  // ABS: sum |c| |x| of the segment
 #pragma unroll
-    for (int j = 0; j < 8; j++) a[j] = 0.0;
+    for (int j = 0; j < 8; j++) {
+      a[j] = 0.0;
+      aa[j] = 0.0f;
+    }
     int cur = __ldg(seg + k0);
     auto flush = [&](int sg) {
 #pragma unroll
@@ -336,7 +363,10 @@ __global__ void __launch_bounds__(128) k_spmm_wm(const int* __restrict__ seg, co
       if (rdot) {
         const double* rp = rdot + (size_t)sg * wp + wb;
 #pragma unroll
-        for (int j = 0; j < 8; j++) atomicAdd(psit + wb + j, rp[j] * a[j]);
+        for (int j = 0; j < 8; j++) {
+          atomicAdd(psit + wb + j, rp[j] * a[j]);
+          if (ABS) atomicAdd(psia + wb + j, abs_f32_of(rp[j]) * aa[j]);
+        }
       }
     };
     for (int64_t k = k0; k < k1; k++) {
@@ -345,7 +375,10 @@ __global__ void __launch_bounds__(128) k_spmm_wm(const int* __restrict__ seg, co
         flush(cur);
         cur = sg;
 #pragma unroll
-        for (int j = 0; j < 8; j++) a[j] = 0.0;
+        for (int j = 0; j < 8; j++) {
+          a[j] = 0.0;
+          aa[j] = 0.0f;
+        }
       }
       const double c = __ldg(val + k);
       const double2* xp = reinterpret_cast<const double2*>(x + (size_t)__ldg(gidx + k) * wp + wb);
@@ -358,6 +391,17 @@ __global__ void __launch_bounds__(128) k_spmm_wm(const int* __restrict__ seg, co
       a[5] = fma(c, x2.y, a[5]);
       a[6] = fma(c, x3.x, a[6]);
       a[7] = fma(c, x3.y, a[7]);
+      if (ABS) {
+        const float ca = abs_f32_of(c);
+        aa[0] = fmaf(ca, abs_f32_of(x0.x), aa[0]);
+        aa[1] = fmaf(ca, abs_f32_of(x0.y), aa[1]);
+        aa[2] = fmaf(ca, abs_f32_of(x1.x), aa[2]);
+        aa[3] = fmaf(ca, abs_f32_of(x1.y), aa[3]);
+        aa[4] = fmaf(ca, abs_f32_of(x2.x), aa[4]);
+        aa[5] = fmaf(ca, abs_f32_of(x2.y), aa[5]);
+        aa[6] = fmaf(ca, abs_f32_of(x3.x), aa[6]);
+        aa[7] = fmaf(ca, abs_f32_of(x3.y), aa[7]);
+      }
     }
     flush(cur);
   }
@@ -375,7 +419,8 @@ __global__ void __launch_bounds__(128) k_spmm_df(const int* __restrict__ seg, co
                                                  int64_t n_chunks, int64_t n_groups,
                                                  const float2* __restrict__ x, int64_t wp,
                                                  double* __restrict__ y, int64_t ldy, int seg_off,
-                                                 const double* __restrict__ rdot, double* __restrict__ psit) {
+                                                 const double* __restrict__ rdot, double* __restrict__ psit,
+                                                 float* __restrict__ psia) {
   const int lane = threadIdx.x & 31;
   const int64_t nwarps = (int64_t)gridDim.x * (blockDim.x >> 5);
   for (int64_t item = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); item < n_chunks * n_groups;
@@ -383,9 +428,9 @@ __global__ void __launch_bounds__(128) k_spmm_df(const int* __restrict__ seg, co
     const int64_t ch = item % n_chunks, grp = item / n_chunks;
     const int64_t k0 = ch * chunk, k1 = min(k0 + (int64_t)chunk, nnz);
     const int64_t wb = grp * 256 + lane * 8;
-    float s[8], e[8];
+    float s[8], e[8], aa[8];
 #pragma unroll
-    for (int j = 0; j < 8; j++) s[j] = e[j] = 0.0f;
+    for (int j = 0; j < 8; j++) s[j] = e[j] = aa[j] = 0.0f;
     int cur = __ldg(seg + k0);
     auto flush = [&](int sg) {
       const double* rp = rdot ? rdot + (size_t)sg * wp + wb : nullptr;
@@ -393,7 +438,10 @@ __global__ void __launch_bounds__(128) k_spmm_df(const int* __restrict__ seg, co
       for (int j = 0; j < 8; j++) {
         const double v = (double)s[j] + (double)e[j];
         atomicAdd(y + (wb + j) * ldy + seg_off + sg, v);
-        if (rp) atomicAdd(psit + wb + j, rp[j] * v);
+        if (rp) {
+          atomicAdd(psit + wb + j, rp[j] * v);
+          atomicAdd(psia + wb + j, abs_f32_of(rp[j]) * aa[j]);
+        }
       }
     };
     for (int64_t k = k0; k < k1; k++) {
@@ -402,7 +450,7 @@ __global__ void __launch_bounds__(128) k_spmm_df(const int* __restrict__ seg, co
         flush(cur);
         cur = sg;
 #pragma unroll
-        for (int j = 0; j < 8; j++) s[j] = e[j] = 0.0f;
+        for (int j = 0; j < 8; j++) s[j] = e[j] = aa[j] = 0.0f;
       }
       const float2 c = __ldg(val + k);
       const float4* xp = reinterpret_cast<const float4*>(x + (size_t)__ldg(gidx + k) * wp + wb);
@@ -425,6 +473,7 @@ __global__ void __launch_bounds__(128) k_spmm_df(const int* __restrict__ seg, co
         two_sum(s[j], p, t, err);
         s[j] = t;
         e[j] = __fadd_rn(e[j], __fadd_rn(err, __fadd_rn(pe, cross)));
+        if (rdot) aa[j] = fmaf(fabsf(c.x), fabsf(xh), aa[j]);
       }
     }
     flush(cur);
@@ -638,11 +687,14 @@ __global__ void __launch_bounds__(128) k_final(DevProblem P, DevScratch S, const
     finite &= isfinite(gx) && isfinite(gy) && isfinite(gz) && isfinite(lp);
   }
   const int all_finite = __syncthreads_and(finite);
-  // first-order error estimate of the table result: the terms of each
-  // derivative sum carry relative errors ~ u cond_1(S_ref), so the error of G
-  // relative to max(|G|, rms over the walker's electrons) is about
-  // u cond_1 (sum of |terms|) / max(|G|, rms), or with the terms added in
-  // quadrature for independent rounding errors
+  // first-order error estimate of the table result: every determinant ratio
+  // carries a relative error ~ u cond_1(S_ref); the derivative sums add terms
+  // of the aggregated matrices with cancellation ratio (sum of |terms|) /
+  // max(|G|, rms over the walker's electrons), and the aggregation over the
+  // expansion cancels like the CI sum itself, kappa_Psi = (sum_ij |c_ij r_i r_j|)
+  // / |Psi~|. The estimate is u cond_1 (sum of |terms|) / max(|G|, rms) kappa_Psi
+  // (l1 form; the l2 form adds the terms in quadrature). The l1 form decides the
+  // fallback.
   const bool fb_on = P.fallback_tol > 0.0 && P.n_up <= MDET_FALLBACK_MAX_SPIN;
   if (fb_on) {
     if (threadIdx.x < 4) {
@@ -689,9 +741,11 @@ __global__ void __launch_bounds__(128) k_final(DevProblem P, DevScratch S, const
     if (e_local) e_local[w] = el;
     uint32_t st = S.wstat[w];
     if (fb_on) {
-      S.est[w * 2] = estw[0][0];
-      S.est[w * 2 + 1] = estw[1][0];
-      if (!(estw[1][0] <= (float)P.fallback_tol)) st |= MDET_WS_FALLBACK;
+      const float kpsi = fmaxf(1.0f, S.psia[w] / fabsf((float)psit));  // conditioning of the CI sum
+      const float e1 = estw[0][0] * kpsi, e2 = estw[1][0] * kpsi;
+      S.est[w * 2] = e1;
+      S.est[w * 2 + 1] = e2;
+      if (!(e1 <= (float)P.fallback_tol)) st |= MDET_WS_FALLBACK;
     }
     if (psit == 0.0) st |= MDET_WS_PSI_ZERO;
     if (!all_finite || !isfinite(el) || !isfinite(lg)) st |= MDET_WS_NONFINITE;
@@ -746,47 +800,51 @@ cudaError_t launch_zero_f64(const DevProblem& P, const DevScratch& S, int64_t n_
   const int64_t npad = (n_walk + kWalkerPad - 1) / kWalkerPad * kWalkerPad;
   cudaError_t e = cudaMemsetAsync(S.vu, 0, sizeof(double) * ndt * npad, st);
   if (e != cudaSuccess) return e;
+  if ((e = cudaMemsetAsync(S.psia, 0, sizeof(float) * npad, st)) != cudaSuccess) return e;
   return cudaMemsetAsync(S.psit, 0, sizeof(double) * npad, st);
 }
 
-cudaError_t launch_contract_f64(const DevProblem& P, const DevScratch& S, int64_t n_walk, cudaStream_t st) {
-  static int n_sm = 0;
-  if (!n_sm) {
-    int dev = 0;
-    cudaGetDevice(&dev);
-    if (cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n_sm <= 0) n_sm = 132;
-  }
+cudaError_t launch_contract_f64(const DevProblem& P, const DevScratch& S, int64_t n_walk, cudaStream_t st,
+                                unsigned long long* queue, int persistent_blocks) {
   const int chunk = P.spmm_chunk > 0 ? P.spmm_chunk : 512;
   const int64_t n_chunks = (P.nnz + chunk - 1) / chunk;
   const int64_t n_groups = (n_walk + 255) / 256;
   const int64_t items = n_chunks * n_groups;
   // one work item per warp (full occupancy hides the L2 latency of the gathers), or a
-  // persistent grid of spmm_blocks blocks looping over the items
+  // persistent grid whose warps draw items from a queue (two counters, one per launch)
   int64_t blocks = (items + 3) / 4;
-  if (P.spmm_blocks > 0) blocks = std::min<int64_t>(blocks, P.spmm_blocks);
-  (void)n_sm;
+  int cap = P.spmm_blocks > 0 ? P.spmm_blocks : persistent_blocks;
+  const bool q = queue && cap > 0 && cap < blocks;
+  if (q) {
+    blocks = cap;
+    cudaError_t e = cudaMemsetAsync(queue, 0, 2 * sizeof(unsigned long long), st);
+    if (e != cudaSuccess) return e;
+  }
   const int64_t ndt = (int64_t)P.n_det_sp[0] + P.n_det_sp[1];
   const double* r_up = S.r;
   const double* r_dn = S.r + (size_t)P.n_det_sp[0] * S.wp;
   if (P.contract_impl == 1 && S.rdf && P.csr_val_df) {  // double-float option of the mixed path
     const float2* x_up = S.rdf;
     const float2* x_dn = S.rdf + (size_t)P.n_det_sp[0] * S.wp;
-    k_spmm_df<<<(unsigned)blocks, 128, 0, st>>>(P.csr_row, P.csr_col, P.csr_val_df, P.nnz, chunk, n_chunks,
-                                                 n_groups, x_dn, S.wp, S.vu, ndt, 0, r_up, S.psit);
+    const int64_t b = P.spmm_blocks > 0 ? std::min<int64_t>((items + 3) / 4, P.spmm_blocks) : (items + 3) / 4;
+    k_spmm_df<<<(unsigned)b, 128, 0, st>>>(P.csr_row, P.csr_col, P.csr_val_df, P.nnz, chunk, n_chunks, n_groups,
+                                            x_dn, S.wp, S.vu, ndt, 0, r_up, S.psit, S.psia);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    k_spmm_df<<<(unsigned)blocks, 128, 0, st>>>(P.csc_col, P.csc_row, P.csc_val_df, P.nnz, chunk, n_chunks,
-                                                 n_groups, x_up, S.wp, S.vu, ndt, P.n_det_sp[0], nullptr, nullptr);
+    k_spmm_df<<<(unsigned)b, 128, 0, st>>>(P.csc_col, P.csc_row, P.csc_val_df, P.nnz, chunk, n_chunks, n_groups,
+                                            x_up, S.wp, S.vu, ndt, P.n_det_sp[0], nullptr, nullptr, nullptr);
     return cudaGetLastError();
   }
-  // v = C r_dn (rows = up determinants) with Psi~ = r_up . v
-  k_spmm_wm<<<(unsigned)blocks, 128, 0, st>>>(P.csr_row, P.csr_col, P.csr_val, P.nnz, chunk, n_chunks, n_groups,
-                                               r_dn, S.wp, S.vu, ndt, 0, r_up, S.psit);
+  // v = C r_dn (rows = up determinants) with Psi~ = r_up . v and its magnitude sum
+  auto* kv = q ? k_spmm_wm<true, true> : k_spmm_wm<false, true>;
+  kv<<<(unsigned)blocks, 128, 0, st>>>(P.csr_row, P.csr_col, P.csr_val, P.nnz, chunk, n_chunks, n_groups, r_dn, S.wp,
+                                       S.vu, ndt, 0, r_up, S.psit, S.psia, queue);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   // u = C^T r_up (columns = down determinants), in the paper's column-major order
-  k_spmm_wm<<<(unsigned)blocks, 128, 0, st>>>(P.csc_col, P.csc_row, P.csc_val, P.nnz, chunk, n_chunks, n_groups,
-                                               r_up, S.wp, S.vu, ndt, P.n_det_sp[0], nullptr, nullptr);
+  auto* ku = q ? k_spmm_wm<true, false> : k_spmm_wm<false, false>;
+  ku<<<(unsigned)blocks, 128, 0, st>>>(P.csc_col, P.csc_row, P.csc_val, P.nnz, chunk, n_chunks, n_groups, r_up, S.wp,
+                                       S.vu, ndt, P.n_det_sp[0], nullptr, nullptr, nullptr, q ? queue + 1 : nullptr);
   return cudaGetLastError();
 }
 
@@ -809,6 +867,7 @@ DevScratch scratch_view(const DevScratch& S, const DevProblem& P, int64_t off) {
   V.r = S.r + off;
   if (S.rdf) V.rdf = S.rdf + off;
   V.psit = S.psit + off;
+  V.psia = S.psia + off;
   return V;
 }
 

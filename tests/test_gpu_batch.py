@@ -81,7 +81,7 @@ def test_autotune_picks_valid_shapes_and_stays_correct(small_batch):
     t = ctx.autotune(R, budget_ms=100.0)
     assert t["spmm_chunk"] in (256, 512, 1024, 2048)
     assert t["mo_ec"] in (4, 6, 8)
-    assert t["walker_chunks"] in (1, 2, 4)
+    assert t["walker_chunks"] in (1, 2, 3, 4)
     assert t["trials"] >= 1 and t["best_ms"] > 0
     got = {k: v[idx] for k, v in _to_host(ctx.evaluate(R)).items()}
     torch.cuda.synchronize()

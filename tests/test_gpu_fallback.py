@@ -80,3 +80,65 @@ def test_ill_conditioned_reference_walkers_are_caught(prec):
     tol = dict(tol_psi=1e-10, tol_der=1e-8) if prec == pkg.PRECISION_FP64 else dict(tol_psi=1e-9, tol_der=1e-6)
     rep = compare(got, ref, **tol)
     assert rep["ok"], rep
+
+
+def _walker_errors(got, ref):
+    """Per-walker worst relative error over log|Psi|, the gradient and the
+    Laplacian (the gradient and Laplacian relative to max(|x|, the walker's rms))."""
+    e_log = np.abs(got["log_abs_psi"] - ref["log_abs_psi"])
+    gs = np.sqrt(np.mean(ref["grad"] ** 2, axis=(1, 2)))[:, None, None]
+    e_grad = (np.abs(got["grad"] - ref["grad"]) / np.maximum(np.abs(ref["grad"]), gs)).max(axis=(1, 2))
+    ls = np.sqrt(np.mean(ref["lap"] ** 2, axis=1))[:, None]
+    e_lap = (np.abs(got["lap"] - ref["lap"]) / np.maximum(np.abs(ref["lap"]), ls)).max(axis=1)
+    return np.maximum(e_log, np.maximum(e_grad, e_lap))
+
+
+@pytest.fixture(scope="module")
+def o2100_fb():
+    # 2,100 walkers: among them references with cond_1 up to 1e6 and CI sums that
+    # cancel by up to 2e4, the cases an estimate without the CI-sum conditioning missed
+    wl = synth.oxygen_like_1k(n_walk=2100, seed=123)
+    return wl, oracle.evaluate(wl)
+
+
+@pytest.mark.parametrize("prec", [pkg.PRECISION_FP64, pkg.PRECISION_MIXED])
+def test_error_estimate_bounds_the_error(o2100_fb, prec):
+    """With re-evaluation off (infinite tolerance, estimates still computed), every
+    walker's error against the oracle stays below its l1 estimate (plus 1e-12 for
+    the oracle's own rounding). The estimate is a worst-case bound, typically
+    10^3-10^4 above the error, but not a vacuous one: the median walker sits two
+    orders of magnitude below the path's default tolerance."""
+    wl, ref = o2100_fb
+    ctx = pkg.Context.from_workload(wl, device=0, precision=prec)
+    default_tol = ctx.fallback[0]
+    ctx.set_fallback(1e30, 1)
+    got = _eval(ctx, wl.R)
+    _, est = ctx.error_estimates(wl.n_walk)
+    err = _walker_errors(got, ref)
+    ratio = err / (est[:, 0] + 1e-12)
+    worst = int(np.argmax(ratio))
+    assert ratio[worst] <= 1.0, (worst, err[worst], est[worst], ref["kappa"][worst])
+    assert np.median(err) <= np.median(est[:, 0]) <= default_tol / 100
+    ctx.close()
+
+
+@pytest.mark.parametrize("prec", [pkg.PRECISION_FP64, pkg.PRECISION_MIXED])
+def test_default_tolerance_meets_each_path_target(o2100_fb, prec):
+    """With the default fallback (1e-8 FP64, 1e-5 mixed) every walker of the
+    2,100-walker set is within its path's target of the oracle: the ones the
+    estimate flags are re-evaluated by LU, the others are bounded by it."""
+    wl, ref = o2100_fb
+    ctx = pkg.Context.from_workload(wl, device=0, precision=prec)
+    tol, cap = ctx.fallback
+    assert tol == (1e-8 if prec == pkg.PRECISION_FP64 else 1e-5)
+    got = _eval(ctx, wl.R)
+    fb = (got["status"] & pkg.WS_FALLBACK) != 0
+    assert 0 < fb.sum() <= cap
+    err = _walker_errors(got, ref)
+    assert err[~fb].max() <= tol, (int(np.flatnonzero(~fb)[np.argmax(err[~fb])]), err[~fb].max())
+    # the re-evaluated walkers: the FP64 LU result, at the FP64 tolerances of the parity tests
+    idx = np.flatnonzero(fb)
+    rep = compare({k: v[idx] for k, v in got.items()}, {k: np.asarray(v)[idx] for k, v in ref.items()},
+                  tol_psi=1e-10, tol_der=1e-8)
+    assert rep["ok"], rep
+    ctx.close()

@@ -56,6 +56,12 @@ def _gpu_eval(ctx, R):
 
 
 @pytest.fixture(scope="module")
+def o2100():
+    wl = synth.oxygen_like_1k(n_walk=2100, seed=123)
+    return wl, oracle.evaluate(wl)
+
+
+@pytest.fixture(scope="module")
 def o1k():
     wl = synth.oxygen_like_1k(n_walk=64)
     return wl, oracle.evaluate(wl)
@@ -120,14 +126,37 @@ def test_ragged_walker_counts(n_walk, prec):
 
 @pytest.mark.parametrize("chunks", [1, 2, 3, 4])
 def test_mixed_walker_chunks(chunks):
-    """Mixed precision with the batch cut into chunks evaluated on overlapping
-    streams (ragged: 900 walkers = 3.5 tiles of 256)."""
+    """Mixed precision with the batch cut into chunks pipelined over two streams
+    (ragged: 900 walkers = 3.5 tiles of 256)."""
     wl = synth.oxygen_like_1k(n_walk=900, seed=99)
     ref = oracle.evaluate(wl)
     ctx = pkg.Context.from_workload(wl, device=0, precision=pkg.PRECISION_MIXED)
     ctx.set_walker_chunks(chunks)
     rep = compare(_gpu_eval(ctx, wl.R), ref, **TOL[pkg.PRECISION_MIXED])
     assert rep["ok"], rep
+    assert ctx.last_chunks == chunks
+
+
+@pytest.mark.parametrize("prec,chunks,blocks", [(pkg.PRECISION_MIXED, 8, 0), (pkg.PRECISION_MIXED, 5, 3),
+                                                (pkg.PRECISION_MIXED, 3, 1), (pkg.PRECISION_FP64, 1, 2)])
+def test_persistent_contraction_grids(o2100, prec, chunks, blocks):
+    """The contraction on persistent grids whose warps draw work items from a
+    counter: 8 and 5 pipelined chunks of a ragged 2,100-walker batch, grids of 1
+    to 3 blocks (every warp takes many items) and the FP64 path with a capped grid.
+    The mixed fallback tolerance is tightened to 1e-7, so that every walker meets
+    the test tolerances: the fallback then re-evaluates tens of walkers flagged by
+    the pipelined chunks. Stage times come back for every stage."""
+    wl, ref = o2100
+    ctx = pkg.Context.from_workload(wl, device=0, precision=prec)
+    ctx.set_tuning(walker_chunks=chunks, spmm_blocks=blocks)
+    if prec == pkg.PRECISION_MIXED:
+        ctx.set_fallback(1e-7, 512)
+    ctx.set_profiling(True)
+    rep = compare(_gpu_eval(ctx, wl.R), ref, **TOL[prec])
+    assert rep["ok"], rep
+    assert ctx.last_chunks == chunks
+    prof = ctx.profile()
+    assert all(v > 0 for k, v in prof.items() if k != "zero"), prof
 
 
 def test_fp64_grow_and_shrink_batch(o1k):
