@@ -237,8 +237,10 @@ def run_ours(args):
                                             clock_index)
         n_fb = int(((out["status"] & pkg.WS_FALLBACK) != 0).sum().item())
         ms = _max_over_ranks(statistics.mean(step_ms), dist, dev)
+        n_esc = int(((out["status"] & pkg.WS_ESCALATED) != 0).sum().item())
         results[name] = dict(ms=ms, value=whole_job_value(W, world, ms), kern=kern, clocks=clocks, n_fb=n_fb,
-                             chunks=ctx.last_chunks, fallback_tol=ctx.fallback[0])
+                             n_esc=n_esc, chunks=ctx.last_chunks, kernels=ctx.last_kernels,
+                             fallback_tol=ctx.fallback[0])
 
     for pname in [primary] + others:
         ctx = pkg.Context.from_workload(wl, device=local, precision=prec_of[pname])
@@ -270,10 +272,8 @@ def run_ours(args):
     st = ctxs[primary].stats()
     main = results[primary]
     main_chunks = main["chunks"]
-    # kernels per evaluation: orbitals, reference, ratios, 2 contractions, final per walker chunk,
-    # plus the 5 kernels of the stability fallback when it is enabled
-    fb_tol, fb_cap = ctxs[primary].fallback
-    st_launches = 6 * main_chunks + (5 if fb_tol > 0 else 0)
+    # kernels per evaluation, as the library counts them (chunks and fallback included)
+    st_launches = main["kernels"]
 
     # end to end through the host-memory C-ABI call: H2D of R and D2H of all outputs per step
     ctx = ctxs[primary]
@@ -328,7 +328,7 @@ def run_ours(args):
                     "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms},
             "gpu_launches": st_launches * args.steps,
             "kernels_ms": kern,
-            "fallback_walkers": main["n_fb"],
+            "fallback_walkers": main["n_fb"], "escalated_walkers": main["n_esc"],
             "roofline": roofline}
     if df_contract is not None:
         line["mixed_df_contraction"] = df_contract
@@ -373,6 +373,7 @@ def run_batched(args):
     tunes = [c.autotune(R, budget_ms=args.tune_ms) for c, R in zip(ctxs, Rs)]
     tune_s = time.perf_counter() - t0
     batch = pkg.Batch(ctxs, Rs, n_streams=args.streams)
+    batched_kernels = sum(c.last_kernels for c in ctxs)  # as enqueued by the batch (its warm-up pass)
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
     stream = torch.cuda.current_stream(dev)
     for _ in range(args.warmup):
@@ -409,7 +410,10 @@ def run_batched(args):
             "sum_of_solo_ms": solo, "batch_gain": solo / ms,
             "tuning_histogram": {k: dict(zip(*np.unique([t[k] for t in tunes], return_counts=True)))
                                  for k in ("spmm_chunk", "mo_ec", "walker_chunks")},
-            "clocks": clk.summary(), "gpu_launches": 6 * len(wls) * args.steps}
+            "clocks": clk.summary(),
+            # kernels per expansion as the library counts them (the solo runs above are not in a
+            # batch, so the count of a batched evaluation is taken with the batch's choices)
+            "gpu_launches": batched_kernels * args.steps}
     line["tuning_histogram"] = {k: {str(a): int(b) for a, b in v.items()} for k, v in line["tuning_histogram"].items()}
     print(json.dumps(line), flush=True)
     batch.close()

@@ -68,6 +68,9 @@ enum {
 #define MDET_WS_FALLBACK 0x10u      /* the ratio-table result was estimated too inaccurate (or the
                                        reference singular): the walker was re-evaluated by full LU
                                        of every determinant (see mdet_set_fallback) */
+#define MDET_WS_ESCALATED 0x20u     /* mixed precision: the walker's estimate exceeded the tolerance
+                                       and it was re-evaluated by the FP64 ratio table (and, with
+                                       MDET_WS_FALLBACK, then by full LU; see mdet_set_fallback) */
 
 typedef struct {
   int32_t n_up, n_dn, n_ao, n_mo, n_int;
@@ -230,10 +233,13 @@ mdet_status mdet_get_ratios(mdet_ctx* ctx, int64_t n_walk, double* r_up, double*
  * tol (default 1e-5 for mixed, 1e-8 for FP64 precision: the accuracy target of
  * each path), or whose reference is singular, is re-evaluated on the GPU in FP64
  * by LU of every distinct determinant, its own contraction and epilogue; its
- * status gets MDET_WS_FALLBACK. At most max_walkers walkers per evaluation are
- * re-evaluated (default 256 for mixed, 512 for FP64; the scratch grows with
- * it); further ones keep the table result and MDET_WS_REF_ILLCOND. tol <= 0
- * disables the fallback. Supported for n_up, n_dn <= MDET_FALLBACK_MAX_SPIN.
+ * status gets MDET_WS_FALLBACK. With mixed precision the flagged walkers may
+ * first be re-evaluated by the FP64 ratio table (mdet_set_escalation), whose
+ * estimate is 2^6 smaller; only those still above tol then go through full LU.
+ * At most max_walkers walkers per evaluation are re-evaluated (default 256 for
+ * mixed, 512 for FP64; the scratch grows with it); further ones keep the table
+ * result and MDET_WS_REF_ILLCOND. tol <= 0 disables the fallback. Supported for
+ * n_up, n_dn <= MDET_FALLBACK_MAX_SPIN.
  */
 #define MDET_FALLBACK_MAX_SPIN 17
 mdet_status mdet_set_fallback(mdet_ctx* ctx, double tol, int max_walkers);
@@ -262,6 +268,18 @@ mdet_status mdet_truncate_norm(int64_t n_det, int n_int, const uint64_t* det_up,
                                const double* coef, double eps_up, double eps_dn, uint8_t* keep, double* norm_up,
                                double* norm_dn, int64_t* counts);
 
+/*
+ * Escalation of flagged mixed-precision walkers to the FP64 ratio table before
+ * the full-LU path: MDET_ESCALATE_AUTO (default) takes it when full LU is the
+ * costlier (distinct determinants x n^3 above 8e6, n the larger spin count),
+ * MDET_ESCALATE_ALWAYS and MDET_ESCALATE_NEVER force the choice. Escalated
+ * walkers get MDET_WS_ESCALATED. No effect on FP64 contexts.
+ */
+#define MDET_ESCALATE_AUTO 0
+#define MDET_ESCALATE_ALWAYS 1
+#define MDET_ESCALATE_NEVER 2
+mdet_status mdet_set_escalation(mdet_ctx* ctx, int mode);
+
 /* The current fallback tolerance and walker cap (host pointers). */
 mdet_status mdet_get_fallback(const mdet_ctx* ctx, double* tol, int* max_walkers);
 
@@ -281,9 +299,10 @@ mdet_status mdet_get_fallback(const mdet_ctx* ctx, double* tol, int* max_walkers
  */
 mdet_status mdet_set_walker_chunks(mdet_ctx* ctx, int n_chunks);
 
-/* Walker chunks the last mdet_evaluate of this context was cut into (0 before
- * the first evaluation). */
-mdet_status mdet_get_last_chunks(const mdet_ctx* ctx, int32_t* n_chunks);
+/* The walker chunks the last mdet_evaluate of this context was cut into and the
+ * kernels it launched (memset and copy operations not counted); 0 before the
+ * first evaluation. Either pointer may be null. */
+mdet_status mdet_get_last_launches(const mdet_ctx* ctx, int32_t* n_chunks, int32_t* n_kernels);
 
 /*
  * Tile shapes of the evaluation kernels (tuning knobs with no counterpart in

@@ -21,6 +21,7 @@ WS_REF_ILLCOND = 0x2
 WS_PSI_ZERO = 0x4
 WS_NONFINITE = 0x8
 WS_FALLBACK = 0x10
+WS_ESCALATED = 0x20
 MAX_EXC = 4
 
 _lib = None
@@ -83,7 +84,8 @@ def load_library(build_if_missing: bool = True):
     L.mdet_psi_tilde_noalloc.argtypes = [vp, i64, vp, i64, vp, vp]
     L.mdet_set_profiling.argtypes = [vp, i32]
     L.mdet_set_walker_chunks.argtypes = [vp, i32]
-    L.mdet_get_last_chunks.argtypes = [vp, vp]
+    L.mdet_get_last_launches.argtypes = [vp, vp, vp]
+    L.mdet_set_escalation.argtypes = [vp, i32]
     L.mdet_set_fallback.argtypes = [vp, C.c_double, i32]
     L.mdet_get_fallback.argtypes = [vp, vp, vp]
     L.mdet_get_error_estimates.argtypes = [vp, i64, vp, vp]
@@ -101,7 +103,7 @@ def load_library(build_if_missing: bool = True):
     for name in ("mdet_create", "mdet_set_system", "mdet_set_orbitals", "mdet_set_ci_expansion", "mdet_evaluate",
                  "mdet_evaluate_host", "mdet_get_ratios", "mdet_get_stats", "mdet_get_spin_dets",
                  "mdet_get_ci_matrix", "mdet_omega_sort", "mdet_truncate_norm", "mdet_sm_chain", "mdet_set_ci_expansion_device", "mdet_set_profiling", "mdet_get_profile",
-                 "mdet_psi_tilde_noalloc", "mdet_set_walker_chunks", "mdet_get_last_chunks", "mdet_selftest_df32", "mdet_get_tuning",
+                 "mdet_psi_tilde_noalloc", "mdet_set_walker_chunks", "mdet_get_last_launches", "mdet_set_escalation", "mdet_selftest_df32", "mdet_get_tuning",
                  "mdet_set_tuning", "mdet_autotune", "mdet_batch_evaluate", "mdet_batch_create", "mdet_batch_launch", "mdet_set_fallback", "mdet_get_fallback",
                  "mdet_get_error_estimates"):
         getattr(L, name).restype = i32
@@ -412,8 +414,18 @@ class Context:
                     trials=t.trials, spmm_blocks=t.spmm_blocks, mo_impl=t.mo_impl,
                     contract_impl=t.contract_impl)
 
-    def set_fallback(self, tol, max_walkers=64):
-        """Re-evaluate walkers whose estimated table error exceeds tol by full LU (tol <= 0: off)."""
+    ESCALATE_AUTO, ESCALATE_ALWAYS, ESCALATE_NEVER = 0, 1, 2
+
+    def set_escalation(self, mode):
+        """Mixed precision: FP64 re-evaluation of flagged walkers before full LU
+        (mdet_set_escalation; ESCALATE_AUTO, ESCALATE_ALWAYS or ESCALATE_NEVER)."""
+        self._check(self._L.mdet_set_escalation(self._h, int(mode)), "mdet_set_escalation")
+
+    def set_fallback(self, tol, max_walkers=None):
+        """Re-evaluate walkers whose estimated table error exceeds tol (tol <= 0: off), at most
+        max_walkers per evaluation (None keeps the current cap)."""
+        if max_walkers is None:
+            max_walkers = self.fallback[1]
         self._check(self._L.mdet_set_fallback(self._h, float(tol), int(max_walkers)), "mdet_set_fallback")
 
     @property
@@ -434,12 +446,20 @@ class Context:
         """Mixed precision: pipeline a batch in n_chunks walker chunks (0 = automatic, 1 = none)."""
         self._check(self._L.mdet_set_walker_chunks(self._h, int(n_chunks)), "mdet_set_walker_chunks")
 
+    def _last_launches(self):
+        ch, nk = C.c_int32(0), C.c_int32(0)
+        self._check(self._L.mdet_get_last_launches(self._h, C.byref(ch), C.byref(nk)), "mdet_get_last_launches")
+        return int(ch.value), int(nk.value)
+
     @property
     def last_chunks(self):
-        """Walker chunks of the last evaluation (mdet_get_last_chunks; 0 before the first)."""
-        n = C.c_int32(0)
-        self._check(self._L.mdet_get_last_chunks(self._h, C.byref(n)), "mdet_get_last_chunks")
-        return int(n.value)
+        """Walker chunks of the last evaluation (mdet_get_last_launches; 0 before the first)."""
+        return self._last_launches()[0]
+
+    @property
+    def last_kernels(self):
+        """Kernels the last evaluation launched (mdet_get_last_launches; 0 before the first)."""
+        return self._last_launches()[1]
 
     def set_profiling(self, enable=True):
         self._check(self._L.mdet_set_profiling(self._h, int(bool(enable))), "mdet_set_profiling")

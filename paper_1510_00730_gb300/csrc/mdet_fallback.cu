@@ -12,6 +12,12 @@
 //   k_fb_rows    fixed grid over (walker, 64 rows) items, a warp per row: v = C d_dn, u = C^T d_up, Psi, gradient
 //                and Laplacian sums, reduced per block then with atomics
 //   k_fb_out     per flagged walker: potential energy and outputs
+//
+// Mixed precision first escalates: the flagged walkers (at most the cap) are
+// gathered (k_esc_gather), evaluated again by the FP64 ratio-table kernels on a
+// scratch of their own, and only those whose FP64 estimate still exceeds the
+// tolerance go through the full-LU path above; k_esc_scatter writes the results
+// back to the walkers' slots.
 #include <algorithm>
 #include <cfloat>
 #include <cmath>
@@ -290,16 +296,85 @@ __global__ void __launch_bounds__(64) k_fb_out(DevProblem P, DevScratch S, const
   }
 }
 
+// Escalation: the listed walkers (count, then indices; at most cap) are copied to
+// the front of Re, and *live receives min(count, cap) for the FP64 kernels.
+__global__ void k_esc_gather(const int* __restrict__ list, int cap, int n3, const double* __restrict__ R,
+                             double* __restrict__ Re, int* __restrict__ live) {
+  const int count = min(list[0], cap);
+  if (blockIdx.x == 0 && threadIdx.x == 0) *live = count;
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < (int64_t)count * n3;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = t / n3, q = t - i * n3;
+    Re[t] = R[(int64_t)list[1 + i] * n3 + q];
+  }
+}
+
+// Without the FP64 table every gathered walker goes to full LU.
+__global__ void k_esc_mark(const int* __restrict__ live, uint32_t* __restrict__ wstat, int cap) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < cap && i < *live) wstat[i] = MDET_WS_FALLBACK;
+}
+
+// Escalation: the results of slot i go back to walker list[1 + i], whose status
+// becomes that of its FP64 re-evaluation plus or_bits. grid cap, block 64.
+__global__ void __launch_bounds__(64) k_esc_scatter(const int* __restrict__ list, int cap, int N,
+                                                    const EscOut e, uint32_t or_bits, double* __restrict__ log_abs_psi,
+                                                    int8_t* __restrict__ sign, double* __restrict__ grad,
+                                                    double* __restrict__ lap, double* __restrict__ e_local,
+                                                    uint32_t* __restrict__ status, uint32_t* __restrict__ wstat) {
+  const int count = min(list[0], cap);
+  const int i = blockIdx.x;
+  if (i >= count) return;
+  const int64_t w = list[1 + i];
+  for (int q = threadIdx.x; q < 3 * N; q += blockDim.x) grad[w * 3 * N + q] = e.grad[(int64_t)i * 3 * N + q];
+  for (int q = threadIdx.x; q < N; q += blockDim.x) lap[w * N + q] = e.lap[(int64_t)i * N + q];
+  if (threadIdx.x == 0) {
+    log_abs_psi[w] = e.log_abs_psi[i];
+    sign[w] = e.sign[i];
+    if (e_local) e_local[w] = e.e_local[i];
+    const uint32_t st = e.status[i] | or_bits;
+    wstat[w] = st;
+    if (status) status[w] = st;
+  }
+}
+
 }  // namespace
+
+cudaError_t launch_fb_list(const DevProblem& P, uint32_t* wstat, uint32_t* status, int64_t n_walk, int* list,
+                           cudaStream_t st) {
+  cudaError_t e = cudaMemsetAsync(list, 0, sizeof(int), st);
+  if (e != cudaSuccess) return e;
+  k_fb_list<<<(unsigned)((n_walk + 255) / 256), 256, 0, st>>>(P, wstat, status, n_walk, list);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_esc_gather(const int* list, int cap, int n3, const double* R, double* Re, int* live,
+                              cudaStream_t st) {
+  const int64_t total = (int64_t)cap * n3;
+  k_esc_gather<<<(unsigned)std::max<int64_t>(1, std::min<int64_t>((total + 255) / 256, 1024)), 256, 0, st>>>(
+      list, cap, n3, R, Re, live);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_esc_mark(const int* live, uint32_t* wstat, int cap, cudaStream_t st) {
+  k_esc_mark<<<(unsigned)((cap + 255) / 256), 256, 0, st>>>(live, wstat, cap);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_esc_scatter(const int* list, int cap, int N, const EscOut& e, uint32_t or_bits,
+                               double* log_abs_psi, int8_t* sign, double* grad, double* lap, double* e_local,
+                               uint32_t* status, uint32_t* wstat, cudaStream_t st) {
+  k_esc_scatter<<<(unsigned)cap, 64, 0, st>>>(list, cap, N, e, or_bits, log_abs_psi, sign, grad, lap, e_local, status,
+                                              wstat);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_fallback(const DevProblem& P, const DevScratch& S, int64_t n_walk, const double* R,
                             double* log_abs_psi, int8_t* sign, double* grad, double* lap, double* e_local,
                             uint32_t* status, cudaStream_t st) {
   if (!(P.fallback_tol > 0.0) || !S.fb || P.n_up > kFbMax) return cudaSuccess;
-  cudaError_t e = cudaMemsetAsync(S.fb_list, 0, sizeof(int), st);
+  cudaError_t e = launch_fb_list(P, S.wstat, status, n_walk, S.fb_list, st);
   if (e != cudaSuccess) return e;
-  k_fb_list<<<(unsigned)((n_walk + 255) / 256), 256, 0, st>>>(P, S.wstat, status, n_walk, S.fb_list);
-  if ((e = cudaGetLastError()) != cudaSuccess) return e;
   const int nmax = P.n_up > P.n_dn ? P.n_up : P.n_dn;
   const int ntot = P.n_det_sp[0] + P.n_det_sp[1];
   const size_t smem = sizeof(double) * 64 * nmax * nmax;

@@ -40,6 +40,12 @@ struct mdet_ctx {
   std::vector<void*> dev_problem_allocs;
   DevProblem P{};
   DevScratch S{};
+  // escalation of mixed-precision walkers (FP64 re-evaluation of the flagged ones):
+  // scratch for fallback_cap walkers, their positions, compact outputs and live count
+  DevScratch E{};
+  EscOut eo{};
+  double* e_R = nullptr;
+  int* e_live = nullptr;
   cudaStream_t own_stream = nullptr;
   cudaStream_t last_stream = nullptr;
   int64_t last_walk = 0;
@@ -51,6 +57,8 @@ struct mdet_ctx {
   int n_chunks_cfg = 0;  // 0: automatic
   double fallback_tol = 0.0;  // set from the precision in mdet_create
   int fallback_cap = 256;  // set from the precision in mdet_create
+  int escalate = MDET_ESCALATE_AUTO;
+  bool in_batch = false;  // set while a batch enqueues this context's evaluation
   std::vector<int32_t> csr_ptr, csc_ptr;
   int spmm_chunk = 512;  // tile shapes (mdet_set_tuning / mdet_autotune)
   int spmm_blocks = 0;
@@ -65,6 +73,7 @@ struct mdet_ctx {
   bool profiling = false;
   bool have_profile = false;
   int prof_chunks = 0;
+  int last_kernels = 0;  // kernels the last evaluation launched
   // per chunk: the start and end of every stage (stages of one chunk may run on
   // different streams, after waits)
   static constexpr int kEvPerChunk = 2 * MDET_N_STAGES;
@@ -204,13 +213,24 @@ void free_problem(mdet_ctx* c) {
   c->P = DevProblem{};
 }
 
-void free_scratch(mdet_ctx* c) {
-  DevScratch& S = c->S;
+void free_arrays(DevScratch& S) {
   void* ptrs[] = {S.phi, S.Ainv, S.ld0, S.sg0, S.g, S.kap, S.est, S.T, S.Tdf, S.r, S.rdf, S.vu, S.psit, S.psia, S.wstat,
                   S.fb, S.fb_list, S.fb_acc, S.queue, S.R_stage, S.out_stage};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   S = DevScratch{};
+}
+
+void free_scratch(mdet_ctx* c) {
+  free_arrays(c->S);
+  free_arrays(c->E);
+  void* ptrs[] = {c->e_R, c->e_live, c->eo.log_abs_psi, c->eo.sign, c->eo.grad, c->eo.lap, c->eo.e_local,
+                  c->eo.status};
+  for (void* p : ptrs)
+    if (p) cudaFree(p);
+  c->e_R = nullptr;
+  c->e_live = nullptr;
+  c->eo = EscOut{};
 }
 
 // Host step shared by both preprocessing paths. From the distinct determinants
@@ -424,12 +444,11 @@ mdet_status dalloc(mdet_ctx* c, T** p, size_t count) {
   return MDET_OK;
 }
 
-mdet_status ensure_scratch(mdet_ctx* c, int64_t n_walk) {
-  DevScratch& S = c->S;
-  if (n_walk <= S.cap_walk) return MDET_OK;
-  free_scratch(c);
+// The per-walker arrays of one evaluation of W walkers: FP64 tables and, with
+// df_tables / df_ratios, their double-float copies (mixed path). Padded walker
+// columns of the walker-minor tables hold finite values.
+mdet_status alloc_eval_arrays(mdet_ctx* c, DevScratch& S, int64_t W, bool df_tables, bool df_ratios) {
   const DevProblem& P = c->P;
-  const int64_t W = n_walk;
   const int64_t wp = (W + kWalkerPad - 1) / kWalkerPad * kWalkerPad;
   const int64_t N = P.n_elec, M = P.n_mo;
   const int64_t ndt = (int64_t)P.n_det_sp[0] + P.n_det_sp[1];
@@ -442,12 +461,14 @@ mdet_status ensure_scratch(mdet_ctx* c, int64_t n_walk) {
   if ((s = dalloc(c, &S.kap, (size_t)W * 2))) return s;
   if ((s = dalloc(c, &S.est, (size_t)W * 2))) return s;
   if ((s = dalloc(c, &S.T, (size_t)N * M * wp))) return s;
-  if (c->precision == MDET_PRECISION_MIXED) {
+  CUDA_TRY(c, cudaMemset(S.T, 0, sizeof(double) * N * M * wp));
+  if (df_tables) {
     if ((s = dalloc(c, &S.Tdf, (size_t)N * M * wp))) return s;
     CUDA_TRY(c, cudaMemset(S.Tdf, 0, sizeof(float2) * N * M * wp));
   }
   if ((s = dalloc(c, &S.r, (size_t)ndt * wp))) return s;
-  if (c->precision == MDET_PRECISION_MIXED && c->contract_impl == 1) {
+  CUDA_TRY(c, cudaMemset(S.r, 0, sizeof(double) * ndt * wp));
+  if (df_ratios) {
     if ((s = dalloc(c, &S.rdf, (size_t)ndt * wp))) return s;
     CUDA_TRY(c, cudaMemset(S.rdf, 0, sizeof(float2) * ndt * wp));
   }
@@ -455,17 +476,106 @@ mdet_status ensure_scratch(mdet_ctx* c, int64_t n_walk) {
   if ((s = dalloc(c, &S.psit, (size_t)wp))) return s;
   if ((s = dalloc(c, &S.psia, (size_t)wp))) return s;
   if ((s = dalloc(c, &S.wstat, (size_t)W))) return s;
-  if ((s = dalloc(c, &S.queue, (size_t)2 * mdet_ctx::kMaxChunks))) return s;
-  if (P.fallback_tol > 0.0 && P.n_up <= MDET_FALLBACK_MAX_SPIN) {
-    const int64_t nmax = std::max(P.n_up, P.n_dn);
-    if ((s = dalloc(c, &S.fb, (size_t)P.fallback_cap * ndt * (3 + 4 * nmax)))) return s;
-    if ((s = dalloc(c, &S.fb_list, (size_t)P.fallback_cap + 1))) return s;
-    if ((s = dalloc(c, &S.fb_acc, (size_t)P.fallback_cap * (3 + 8 * MDET_FALLBACK_MAX_SPIN)))) return s;
-  }
-  // padded walker columns of the tables must hold finite values
-  CUDA_TRY(c, cudaMemset(S.T, 0, sizeof(double) * N * M * wp));
   S.cap_walk = W;
   S.wp = wp;
+  return MDET_OK;
+}
+
+// The full-LU fallback's scratch for P.fallback_cap walkers.
+mdet_status alloc_fallback(mdet_ctx* c, DevScratch& S) {
+  const DevProblem& P = c->P;
+  const int64_t ndt = (int64_t)P.n_det_sp[0] + P.n_det_sp[1];
+  const int64_t nmax = std::max(P.n_up, P.n_dn);
+  mdet_status s;
+  if ((s = dalloc(c, &S.fb, (size_t)P.fallback_cap * ndt * (3 + 4 * nmax)))) return s;
+  if ((s = dalloc(c, &S.fb_list, (size_t)P.fallback_cap + 1))) return s;
+  return dalloc(c, &S.fb_acc, (size_t)P.fallback_cap * (3 + 8 * MDET_FALLBACK_MAX_SPIN));
+}
+
+// Whether mixed precision re-evaluates its flagged walkers by the FP64 ratio
+// table before the full-LU path (MDET_ESCALATE_AUTO: when it pays). The
+// escalation costs a fixed latency of about 0.5-2 ms (a dozen dependent launches
+// over up to a few hundred walkers) and a few microseconds per walker; full LU
+// costs about 5-7 ns per (distinct determinant x n^3), n the larger spin count:
+// 24 us per walker for 6,030 determinants of 9 electrons, 320 us for the largest
+// 17-electron expansions. Alone on the GPU the two tie at about 4e6 units per
+// walker with ~100 flagged walkers, so escalation is taken above 8e6; in a batch
+// the other expansions' kernels hide its latency, and it is always taken.
+bool escalation_on(const mdet_ctx* c) {
+  if (c->escalate != MDET_ESCALATE_AUTO) return c->escalate == MDET_ESCALATE_ALWAYS;
+  if (c->in_batch) return true;
+  const double ndt = (double)c->P.n_det_sp[0] + c->P.n_det_sp[1];
+  const double n = std::max(c->P.n_up, c->P.n_dn);
+  return ndt * n * n * n > 8e6;
+}
+
+mdet_status ensure_scratch(mdet_ctx* c, int64_t n_walk) {
+  DevScratch& S = c->S;
+  if (n_walk <= S.cap_walk) return MDET_OK;
+  free_scratch(c);
+  const DevProblem& P = c->P;
+  const bool mixed = c->precision == MDET_PRECISION_MIXED;
+  mdet_status s;
+  if ((s = alloc_eval_arrays(c, S, n_walk, mixed, mixed && c->contract_impl == 1))) return s;
+  if ((s = dalloc(c, &S.queue, (size_t)2 * mdet_ctx::kMaxChunks))) return s;
+  if (P.fallback_tol > 0.0 && P.n_up <= MDET_FALLBACK_MAX_SPIN) {
+    if (!mixed) return alloc_fallback(c, S);
+    // mixed: the list of flagged walkers, then an FP64 re-evaluation of at most fallback_cap
+    // of them (orbitals, optionally the ratio table, then full LU) on a scratch of their own
+    const int cap = P.fallback_cap;
+    const int64_t N = P.n_elec;
+    if ((s = dalloc(c, &S.fb_list, (size_t)cap + 1))) return s;
+    DevScratch& E = c->E;
+    if ((s = alloc_eval_arrays(c, E, cap, false, false)) || (s = alloc_fallback(c, E))) return s;
+    if ((s = dalloc(c, &c->e_R, (size_t)cap * N * 3)) || (s = dalloc(c, &c->e_live, 1)) ||
+        (s = dalloc(c, &c->eo.log_abs_psi, (size_t)cap)) || (s = dalloc(c, &c->eo.sign, (size_t)cap)) ||
+        (s = dalloc(c, &c->eo.grad, (size_t)cap * N * 3)) || (s = dalloc(c, &c->eo.lap, (size_t)cap * N)) ||
+        (s = dalloc(c, &c->eo.e_local, (size_t)cap)) || (s = dalloc(c, &c->eo.status, (size_t)cap)))
+      return s;
+    E.live = c->e_live;
+  }
+  return MDET_OK;
+}
+
+// Mixed precision: walkers whose estimate exceeds the tolerance (at most
+// fallback_cap) are gathered and their orbitals evaluated in FP64. With `table`
+// they are evaluated again by the FP64 ratio-table kernels, whose estimate is
+// 2^6 smaller, and those still above the tolerance go through the full-LU path;
+// without it, all of them do. The results replace the mixed ones. All on stream
+// st, without host waits.
+mdet_status refine(mdet_ctx* c, bool table, int64_t n_walk, const double* R, double* log_abs_psi, int8_t* sign,
+                   double* grad, double* lap, double* e_local, uint32_t* status, cudaStream_t st) {
+  const DevProblem& P = c->P;
+  DevScratch& S = c->S;
+  DevScratch& E = c->E;
+  const int cap = P.fallback_cap;
+  const int N = P.n_elec;
+  CUDA_TRY(c, launch_fb_list(P, S.wstat, status, n_walk, S.fb_list, st));
+  CUDA_TRY(c, cudaMemsetAsync(E.wstat, 0, sizeof(uint32_t) * cap, st));
+  CUDA_TRY(c, launch_esc_gather(S.fb_list, cap, 3 * N, R, c->e_R, c->e_live, st));
+  CUDA_TRY(c, launch_mo_f64(P, E, cap, c->e_R, st));
+  const EscOut& o = c->eo;
+  if (!table) {
+    CUDA_TRY(c, launch_esc_mark(c->e_live, E.wstat, cap, st));
+    CUDA_TRY(c, launch_fallback(P, E, cap, c->e_R, o.log_abs_psi, o.sign, o.grad, o.lap, o.e_local, o.status, st));
+    CUDA_TRY(c, launch_esc_scatter(S.fb_list, cap, N, o, 0u, log_abs_psi, sign, grad, lap, e_local, status, S.wstat,
+                                   st));
+    return MDET_OK;
+  }
+  CUDA_TRY(c, launch_ref_tables(P, E, cap, false, st));
+  CUDA_TRY(c, launch_ratios_f64(P, E, cap, st));
+  CUDA_TRY(c, launch_zero_f64(P, E, cap, st));
+  // few walkers: short work items (64 nonzeros) keep the contraction's chains short, and the
+  // epilogue spreads each walker's determinants over 512 threads
+  DevProblem Pe = P;
+  Pe.spmm_chunk = 64;
+  Pe.spmm_blocks = 0;
+  CUDA_TRY(c, launch_contract_f64(Pe, E, cap, st));
+  CUDA_TRY(c, launch_final(P, E, cap, c->e_R, o.log_abs_psi, o.sign, o.grad, o.lap, o.e_local, o.status, false, st,
+                           true));
+  CUDA_TRY(c, launch_fallback(P, E, cap, c->e_R, o.log_abs_psi, o.sign, o.grad, o.lap, o.e_local, o.status, st));
+  CUDA_TRY(c, launch_esc_scatter(S.fb_list, cap, N, o, MDET_WS_ESCALATED, log_abs_psi, sign, grad, lap, e_local,
+                                 status, S.wstat, st));
   return MDET_OK;
 }
 
@@ -968,8 +1078,21 @@ mdet_status mdet_evaluate(mdet_ctx* c, int64_t n_walk, const double* R, double* 
     CUDA_TRY(c, cudaStreamWaitEvent(st, c->joined, 0));
   }
   c->prof_chunks = nch;
-  // stability fallback over the whole batch, after every chunk has finished
-  CUDA_TRY(c, launch_fallback(P, c->S, n_walk, R, log_abs_psi, sign, grad, lap, e_local, status, st));
+  // stability fallback over the whole batch, after every chunk has finished: mixed precision
+  // escalates to FP64 first, FP64 goes to full LU directly
+  // kernels: 6 per chunk (orbitals, reference, ratios, 2 contractions, epilogue); the full-LU
+  // fallback 5 (list, dets, scale, rows, out); the mixed refinement adds its list, gather,
+  // FP64 orbitals and scatter, and either the mark or the 5 FP64 table kernels
+  c->last_kernels = 6 * nch;
+  if (mixed && c->E.fb && P.fallback_tol > 0.0) {
+    const bool table = escalation_on(c);
+    mdet_status es = refine(c, table, n_walk, R, log_abs_psi, sign, grad, lap, e_local, status, st);
+    if (es != MDET_OK) return es;
+    c->last_kernels += 4 + 5 + (table ? 5 : 1);
+  } else {
+    CUDA_TRY(c, launch_fallback(P, c->S, n_walk, R, log_abs_psi, sign, grad, lap, e_local, status, st));
+    if (P.fallback_tol > 0.0 && c->S.fb && P.n_up <= MDET_FALLBACK_MAX_SPIN) c->last_kernels += 5;
+  }
   c->have_profile = prof;
   c->last_stream = st;
   c->last_walk = n_walk;
@@ -1048,12 +1171,18 @@ mdet_status mdet_get_ratios(mdet_ctx* c, int64_t n_walk, double* r_up, double* r
 
 mdet_status mdet_set_fallback(mdet_ctx* c, double tol, int max_walkers) {
   if (!c || max_walkers < 1 || max_walkers > 65535) return MDET_E_ARG;
-  const bool resize = max_walkers != c->fallback_cap || (tol > 0.0 && !c->S.fb && c->S.cap_walk > 0);
+  const bool resize = max_walkers != c->fallback_cap || (tol > 0.0 && !c->S.fb && !c->E.fb && c->S.cap_walk > 0);
   c->fallback_tol = tol;
   c->fallback_cap = max_walkers;
   c->P.fallback_tol = tol;
   c->P.fallback_cap = max_walkers;
   if (resize) free_scratch(c);  // the fallback scratch is sized by the cap
+  return MDET_OK;
+}
+
+mdet_status mdet_set_escalation(mdet_ctx* c, int mode) {
+  if (!c || mode < MDET_ESCALATE_AUTO || mode > MDET_ESCALATE_NEVER) return MDET_E_ARG;
+  c->escalate = mode;
   return MDET_OK;
 }
 
@@ -1070,9 +1199,10 @@ mdet_status mdet_set_walker_chunks(mdet_ctx* c, int n_chunks) {
   return MDET_OK;
 }
 
-mdet_status mdet_get_last_chunks(const mdet_ctx* c, int32_t* n_chunks) {
-  if (!c || !n_chunks) return MDET_E_ARG;
-  *n_chunks = c->last_walk > 0 ? c->prof_chunks : 0;
+mdet_status mdet_get_last_launches(const mdet_ctx* c, int32_t* n_chunks, int32_t* n_kernels) {
+  if (!c) return MDET_E_ARG;
+  if (n_chunks) *n_chunks = c->last_walk > 0 ? c->prof_chunks : 0;
+  if (n_kernels) *n_kernels = c->last_walk > 0 ? c->last_kernels : 0;
   return MDET_OK;
 }
 
@@ -1300,8 +1430,10 @@ mdet_status batch_enqueue(mdet_batch* b, const int64_t* n_walk, const double* co
   for (int i : order) {
     const int k = (int)(std::min_element(load.begin(), load.end()) - load.begin());
     load[k] += cost[i];
+    b->ctxs[i]->in_batch = true;
     mdet_status s = mdet_evaluate(b->ctxs[i], n_walk[i], R[i], log_abs_psi[i], sign[i], grad[i], lap[i],
                                   e_local ? e_local[i] : nullptr, status ? status[i] : nullptr, b->streams[k]);
+    b->ctxs[i]->in_batch = false;
     if (s != MDET_OK) return s;
   }
   for (int k = 0; k < ns; k++) {

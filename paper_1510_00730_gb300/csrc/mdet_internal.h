@@ -125,6 +125,8 @@ struct DevScratch {
   int* fb_list = nullptr;     // fallback: [1 + cap] count, then walker indices
   double* fb_acc = nullptr;   // fallback: [cap][3 + 8 MDET_FALLBACK_MAX_SPIN] scales, Psi, G
   unsigned long long* queue = nullptr;  // [2 * walker chunks] work counters of persistent contractions
+  const int* live = nullptr;  // device count of the walkers to evaluate (null: all n_walk); the FP64
+                              // kernels skip walkers at or beyond it (escalated re-evaluations)
   double* R_stage = nullptr;  // host-API staging buffers
   double* out_stage = nullptr;
 };
@@ -153,6 +155,28 @@ DevScratch scratch_view(const DevScratch& S, const DevProblem& P, int64_t off);
 // psit, for walker-minor arrays of leading dimension ld (a multiple of 128).
 cudaError_t launch_spmm_rows_f64(const DevProblem& P, const double* r_dn, const double* r_up, double* v,
                                  double* psit, int64_t ld, int64_t n_walk, cudaStream_t st);
+// Compact outputs of an escalated re-evaluation (slot i holds the i-th listed walker).
+struct EscOut {
+  double* log_abs_psi;  // [cap]
+  int8_t* sign;         // [cap]
+  double* grad;         // [cap][N][3]
+  double* lap;          // [cap][N]
+  double* e_local;      // [cap]
+  uint32_t* status;     // [cap]
+};
+// Lists the walkers whose status has MDET_WS_FALLBACK into list (count, then at
+// most P.fallback_cap indices); further ones lose the bit and get MDET_WS_REF_ILLCOND.
+cudaError_t launch_fb_list(const DevProblem& P, uint32_t* wstat, uint32_t* status, int64_t n_walk, int* list,
+                           cudaStream_t st);
+// Escalation of mixed-precision walkers: gather of the listed walkers' positions
+// (and *live = their count), and scatter of their FP64 results back.
+cudaError_t launch_esc_gather(const int* list, int cap, int n3, const double* R, double* Re, int* live,
+                              cudaStream_t st);
+// Marks the gathered walkers for full LU (wstat[i] = MDET_WS_FALLBACK, i < *live).
+cudaError_t launch_esc_mark(const int* live, uint32_t* wstat, int cap, cudaStream_t st);
+cudaError_t launch_esc_scatter(const int* list, int cap, int N, const EscOut& e, uint32_t or_bits,
+                               double* log_abs_psi, int8_t* sign, double* grad, double* lap, double* e_local,
+                               uint32_t* status, uint32_t* wstat, cudaStream_t st);
 cudaError_t launch_fallback(const DevProblem& P, const DevScratch& S, int64_t n_walk, const double* R,
                             double* log_abs_psi, int8_t* sign, double* grad, double* lap, double* e_local,
                             uint32_t* status, cudaStream_t st);
@@ -163,9 +187,10 @@ void ctx_set_error(mdet_ctx* ctx, const char* msg);
 cudaError_t launch_selftest_df(int64_t n, const double* x, double* y_df, double* y_ref, double* prod_df,
                                cudaStream_t st);
 size_t final_smem_bytes(const DevProblem& P, bool mixed);
+// wide: 512 threads per walker instead of 128 (FP64 only; lower latency for a few walkers)
 cudaError_t launch_final(const DevProblem& P, const DevScratch& S, int64_t n_walk, const double* R,
                          double* log_abs_psi, int8_t* sign, double* grad, double* lap, double* e_local,
-                         uint32_t* status, bool mixed, cudaStream_t st);
+                         uint32_t* status, bool mixed, cudaStream_t st, bool wide = false);
 
 // ---- expansion preprocessing on the GPU (mdet_preprocess.cu), Sec. 2.1 ----
 // Results of the O(N_det) steps for one spin: the distinct determinants in the

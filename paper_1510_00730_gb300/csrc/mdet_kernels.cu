@@ -52,10 +52,11 @@ namespace {
 // (Euler: x P_x + y P_y + z P_z = l P). Then Phi[c][e][m] = sum_mu X[c][e][mu] B[mu][m].
 template <int kEC>
 __global__ void __launch_bounds__(128) k_mo_f64(DevProblem P, double* __restrict__ phi,
-                                                const double* __restrict__ R) {
+                                                const double* __restrict__ R, const int* __restrict__ live) {
   extern __shared__ double smem[];
   const int K = P.n_ao, M = P.n_mo, N = P.n_elec;
   const int64_t w = blockIdx.x;
+  if (live && w >= *live) return;
   const int e_begin = blockIdx.y * kEC;
   const int ne = min(kEC, N - e_begin);
   double* X = smem;  // X[(c * kEC + e) * K + mu]
@@ -101,6 +102,7 @@ __global__ void __launch_bounds__(64) k_ref(DevProblem P, DevScratch S) {
   __shared__ int bad[2];
   __shared__ uint32_t stf[2];
   const int64_t w = blockIdx.x;
+  if (S.live && w >= *S.live) return;
   const int N = P.n_elec, M = P.n_mo;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   {
@@ -235,6 +237,7 @@ __global__ void __launch_bounds__(64) k_ref(DevProblem P, DevScratch S) {
 // block 128 = 4 warps; lanes are walkers, each warp takes 8 determinants.
 __global__ void __launch_bounds__(128) k_ratio_f64(DevProblem P, DevScratch S) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if (S.live && (int64_t)blockIdx.y * 32 >= *S.live) return;
   const int64_t w = (int64_t)blockIdx.y * 32 + lane;
   const int nu_det = P.n_det_sp[0], ntot = nu_det + P.n_det_sp[1];
   const int M = P.n_mo;
@@ -336,9 +339,11 @@ __global__ void __launch_bounds__(128) k_spmm_wm(const int* __restrict__ seg, co
                                                  const double* __restrict__ x, int64_t wp,
                                                  double* __restrict__ y, int64_t ldy, int seg_off,
                                                  const double* __restrict__ rdot, double* __restrict__ psit,
-                                                 float* __restrict__ psia, unsigned long long* __restrict__ queue) {
+                                                 float* __restrict__ psia, unsigned long long* __restrict__ queue,
+                                                 const int* __restrict__ live) {
   const int lane = threadIdx.x & 31;
-  const int64_t n_items = n_chunks * n_groups;
+  // walker groups at or beyond the live count (escalated re-evaluations) are skipped
+  const int64_t n_items = n_chunks * (live ? min(n_groups, (int64_t)(*live + 255) / 256) : n_groups);
   auto next_item = [&]() -> int64_t {
     unsigned long long t = 0;
     if (lane == 0) t = atomicAdd(queue, 1ULL);
@@ -492,8 +497,8 @@ __global__ void __launch_bounds__(128) k_spmm_df(const int* __restrict__ seg, co
 // smem, FP64: T[N][M], W[N][M], Q[N][M], A blocks, Pm.
 // smem, MIXED: W[N][M] (hi/lo FP32 pairs during the scatter, then the FP64 T
 //       for Pm), Q[N][M], A blocks, Pm, Tdf[N][M] (then W in FP64).
-template <bool MIXED>
-__global__ void __launch_bounds__(128) k_final(DevProblem P, DevScratch S, const double* __restrict__ R,
+template <bool MIXED, int NT>
+__global__ void __launch_bounds__(NT) k_final(DevProblem P, DevScratch S, const double* __restrict__ R,
                                                double* __restrict__ log_abs_psi, int8_t* __restrict__ sign,
                                                double* __restrict__ grad, double* __restrict__ lap,
                                                double* __restrict__ e_local, uint32_t* __restrict__ status) {
@@ -501,6 +506,7 @@ __global__ void __launch_bounds__(128) k_final(DevProblem P, DevScratch S, const
   const int nu = P.n_up, nd = P.n_dn, N = nu + nd, M = P.n_mo;
   const int NM = N * M;
   const int64_t w = blockIdx.x, wp = S.wp;
+  if (S.live && w >= *S.live) return;
   double* Ts = MIXED ? nullptr : sm;    // [N][M]; MIXED: loaded into the W space after the scatter
   double* Ws = MIXED ? sm : sm + NM;    // [N][M]
   double* Qs = Ws + NM;                 // [N][M]
@@ -509,7 +515,8 @@ __global__ void __launch_bounds__(128) k_final(DevProblem P, DevScratch S, const
   float2* Tdf = reinterpret_cast<float2*>(Pm + nu * nu + nd * nd);  // [N][M] (MIXED)
   float* Whi = reinterpret_cast<float*>(Ws);                          // MIXED: [N][M] hi words
   float* Wlo = Whi + NM;                                              //        [N][M] lo words
-  __shared__ double red[4];
+  constexpr int NW = NT / 32;  // warps per block
+  __shared__ double red[NW];
   __shared__ double Gs[kMaxSpin * 2][4];
   __shared__ float Ga[kMaxSpin * 2][4];
   __shared__ float G2[kMaxSpin * 2][4];
@@ -527,7 +534,7 @@ __global__ void __launch_bounds__(128) k_final(DevProblem P, DevScratch S, const
   for (int t = threadIdx.x; t < nu * nu + nd * nd; t += blockDim.x) As[t] = S.Ainv[w * (nu * nu + nd * nd) + t];
   __syncthreads();
   const int nu_det = P.n_det_sp[0], ntot = nu_det + P.n_det_sp[1];
-  // MIXED: determinant t = (q * stride) mod ntot for q = thread, thread + 128,
+  // MIXED: determinant t = (q * stride) mod ntot for q = thread, thread + NT,
   // ..., with a prime stride that does not divide ntot (a permutation): every
   // thread gets a mix of excitation degrees, so the double-float cofactor work
   // (k^2 per determinant) is balanced across the block. FP64: each thread walks
@@ -717,22 +724,28 @@ __global__ void __launch_bounds__(128) k_final(DevProblem P, DevScratch S, const
       e1 = fmaxf(e1, __shfl_xor_sync(0xffffffffu, e1, off));
       e2 = fmaxf(e2, __shfl_xor_sync(0xffffffffu, e2, off));
     }
-    __shared__ float wmax[2][4];
+    __shared__ float wmax[2][NW];
     if ((threadIdx.x & 31) == 0) {
       wmax[0][threadIdx.x >> 5] = e1;
       wmax[1][threadIdx.x >> 5] = e2;
     }
     __syncthreads();
     if (threadIdx.x == 0) {
-      estw[0][0] = fmaxf(fmaxf(wmax[0][0], wmax[0][1]), fmaxf(wmax[0][2], wmax[0][3]));
-      estw[1][0] = fmaxf(fmaxf(wmax[1][0], wmax[1][1]), fmaxf(wmax[1][2], wmax[1][3]));
+      float m0 = 0.0f, m1 = 0.0f;
+      for (int q = 0; q < NW; q++) {
+        m0 = fmaxf(m0, wmax[0][q]);
+        m1 = fmaxf(m1, wmax[1][q]);
+      }
+      estw[0][0] = m0;
+      estw[1][0] = m1;
     }
     __syncthreads();
   }
   if (threadIdx.x == 0) {
     double tl = 0.0;
     for (int i = 0; i < N; i++) tl += Gs[i][3];
-    const double vpot = red[0] + red[1] + red[2] + red[3];
+    double vpot = 0.0;
+    for (int q = 0; q < NW; q++) vpot += red[q];
     const double el = -0.5 * tl * inv + vpot;
     const double lg = ld + log(fabs(psit));
     const int s = (psit > 0.0) - (psit < 0.0);
@@ -765,7 +778,7 @@ static cudaError_t launch_mo_f64_ec(const DevProblem& P, const DevScratch& S, in
   cudaError_t e = opt.ensure(k_mo_f64<EC>, smem);
   if (e != cudaSuccess) return e;
   dim3 grid((unsigned)n_walk, (P.n_elec + EC - 1) / EC);
-  k_mo_f64<EC><<<grid, 128, smem, st>>>(P, S.phi, R);
+  k_mo_f64<EC><<<grid, 128, smem, st>>>(P, S.phi, R, S.live);
   return cudaGetLastError();
 }
 
@@ -838,13 +851,14 @@ cudaError_t launch_contract_f64(const DevProblem& P, const DevScratch& S, int64_
   // v = C r_dn (rows = up determinants) with Psi~ = r_up . v and its magnitude sum
   auto* kv = q ? k_spmm_wm<true, true> : k_spmm_wm<false, true>;
   kv<<<(unsigned)blocks, 128, 0, st>>>(P.csr_row, P.csr_col, P.csr_val, P.nnz, chunk, n_chunks, n_groups, r_dn, S.wp,
-                                       S.vu, ndt, 0, r_up, S.psit, S.psia, queue);
+                                       S.vu, ndt, 0, r_up, S.psit, S.psia, queue, S.live);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   // u = C^T r_up (columns = down determinants), in the paper's column-major order
   auto* ku = q ? k_spmm_wm<true, false> : k_spmm_wm<false, false>;
   ku<<<(unsigned)blocks, 128, 0, st>>>(P.csc_col, P.csc_row, P.csc_val, P.nnz, chunk, n_chunks, n_groups, r_up, S.wp,
-                                       S.vu, ndt, P.n_det_sp[0], nullptr, nullptr, nullptr, q ? queue + 1 : nullptr);
+                                       S.vu, ndt, P.n_det_sp[0], nullptr, nullptr, nullptr, q ? queue + 1 : nullptr,
+                                       S.live);
   return cudaGetLastError();
 }
 
@@ -889,13 +903,16 @@ size_t final_smem_bytes(const DevProblem& P, bool mixed) {
 
 cudaError_t launch_final(const DevProblem& P, const DevScratch& S, int64_t n_walk, const double* R,
                          double* log_abs_psi, int8_t* sign, double* grad, double* lap, double* e_local,
-                         uint32_t* status, bool mixed, cudaStream_t st) {
+                         uint32_t* status, bool mixed, cudaStream_t st, bool wide) {
   const size_t smem = final_smem_bytes(P, mixed);
-  auto kern = mixed ? k_final<true> : k_final<false>;
-  static SmemOptIn opt[2];  // dynamic shared memory per variant (static arrays come on top)
-  cudaError_t e = opt[mixed].ensure(kern, smem);
+  // wide: 512 threads per walker (FP64 only), for a few walkers whose latency matters
+  const int variant = mixed ? 1 : (wide ? 2 : 0);
+  auto kern = variant == 1 ? k_final<true, 128> : (variant == 2 ? k_final<false, 512> : k_final<false, 128>);
+  const int nt = variant == 2 ? 512 : 128;
+  static SmemOptIn opt[3];  // dynamic shared memory per variant (static arrays come on top)
+  cudaError_t e = opt[variant].ensure(kern, smem);
   if (e != cudaSuccess) return e;
-  kern<<<(unsigned)n_walk, 128, smem, st>>>(P, S, R, log_abs_psi, sign, grad, lap, e_local, status);
+  kern<<<(unsigned)n_walk, nt, smem, st>>>(P, S, R, log_abs_psi, sign, grad, lap, e_local, status);
   return cudaGetLastError();
 }
 

@@ -21,18 +21,29 @@ def _eval(ctx, R):
     return {k: v.cpu().numpy() for k, v in out.items()}
 
 
-@pytest.mark.parametrize("prec", [pkg.PRECISION_FP64, pkg.PRECISION_MIXED])
-def test_forced_fallback_for_every_walker_matches_oracle(prec):
-    """With a tiny tolerance every walker goes through the full-LU path; at most
-    `cap` of them are re-evaluated, the rest keep the table result and are flagged."""
+ESC = pkg.Context.ESCALATE_ALWAYS
+NO_ESC = pkg.Context.ESCALATE_NEVER
+MODES = [(pkg.PRECISION_FP64, None), (pkg.PRECISION_MIXED, NO_ESC), (pkg.PRECISION_MIXED, ESC)]
+
+
+@pytest.mark.parametrize("prec,mode", MODES)
+def test_forced_fallback_for_every_walker_matches_oracle(prec, mode):
+    """With a tiny tolerance every walker goes through the full-LU path (mixed:
+    directly, or after the FP64 re-evaluation); at most `cap` of them are
+    re-evaluated, the rest keep the table result and are flagged."""
     wl = synth.oxygen_like_1k(n_walk=40, seed=31)
     ref = oracle.evaluate(wl)
     ctx = pkg.Context.from_workload(wl, device=0, precision=prec)
+    if mode is not None:
+        ctx.set_escalation(mode)
     ctx.set_fallback(1e-30, max_walkers=32)
     got = _eval(ctx, wl.R)
     fb = (got["status"] & pkg.WS_FALLBACK) != 0
     assert fb.sum() == 32
     assert np.all(got["status"][~fb] & pkg.WS_REF_ILLCOND)
+    # with escalation the full-LU path is reached through the FP64 re-evaluation
+    esc = (got["status"] & pkg.WS_ESCALATED) != 0
+    assert np.array_equal(esc, fb) if mode == ESC else not esc.any()
     rep = compare(got, ref, tol_psi=1e-10, tol_der=1e-8) if prec == pkg.PRECISION_FP64 else \
         compare(got, ref, tol_psi=1e-9, tol_der=1e-6)
     assert rep["ok"], rep
@@ -122,18 +133,26 @@ def test_error_estimate_bounds_the_error(o2100_fb, prec):
     ctx.close()
 
 
-@pytest.mark.parametrize("prec", [pkg.PRECISION_FP64, pkg.PRECISION_MIXED])
-def test_default_tolerance_meets_each_path_target(o2100_fb, prec):
+@pytest.mark.parametrize("prec,mode", MODES)
+def test_default_tolerance_meets_each_path_target(o2100_fb, prec, mode):
     """With the default fallback (1e-8 FP64, 1e-5 mixed) every walker of the
     2,100-walker set is within its path's target of the oracle: the ones the
-    estimate flags are re-evaluated by LU, the others are bounded by it."""
+    estimate flags are re-evaluated (mixed: by full LU, or by the FP64 table and
+    then full LU for those still above the tolerance), the others are bounded by it."""
     wl, ref = o2100_fb
     ctx = pkg.Context.from_workload(wl, device=0, precision=prec)
+    if mode is not None:
+        ctx.set_escalation(mode)
     tol, cap = ctx.fallback
     assert tol == (1e-8 if prec == pkg.PRECISION_FP64 else 1e-5)
     got = _eval(ctx, wl.R)
     fb = (got["status"] & pkg.WS_FALLBACK) != 0
+    esc = (got["status"] & pkg.WS_ESCALATED) != 0
     assert 0 < fb.sum() <= cap
+    if mode == ESC:  # escalation resolves some walkers before the full-LU path
+        assert esc.sum() > fb.sum() and not (fb & ~esc).any()
+    else:
+        assert not esc.any()
     err = _walker_errors(got, ref)
     assert err[~fb].max() <= tol, (int(np.flatnonzero(~fb)[np.argmax(err[~fb])]), err[~fb].max())
     # the re-evaluated walkers: the FP64 LU result, at the FP64 tolerances of the parity tests
@@ -141,4 +160,36 @@ def test_default_tolerance_meets_each_path_target(o2100_fb, prec):
     rep = compare({k: v[idx] for k, v in got.items()}, {k: np.asarray(v)[idx] for k, v in ref.items()},
                   tol_psi=1e-10, tol_der=1e-8)
     assert rep["ok"], rep
+    ctx.close()
+
+
+def test_escalated_walkers_carry_fp64_table_results(o2100_fb):
+    """Mixed walkers re-evaluated by the FP64 ratio table (and not by full LU)
+    agree with an FP64 context's table result for the same walkers within the
+    two FP64 estimates; without flagged walkers nothing is escalated."""
+    wl, ref = o2100_fb
+    mixed = pkg.Context.from_workload(wl, device=0, precision=pkg.PRECISION_MIXED)
+    mixed.set_escalation(ESC)
+    got = _eval(mixed, wl.R)
+    only = ((got["status"] & pkg.WS_ESCALATED) != 0) & ((got["status"] & pkg.WS_FALLBACK) == 0)
+    assert only.any()
+    fp64 = pkg.Context.from_workload(wl, device=0, precision=pkg.PRECISION_FP64)
+    fp64.set_fallback(1e30, 1)  # table results with their estimates, nothing re-evaluated
+    want = _eval(fp64, wl.R)
+    _, est = fp64.error_estimates(wl.n_walk)
+    d = _walker_errors({k: v[only] for k, v in got.items()}, {k: v[only] for k, v in want.items()})
+    assert np.all(d <= 2 * est[only, 0] + 1e-13), (d.max(), est[only, 0])
+    mixed.set_fallback(1e30, 256)  # estimates only: no walker exceeds the tolerance
+    got2 = _eval(mixed, wl.R)
+    assert not (got2["status"] & (pkg.WS_ESCALATED | pkg.WS_FALLBACK)).any()
+    mixed.close()
+    fp64.close()
+
+
+def test_escalation_mode_is_validated():
+    wl = synth.oxygen_like_1k(n_walk=8)
+    ctx = pkg.Context.from_workload(wl, device=0, precision=pkg.PRECISION_MIXED)
+    with pytest.raises(pkg.MdetError):
+        ctx.set_escalation(3)
+    ctx.set_escalation(pkg.Context.ESCALATE_AUTO)
     ctx.close()
