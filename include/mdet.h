@@ -271,7 +271,8 @@ mdet_status mdet_truncate_norm(int64_t n_det, int n_int, const uint64_t* det_up,
 /*
  * Escalation of flagged mixed-precision walkers to the FP64 ratio table before
  * the full-LU path: MDET_ESCALATE_AUTO (default) takes it when full LU is the
- * costlier (distinct determinants x n^3 above 8e6, n the larger spin count),
+ * costlier (distinct determinants x n^3 above 1e6, n the larger spin count, or
+ * inside a batch),
  * MDET_ESCALATE_ALWAYS and MDET_ESCALATE_NEVER force the choice. Escalated
  * walkers get MDET_WS_ESCALATED. No effect on FP64 contexts.
  */

@@ -494,19 +494,20 @@ mdet_status alloc_fallback(mdet_ctx* c, DevScratch& S) {
 
 // Whether mixed precision re-evaluates its flagged walkers by the FP64 ratio
 // table before the full-LU path (MDET_ESCALATE_AUTO: when it pays). The
-// escalation costs a fixed latency of about 0.5-2 ms (a dozen dependent launches
-// over up to a few hundred walkers) and a few microseconds per walker; full LU
-// costs about 5-7 ns per (distinct determinant x n^3), n the larger spin count:
-// 24 us per walker for 6,030 determinants of 9 electrons, 320 us for the largest
-// 17-electron expansions. Alone on the GPU the two tie at about 4e6 units per
-// walker with ~100 flagged walkers, so escalation is taken above 8e6; in a batch
-// the other expansions' kernels hide its latency, and it is always taken.
+// escalation costs a fixed latency (a dozen dependent launches over up to a few
+// hundred walkers) and a few microseconds per walker; full LU costs about 5-7 ns
+// per (distinct determinant x n^3) and walker, n the larger spin count: 30 us for
+// 6,030 determinants of 9 electrons, 320 us for the largest 17-electron
+// expansions. Measured with ~100 flagged walkers, the two tie at about 1.3e6
+// units per walker (1,800 determinants of 9 electrons) and escalation saves
+// 1.2 ms at 4.4e6 (6,030), so it is taken above 1e6; in a batch the other
+// expansions' kernels hide its latency, and it is always taken.
 bool escalation_on(const mdet_ctx* c) {
   if (c->escalate != MDET_ESCALATE_AUTO) return c->escalate == MDET_ESCALATE_ALWAYS;
   if (c->in_batch) return true;
   const double ndt = (double)c->P.n_det_sp[0] + c->P.n_det_sp[1];
   const double n = std::max(c->P.n_up, c->P.n_dn);
-  return ndt * n * n * n > 8e6;
+  return ndt * n * n * n > 1e6;
 }
 
 mdet_status ensure_scratch(mdet_ctx* c, int64_t n_walk) {
@@ -553,7 +554,9 @@ mdet_status refine(mdet_ctx* c, bool table, int64_t n_walk, const double* R, dou
   CUDA_TRY(c, launch_fb_list(P, S.wstat, status, n_walk, S.fb_list, st));
   CUDA_TRY(c, cudaMemsetAsync(E.wstat, 0, sizeof(uint32_t) * cap, st));
   CUDA_TRY(c, launch_esc_gather(S.fb_list, cap, 3 * N, R, c->e_R, c->e_live, st));
-  CUDA_TRY(c, launch_mo_f64(P, E, cap, c->e_R, st));
+  DevProblem Pe = P;  // the FP64 orbital kernel's own best electron block
+  Pe.mo_ec = 6;
+  CUDA_TRY(c, launch_mo_f64(Pe, E, cap, c->e_R, st));
   const EscOut& o = c->eo;
   if (!table) {
     CUDA_TRY(c, launch_esc_mark(c->e_live, E.wstat, cap, st));
@@ -567,7 +570,6 @@ mdet_status refine(mdet_ctx* c, bool table, int64_t n_walk, const double* R, dou
   CUDA_TRY(c, launch_zero_f64(P, E, cap, st));
   // few walkers: short work items (64 nonzeros) keep the contraction's chains short, and the
   // epilogue spreads each walker's determinants over 512 threads
-  DevProblem Pe = P;
   Pe.spmm_chunk = 64;
   Pe.spmm_blocks = 0;
   CUDA_TRY(c, launch_contract_f64(Pe, E, cap, st));

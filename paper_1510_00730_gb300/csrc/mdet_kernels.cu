@@ -332,7 +332,9 @@ __device__ __forceinline__ float abs_f32_of(double x) {
 // ABS (with rdot): psia[w] += |rdot[seg][w]| * sum |c| |x| in FP32, so that
 // psia = sum_ij |c_ij| |r_up,i| |r_dn,j|, the magnitude sum behind Psi~ (its
 // ratio to |Psi~| is the conditioning of the CI sum, used by the error estimate).
-template <bool QUEUE, bool ABS>
+// WPL walkers per lane (8, or 4 for the few walkers of an escalated re-evaluation,
+// where a 256-walker group would be mostly padding).
+template <bool QUEUE, bool ABS, int WPL>
 __global__ void __launch_bounds__(128) k_spmm_wm(const int* __restrict__ seg, const int* __restrict__ gidx,
                                                  const double* __restrict__ val, int64_t nnz, int chunk,
                                                  int64_t n_chunks, int64_t n_groups,
@@ -341,9 +343,10 @@ __global__ void __launch_bounds__(128) k_spmm_wm(const int* __restrict__ seg, co
                                                  const double* __restrict__ rdot, double* __restrict__ psit,
                                                  float* __restrict__ psia, unsigned long long* __restrict__ queue,
                                                  const int* __restrict__ live) {
+  constexpr int G = 32 * WPL;  // walkers per work item
   const int lane = threadIdx.x & 31;
   // walker groups at or beyond the live count (escalated re-evaluations) are skipped
-  const int64_t n_items = n_chunks * (live ? min(n_groups, (int64_t)(*live + 255) / 256) : n_groups);
+  const int64_t n_items = n_chunks * (live ? min(n_groups, (int64_t)(*live + G - 1) / G) : n_groups);
   auto next_item = [&]() -> int64_t {
     unsigned long long t = 0;
     if (lane == 0) t = atomicAdd(queue, 1ULL);
@@ -353,22 +356,22 @@ __global__ void __launch_bounds__(128) k_spmm_wm(const int* __restrict__ seg, co
   for (int64_t item = first; item < n_items; item = QUEUE ? next_item() : n_items) {
     const int64_t ch = item % n_chunks, grp = item / n_chunks;
     const int64_t k0 = ch * chunk, k1 = min(k0 + (int64_t)chunk, nnz);
-    const int64_t wb = grp * 256 + lane * 8;
-    double a[8];
-    float aa[8];  // ABS: sum |c| |x| of the segment
+    const int64_t wb = grp * G + lane * WPL;
+    double a[WPL];
+    float aa[WPL];  // ABS: sum |c| |x| of the segment
 #pragma unroll
-    for (int j = 0; j < 8; j++) {
+    for (int j = 0; j < WPL; j++) {
       a[j] = 0.0;
       aa[j] = 0.0f;
     }
     int cur = __ldg(seg + k0);
     auto flush = [&](int sg) {
 #pragma unroll
-      for (int j = 0; j < 8; j++) atomicAdd(y + (wb + j) * ldy + seg_off + sg, a[j]);
+      for (int j = 0; j < WPL; j++) atomicAdd(y + (wb + j) * ldy + seg_off + sg, a[j]);
       if (rdot) {
         const double* rp = rdot + (size_t)sg * wp + wb;
 #pragma unroll
-        for (int j = 0; j < 8; j++) {
+        for (int j = 0; j < WPL; j++) {
           atomicAdd(psit + wb + j, rp[j] * a[j]);
           if (ABS) atomicAdd(psia + wb + j, abs_f32_of(rp[j]) * aa[j]);
         }
@@ -380,32 +383,26 @@ __global__ void __launch_bounds__(128) k_spmm_wm(const int* __restrict__ seg, co
         flush(cur);
         cur = sg;
 #pragma unroll
-        for (int j = 0; j < 8; j++) {
+        for (int j = 0; j < WPL; j++) {
           a[j] = 0.0;
           aa[j] = 0.0f;
         }
       }
       const double c = __ldg(val + k);
       const double2* xp = reinterpret_cast<const double2*>(x + (size_t)__ldg(gidx + k) * wp + wb);
-      const double2 x0 = __ldg(xp), x1 = __ldg(xp + 1), x2 = __ldg(xp + 2), x3 = __ldg(xp + 3);
-      a[0] = fma(c, x0.x, a[0]);
-      a[1] = fma(c, x0.y, a[1]);
-      a[2] = fma(c, x1.x, a[2]);
-      a[3] = fma(c, x1.y, a[3]);
-      a[4] = fma(c, x2.x, a[4]);
-      a[5] = fma(c, x2.y, a[5]);
-      a[6] = fma(c, x3.x, a[6]);
-      a[7] = fma(c, x3.y, a[7]);
+      double xv[WPL];
+#pragma unroll
+      for (int h = 0; h < WPL / 2; h++) {
+        const double2 t = __ldg(xp + h);
+        xv[2 * h] = t.x;
+        xv[2 * h + 1] = t.y;
+      }
+#pragma unroll
+      for (int j = 0; j < WPL; j++) a[j] = fma(c, xv[j], a[j]);
       if (ABS) {
         const float ca = abs_f32_of(c);
-        aa[0] = fmaf(ca, abs_f32_of(x0.x), aa[0]);
-        aa[1] = fmaf(ca, abs_f32_of(x0.y), aa[1]);
-        aa[2] = fmaf(ca, abs_f32_of(x1.x), aa[2]);
-        aa[3] = fmaf(ca, abs_f32_of(x1.y), aa[3]);
-        aa[4] = fmaf(ca, abs_f32_of(x2.x), aa[4]);
-        aa[5] = fmaf(ca, abs_f32_of(x2.y), aa[5]);
-        aa[6] = fmaf(ca, abs_f32_of(x3.x), aa[6]);
-        aa[7] = fmaf(ca, abs_f32_of(x3.y), aa[7]);
+#pragma unroll
+        for (int j = 0; j < WPL; j++) aa[j] = fmaf(ca, abs_f32_of(xv[j]), aa[j]);
       }
     }
     flush(cur);
@@ -821,7 +818,9 @@ cudaError_t launch_contract_f64(const DevProblem& P, const DevScratch& S, int64_
                                 unsigned long long* queue, int persistent_blocks) {
   const int chunk = P.spmm_chunk > 0 ? P.spmm_chunk : 512;
   const int64_t n_chunks = (P.nnz + chunk - 1) / chunk;
-  const int64_t n_groups = (n_walk + 255) / 256;
+  // an escalated re-evaluation (few walkers, live count on the device) uses 4 walkers per lane
+  const bool narrow = S.live != nullptr && !(P.contract_impl == 1 && S.rdf && P.csr_val_df);
+  const int64_t n_groups = narrow ? (n_walk + 127) / 128 : (n_walk + 255) / 256;
   const int64_t items = n_chunks * n_groups;
   // one work item per warp (full occupancy hides the L2 latency of the gathers), or a
   // persistent grid whose warps draw items from a queue (two counters, one per launch)
@@ -849,13 +848,13 @@ cudaError_t launch_contract_f64(const DevProblem& P, const DevScratch& S, int64_
     return cudaGetLastError();
   }
   // v = C r_dn (rows = up determinants) with Psi~ = r_up . v and its magnitude sum
-  auto* kv = q ? k_spmm_wm<true, true> : k_spmm_wm<false, true>;
+  auto* kv = narrow ? k_spmm_wm<false, true, 4> : (q ? k_spmm_wm<true, true, 8> : k_spmm_wm<false, true, 8>);
   kv<<<(unsigned)blocks, 128, 0, st>>>(P.csr_row, P.csr_col, P.csr_val, P.nnz, chunk, n_chunks, n_groups, r_dn, S.wp,
                                        S.vu, ndt, 0, r_up, S.psit, S.psia, queue, S.live);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   // u = C^T r_up (columns = down determinants), in the paper's column-major order
-  auto* ku = q ? k_spmm_wm<true, false> : k_spmm_wm<false, false>;
+  auto* ku = narrow ? k_spmm_wm<false, false, 4> : (q ? k_spmm_wm<true, false, 8> : k_spmm_wm<false, false, 8>);
   ku<<<(unsigned)blocks, 128, 0, st>>>(P.csc_col, P.csc_row, P.csc_val, P.nnz, chunk, n_chunks, n_groups, r_up, S.wp,
                                        S.vu, ndt, P.n_det_sp[0], nullptr, nullptr, nullptr, q ? queue + 1 : nullptr,
                                        S.live);

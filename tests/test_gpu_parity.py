@@ -155,7 +155,8 @@ def test_persistent_contraction_grids(o2100, prec, chunks, blocks):
     rep = compare(_gpu_eval(ctx, wl.R), ref, **TOL[prec])
     assert rep["ok"], rep
     assert ctx.last_chunks == chunks
-    # 6 kernels per chunk; the fallback: FP64 full LU 5, mixed refinement (no escalation here) 10
+    # 6 kernels per chunk; the fallback: FP64 full LU 5, mixed refinement (no escalation for
+    # this small expansion) 10
     assert ctx.last_kernels == 6 * chunks + (5 if prec == pkg.PRECISION_FP64 else 10)
     prof = ctx.profile()
     assert all(v > 0 for k, v in prof.items() if k != "zero"), prof
