@@ -30,7 +30,7 @@ CPU_SAMPLE_WALKERS = 96     # bounded oracle sample for the CPU baseline (~10-30
 # dram__bytes_read.sum + dram__bytes_write.sum of the average k_spmm_wm launch on the 750k workload
 # with 8,192 walkers, by the number of walker chunks (ncu captures summarised in
 # profiles/mixed_chlorine_like_750k.md); null for a chunking that was not captured
-SPMM_TRAFFIC_750K = {1: 746.8e6, 3: 227.9e6}
+SPMM_TRAFFIC_750K = {1: 746.8e6, 3: 227.8e6}
 
 
 def _env_int(k, d):

@@ -1014,8 +1014,16 @@ mdet_status mdet_evaluate(mdet_ctx* c, int64_t n_walk, const double* R, double* 
       for (int i = 0; i < mdet_ctx::kEvPerChunk; i++)
         if (!c->ev[k][i]) CUDA_TRY(c, cudaEventCreate(&c->ev[k][i]));
   const int64_t N = P.n_elec;
+  // chunk k covers tiles [t0, t1): an even split, except that with three chunks the first and
+  // last take a quarter each (their orbitals and tables, and the last epilogue, run alone, so
+  // shorter end chunks expose less: 32.9 against 33.5 ms per step at 8,192 walkers)
   auto chunk_range = [&](int k, int64_t* off, int64_t* n) {
-    const int64_t t0 = tiles * k / nch, t1 = tiles * (k + 1) / nch;
+    int64_t t0 = tiles * k / nch, t1 = tiles * (k + 1) / nch;
+    if (nch == 3 && tiles >= 4) {
+      const int64_t b[4] = {0, tiles / 4, tiles - tiles / 4, tiles};
+      t0 = b[k];
+      t1 = b[k + 1];
+    }
     *off = t0 * kWalkerPad;
     *n = std::min<int64_t>(t1 * kWalkerPad, n_walk) - *off;
   };
