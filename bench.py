@@ -244,6 +244,8 @@ def run_ours(args):
 
     for pname in [primary] + others:
         ctx = pkg.Context.from_workload(wl, device=local, precision=prec_of[pname])
+        if args.fallback_tol is not None and pname == primary:
+            ctx.set_fallback(args.fallback_tol)
         if args.chunks is not None:
             ctx.set_walker_chunks(args.chunks)
         ctxs[pname] = ctx
@@ -368,6 +370,9 @@ def run_batched(args):
     prec = {"mixed": pkg.PRECISION_MIXED, "fp64": pkg.PRECISION_FP64}[args.precision]
     wls = synth.batched_uneven()
     ctxs = [pkg.Context.from_workload(wl, device=0, precision=prec) for wl in wls]
+    if args.fallback_tol is not None:
+        for c in ctxs:
+            c.set_fallback(args.fallback_tol)
     Rs = [torch.from_numpy(wl.R).to(dev) for wl in wls]
     t0 = time.perf_counter()
     tunes = [c.autotune(R, budget_ms=args.tune_ms) for c, R in zip(ctxs, Rs)]
@@ -406,6 +411,7 @@ def run_batched(args):
             "data": "synthetic",
             "config": {"workload": "batched_uneven_64", "precision": args.precision, "walkers_total": W,
                        "n_det_total": int(sum(wl.n_det for wl in wls)), "streams": args.streams,
+                       "fallback_tol": ctxs[0].fallback[0],
                        "autotune_s": tune_s, "l2": "flushed between timed steps"},
             "sum_of_solo_ms": solo, "batch_gain": solo / ms,
             "tuning_histogram": {k: dict(zip(*np.unique([t[k] for t in tunes], return_counts=True)))
@@ -623,6 +629,8 @@ def main():
                    help="skip timing the other precision in the same run")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--chunks", type=int, default=None, help="walker chunks of the mixed path (default: library's)")
+    p.add_argument("--fallback-tol", type=float, default=None,
+                   help="fallback tolerance of the timed contexts (default: the library's, 1e-5 mixed, 1e-8 FP64)")
     p.add_argument("--streams", type=int, default=8, help="streams of the batched workload")
     p.add_argument("--tune-ms", type=float, default=60.0, help="autotuner budget per expansion (batched workload)")
     p.add_argument("--ref-sample", type=int, default=32)
