@@ -39,6 +39,22 @@ static __device__ __forceinline__ df32 df_from_double(double x) {
   return {h, __double2float_rn(x - (double)h)};
 }
 
+// The same split from the bits of x with integer and FP32 instructions only:
+// hi keeps the sign, the exponent and the 23 leading mantissa bits (truncated),
+// lo the 29 remaining bits (rounded to FP32, so hi + lo = x (1 + d), |d| <= 2^-47).
+// Outside 2^-74 <= |x| < 2^128 (and for Inf or NaN) it falls back to the
+// conversions above.
+static __device__ __forceinline__ df32 df_from_bits(long long b) {
+  const unsigned hw = (unsigned)((unsigned long long)b >> 32), lw = (unsigned)b;
+  const int fe = (int)((hw >> 20) & 0x7ff) - 896;  // FP32 biased exponent of x
+  if (fe < 53 || fe > 254) return df_from_double(__longlong_as_double(b));
+  const unsigned sign = hw & 0x80000000u;
+  const float hi = __uint_as_float(sign | ((unsigned)fe << 23) | ((hw & 0xfffffu) << 3) | (lw >> 29));
+  // lo = (lw mod 2^29) 2^(e - 1075), e the FP64 biased exponent: 2^(fe - 179) as an FP32 scale
+  const float lo = __uint2float_rn(lw & 0x1fffffffu) * __uint_as_float((unsigned)(fe - 52) << 23);
+  return {hi, __uint_as_float(__float_as_uint(lo) | sign)};
+}
+
 static __device__ __forceinline__ double df_to_double(df32 a) { return (double)a.hi + (double)a.lo; }
 
 static __device__ __forceinline__ df32 operator+(df32 x, df32 y) {

@@ -377,11 +377,14 @@ cudaError_t launch_fallback(const DevProblem& P, const DevScratch& S, int64_t n_
   if (e != cudaSuccess) return e;
   const int nmax = P.n_up > P.n_dn ? P.n_up : P.n_dn;
   const int ntot = P.n_det_sp[0] + P.n_det_sp[1];
-  const size_t smem = sizeof(double) * 64 * nmax * nmax;
+  // one thread per determinant, its Slater matrix in shared memory: 32-thread blocks from 12
+  // electrons per spin up, so that three blocks (96 threads) fit an SM at 17 instead of one of 64
+  const int tpb = nmax >= 12 ? 32 : 64;
+  const size_t smem = sizeof(double) * tpb * nmax * nmax;
   static SmemOptIn opt;
   if ((e = opt.ensure(k_fb_dets, smem)) != cudaSuccess) return e;
-  dim3 g1((ntot + 63) / 64, P.fallback_cap);
-  k_fb_dets<<<g1, 64, smem, st>>>(P, S);
+  dim3 g1((ntot + tpb - 1) / tpb, P.fallback_cap);
+  k_fb_dets<<<g1, tpb, smem, st>>>(P, S);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   k_fb_scale<<<P.fallback_cap, 256, 0, st>>>(P, S);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;

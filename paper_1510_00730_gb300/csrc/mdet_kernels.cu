@@ -543,13 +543,23 @@ __global__ void __launch_bounds__(NT) k_final(DevProblem P, DevScratch S, const 
   const int tid = threadIdx.x, nth = blockDim.x;
   const int per = (ntot + nth - 1) / nth;
   const int n_mine = MIXED ? (ntot - tid + nth - 1) / nth : max(0, min(per, ntot - tid * per));
+  // MIXED: t_j = (tid + j nth) stride mod ntot, advanced by (nth stride) mod ntot per step
+  const int step = (int)(((int64_t)nth * stride) % ntot);
+  int tq = (int)(((int64_t)tid * stride) % ntot);
   for (int j = 0; j < n_mine; j++) {
-    const int t = MIXED ? (int)(((int64_t)(tid + j * nth) * stride) % ntot) : tid * per + j;
+    const int t = MIXED ? tq : tid * per + j;
+    if (MIXED) {
+      tq += step;
+      if (tq >= ntot) tq -= ntot;
+    }
     const int sp = t < nu_det ? 0 : 1;
     const Exc e = P.exc[sp][sp ? t - nu_det : t];
     if (e.k == 0) continue;
-    const double wgt = (e.eps < 0 ? -1.0 : 1.0) * S.vu[w * ntot + t];
-    if (wgt == 0.0) continue;
+    // the weight eps_I w_I: sign and zero test on the bits (no FP64 instructions)
+    long long wb = __double_as_longlong(S.vu[w * ntot + t]);
+    if ((wb & 0x7fffffffffffffffLL) == 0) continue;
+    if (e.eps < 0) wb ^= (long long)(1ULL << 63);
+    const double wgt = __longlong_as_double(wb);
     const int off = sp ? nu * M : 0;
     if (MIXED) {
       df32 m[4][4], cof[4][4];
@@ -561,7 +571,7 @@ __global__ void __launch_bounds__(NT) k_final(DevProblem P, DevScratch S, const 
           m[a][b] = df32(v.x, v.y);
         }
       small_cof(e.k, m, cof);
-      const df32 wd = df_from_double(wgt);
+      const df32 wd = df_from_bits(wb);
 #pragma unroll
       for (int a = 0; a < 4; a++)
 #pragma unroll
