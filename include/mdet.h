@@ -239,7 +239,10 @@ mdet_status mdet_get_ratios(mdet_ctx* ctx, int64_t n_walk, double* r_up, double*
  * At most max_walkers walkers per evaluation are re-evaluated (default 256 for
  * mixed, 512 for FP64; the scratch grows with it); further ones keep the table
  * result and MDET_WS_REF_ILLCOND. tol <= 0 disables the fallback. Supported for
- * n_up, n_dn <= MDET_FALLBACK_MAX_SPIN.
+ * n_up, n_dn <= MDET_FALLBACK_MAX_SPIN. The re-evaluation runs on the stream of
+ * mdet_evaluate after the walker chunks, with no host wait. Errors: MDET_E_ARG
+ * for a null context or max_walkers outside 1..65535. A new cap frees the
+ * scratch, which the next evaluation allocates again.
  */
 #define MDET_FALLBACK_MAX_SPIN 17
 mdet_status mdet_set_fallback(mdet_ctx* ctx, double tol, int max_walkers);
@@ -272,9 +275,11 @@ mdet_status mdet_truncate_norm(int64_t n_det, int n_int, const uint64_t* det_up,
  * Escalation of flagged mixed-precision walkers to the FP64 ratio table before
  * the full-LU path: MDET_ESCALATE_AUTO (default) takes it when full LU is the
  * costlier (distinct determinants x n^3 above 1e6, n the larger spin count, or
- * inside a batch),
- * MDET_ESCALATE_ALWAYS and MDET_ESCALATE_NEVER force the choice. Escalated
- * walkers get MDET_WS_ESCALATED. No effect on FP64 contexts.
+ * inside a batch); MDET_ESCALATE_ALWAYS and MDET_ESCALATE_NEVER force the
+ * choice. Escalated walkers get MDET_WS_ESCALATED. No effect on FP64 contexts.
+ * The choice is made when an evaluation is enqueued (a captured batch keeps the
+ * one it was captured with). Errors: MDET_E_ARG for a null context or another
+ * mode.
  */
 #define MDET_ESCALATE_AUTO 0
 #define MDET_ESCALATE_ALWAYS 1
