@@ -369,8 +369,8 @@ mdet_status mdet_autotune(mdet_ctx* ctx, int64_t n_walk, const double* R, double
  * mdet_batch_launch replays all evaluations as one graph launch on `stream`.
  * The pointers given to mdet_batch_create are baked into the graph: refill the
  * same R buffers between launches. A batch must be destroyed before its
- * contexts, and a context's tuning or size must not change while a batch
- * refers to it.
+ * contexts, and a context's tuning, fallback cap or size must not change while
+ * a batch refers to it (each may reallocate the scratch the graph points to).
  */
 typedef struct mdet_batch mdet_batch;
 mdet_status mdet_batch_evaluate(int n_ctx, mdet_ctx* const* ctxs, const int64_t* n_walk, const double* const* R,
