@@ -297,15 +297,19 @@ __global__ void __launch_bounds__(64) k_fb_out(DevProblem P, DevScratch S, const
 }
 
 // Escalation: the listed walkers (count, then indices; at most cap) are copied to
-// the front of Re, and *live receives min(count, cap) for the FP64 kernels.
+// the front of Re with their magnitude sums sum |c r r| (psia, from the evaluation
+// that flagged them: the conditioning of the CI sum needs no FP64 recomputation),
+// and *live receives min(count, cap) for the FP64 kernels.
 __global__ void k_esc_gather(const int* __restrict__ list, int cap, int n3, const double* __restrict__ R,
-                             double* __restrict__ Re, int* __restrict__ live) {
+                             double* __restrict__ Re, int* __restrict__ live, const float* __restrict__ psia,
+                             float* __restrict__ psia_e) {
   const int count = min(list[0], cap);
   if (blockIdx.x == 0 && threadIdx.x == 0) *live = count;
   for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < (int64_t)count * n3;
        t += (int64_t)gridDim.x * blockDim.x) {
     const int64_t i = t / n3, q = t - i * n3;
     Re[t] = R[(int64_t)list[1 + i] * n3 + q];
+    if (q == 0) psia_e[i] = psia[list[1 + i]];
   }
 }
 
@@ -349,10 +353,10 @@ cudaError_t launch_fb_list(const DevProblem& P, uint32_t* wstat, uint32_t* statu
 }
 
 cudaError_t launch_esc_gather(const int* list, int cap, int n3, const double* R, double* Re, int* live,
-                              cudaStream_t st) {
+                              const float* psia, float* psia_e, cudaStream_t st) {
   const int64_t total = (int64_t)cap * n3;
   k_esc_gather<<<(unsigned)std::max<int64_t>(1, std::min<int64_t>((total + 255) / 256, 1024)), 256, 0, st>>>(
-      list, cap, n3, R, Re, live);
+      list, cap, n3, R, Re, live, psia, psia_e);
   return cudaGetLastError();
 }
 

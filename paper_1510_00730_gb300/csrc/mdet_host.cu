@@ -553,7 +553,7 @@ mdet_status refine(mdet_ctx* c, bool table, int64_t n_walk, const double* R, dou
   const int N = P.n_elec;
   CUDA_TRY(c, launch_fb_list(P, S.wstat, status, n_walk, S.fb_list, st));
   CUDA_TRY(c, cudaMemsetAsync(E.wstat, 0, sizeof(uint32_t) * cap, st));
-  CUDA_TRY(c, launch_esc_gather(S.fb_list, cap, 3 * N, R, c->e_R, c->e_live, st));
+  CUDA_TRY(c, launch_esc_gather(S.fb_list, cap, 3 * N, R, c->e_R, c->e_live, S.psia, E.psia, st));
   DevProblem Pe = P;  // the FP64 orbital kernel's own best electron block
   Pe.mo_ec = 6;
   CUDA_TRY(c, launch_mo_f64(Pe, E, cap, c->e_R, st));

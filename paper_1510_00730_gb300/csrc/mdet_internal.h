@@ -126,7 +126,8 @@ struct DevScratch {
   double* fb_acc = nullptr;   // fallback: [cap][3 + 8 MDET_FALLBACK_MAX_SPIN] scales, Psi, G
   unsigned long long* queue = nullptr;  // [2 * walker chunks] work counters of persistent contractions
   const int* live = nullptr;  // device count of the walkers to evaluate (null: all n_walk); the FP64
-                              // kernels skip walkers at or beyond it (escalated re-evaluations)
+                              // kernels skip walkers at or beyond it (escalated re-evaluations, whose
+                              // psia is gathered from the evaluation that flagged them)
   double* R_stage = nullptr;  // host-API staging buffers
   double* out_stage = nullptr;
 };
@@ -171,7 +172,7 @@ cudaError_t launch_fb_list(const DevProblem& P, uint32_t* wstat, uint32_t* statu
 // Escalation of mixed-precision walkers: gather of the listed walkers' positions
 // (and *live = their count), and scatter of their FP64 results back.
 cudaError_t launch_esc_gather(const int* list, int cap, int n3, const double* R, double* Re, int* live,
-                              cudaStream_t st);
+                              const float* psia, float* psia_e, cudaStream_t st);
 // Marks the gathered walkers for full LU (wstat[i] = MDET_WS_FALLBACK, i < *live).
 cudaError_t launch_esc_mark(const int* live, uint32_t* wstat, int cap, cudaStream_t st);
 cudaError_t launch_esc_scatter(const int* list, int cap, int N, const EscOut& e, uint32_t or_bits,

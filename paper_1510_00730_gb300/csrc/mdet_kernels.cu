@@ -820,7 +820,7 @@ cudaError_t launch_zero_f64(const DevProblem& P, const DevScratch& S, int64_t n_
   const int64_t npad = (n_walk + kWalkerPad - 1) / kWalkerPad * kWalkerPad;
   cudaError_t e = cudaMemsetAsync(S.vu, 0, sizeof(double) * ndt * npad, st);
   if (e != cudaSuccess) return e;
-  if ((e = cudaMemsetAsync(S.psia, 0, sizeof(float) * npad, st)) != cudaSuccess) return e;
+  if (!S.live && (e = cudaMemsetAsync(S.psia, 0, sizeof(float) * npad, st)) != cudaSuccess) return e;
   return cudaMemsetAsync(S.psit, 0, sizeof(double) * npad, st);
 }
 
@@ -857,10 +857,11 @@ cudaError_t launch_contract_f64(const DevProblem& P, const DevScratch& S, int64_
                                             x_up, S.wp, S.vu, ndt, P.n_det_sp[0], nullptr, nullptr, nullptr);
     return cudaGetLastError();
   }
-  // v = C r_dn (rows = up determinants) with Psi~ = r_up . v and its magnitude sum
-  auto* kv = narrow ? k_spmm_wm<false, true, 4> : (q ? k_spmm_wm<true, true, 8> : k_spmm_wm<false, true, 8>);
+  // v = C r_dn (rows = up determinants) with Psi~ = r_up . v and its magnitude sum (an escalated
+  // re-evaluation reuses the magnitude sum of the evaluation that flagged it)
+  auto* kv = narrow ? k_spmm_wm<false, false, 4> : (q ? k_spmm_wm<true, true, 8> : k_spmm_wm<false, true, 8>);
   kv<<<(unsigned)blocks, 128, 0, st>>>(P.csr_row, P.csr_col, P.csr_val, P.nnz, chunk, n_chunks, n_groups, r_dn, S.wp,
-                                       S.vu, ndt, 0, r_up, S.psit, S.psia, queue, S.live);
+                                       S.vu, ndt, 0, r_up, S.psit, narrow ? nullptr : S.psia, queue, S.live);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   // u = C^T r_up (columns = down determinants), in the paper's column-major order
