@@ -137,27 +137,32 @@ def test_mixed_walker_chunks(chunks):
     assert ctx.last_chunks == chunks
 
 
-@pytest.mark.parametrize("prec,chunks,blocks", [(pkg.PRECISION_MIXED, 8, 0), (pkg.PRECISION_MIXED, 5, 3),
-                                                (pkg.PRECISION_MIXED, 3, 1), (pkg.PRECISION_FP64, 1, 2)])
-def test_persistent_contraction_grids(o2100, prec, chunks, blocks):
+@pytest.mark.parametrize("prec,chunks,blocks,esc", [(pkg.PRECISION_MIXED, 8, 0, False), (pkg.PRECISION_MIXED, 5, 3, False),
+                                                    (pkg.PRECISION_MIXED, 3, 1, False), (pkg.PRECISION_MIXED, 3, 0, True),
+                                                    (pkg.PRECISION_FP64, 1, 2, False)])
+def test_persistent_contraction_grids(o2100, prec, chunks, blocks, esc):
     """The contraction on persistent grids whose warps draw work items from a
-    counter: 8 and 5 pipelined chunks of a ragged 2,100-walker batch, grids of 1
+    counter: 8, 5 and 3 pipelined chunks of a ragged 2,100-walker batch, grids of 1
     to 3 blocks (every warp takes many items) and the FP64 path with a capped grid.
     The mixed fallback tolerance is tightened to 1e-7, so that every walker meets
-    the test tolerances: the fallback then re-evaluates tens of walkers flagged by
-    the pipelined chunks. Stage times come back for every stage."""
+    the test tolerances: the refinement then re-evaluates tens of walkers flagged by
+    the pipelined chunks, by full LU or (esc) by the FP64 ratio table first. Stage
+    times come back for every stage."""
     wl, ref = o2100
     ctx = pkg.Context.from_workload(wl, device=0, precision=prec)
     ctx.set_tuning(walker_chunks=chunks, spmm_blocks=blocks)
     if prec == pkg.PRECISION_MIXED:
         ctx.set_fallback(1e-7, 512)
+        ctx.set_escalation(pkg.Context.ESCALATE_ALWAYS if esc else pkg.Context.ESCALATE_AUTO)
     ctx.set_profiling(True)
-    rep = compare(_gpu_eval(ctx, wl.R), ref, **TOL[prec])
+    got = _gpu_eval(ctx, wl.R)
+    rep = compare(got, ref, **TOL[prec])
     assert rep["ok"], rep
     assert ctx.last_chunks == chunks
-    # 6 kernels per chunk; the fallback: FP64 full LU 5, mixed refinement (no escalation for
-    # this small expansion) 10
-    assert ctx.last_kernels == 6 * chunks + (5 if prec == pkg.PRECISION_FP64 else 10)
+    assert bool(((got["status"] & pkg.WS_ESCALATED) != 0).any()) == esc
+    # 6 kernels per chunk; the fallback: FP64 full LU 5; the mixed refinement 10, or 14 with
+    # the FP64 table (this small expansion escalates only when forced)
+    assert ctx.last_kernels == 6 * chunks + (5 if prec == pkg.PRECISION_FP64 else (14 if esc else 10))
     prof = ctx.profile()
     assert all(v > 0 for k, v in prof.items() if k != "zero"), prof
 
