@@ -21,34 +21,47 @@ _ip = np.ctypeslib.ndpointer(dtype=np.int32, flags="C_CONTIGUOUS")
 _up = np.ctypeslib.ndpointer(dtype=np.uint64, flags="C_CONTIGUOUS")
 
 
+def compile_library(src: str, out: str) -> str:
+    """gcc -O2 without fused multiply-add contraction, src -> shared library out."""
+    tmp = out + ".tmp%d" % os.getpid()
+    subprocess.check_call(["gcc", "-O2", "-ffp-contract=off", "-fPIC", "-shared", src,
+                           "-o", tmp, "-lm", "-lpthread"])
+    os.replace(tmp, out)
+    return out
+
+
 def build(force: bool = False) -> str:
     """Compile oracle.c into liboracle.so (plain gcc, no fused multiply-add contraction)."""
     if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
-        tmp = _LIB + ".tmp%d" % os.getpid()
-        subprocess.check_call(["gcc", "-O2", "-ffp-contract=off", "-fPIC", "-shared", _SRC,
-                               "-o", tmp, "-lm", "-lpthread"])
-        os.replace(tmp, _LIB)
+        compile_library(_SRC, _LIB)
     return _LIB
+
+
+def load(path: str):
+    """ctypes handle of an oracle library at path, with every export's argument types."""
+    L = C.CDLL(path)
+    L.oracle_n_ao.argtypes = [C.c_int, _ip]
+    L.oracle_ao_eval.argtypes = [C.c_int, _ip, _ip, _ip, _dp, _dp, _dp, C.c_int, _dp, _dp]
+    L.oracle_mo_eval.argtypes = [C.c_int, _ip, _ip, _ip, _dp, _dp, _dp, C.c_int, _dp, C.c_int, _dp, _dp]
+    L.oracle_det.argtypes = [C.c_int, _dp, C.POINTER(C.c_double), C.POINTER(C.c_int)]
+    L.oracle_inverse.argtypes = [C.c_int, _dp, _dp]
+    L.oracle_evaluate.argtypes = [C.c_int, C.c_int, C.c_int, _dp, _dp,
+                                  C.c_int, _ip, _ip, _ip, _dp, _dp, C.c_int, _dp,
+                                  C.c_int64, C.c_int, _up, _up, _dp, C.c_int64, _dp, C.c_int, C.c_int,
+                                  _dp, _ip, _dp, _dp, _dp, _dp]
+    L.oracle_spin_dets.argtypes = [C.c_int, C.c_int, C.c_int, C.c_int, _ip, _ip, _ip, _dp, _dp, _dp,
+                                   C.c_int, _dp, C.c_int64, C.c_int, _up, C.c_int64, _dp, C.c_int,
+                                   _dp, _ip, _dp]
+    L.oracle_potential.argtypes = [C.c_int, _dp, C.c_int, _dp, _dp]
+    L.oracle_potential.restype = C.c_double
+    return L
 
 
 def lib():
     global _lib
     if _lib is None:
         build()
-        L = C.CDLL(_LIB)
-        L.oracle_n_ao.argtypes = [C.c_int, _ip]
-        L.oracle_ao_eval.argtypes = [C.c_int, _ip, _ip, _ip, _dp, _dp, _dp, C.c_int, _dp, _dp]
-        L.oracle_mo_eval.argtypes = [C.c_int, _ip, _ip, _ip, _dp, _dp, _dp, C.c_int, _dp, C.c_int, _dp, _dp]
-        L.oracle_det.argtypes = [C.c_int, _dp, C.POINTER(C.c_double), C.POINTER(C.c_int)]
-        L.oracle_inverse.argtypes = [C.c_int, _dp, _dp]
-        L.oracle_evaluate.argtypes = [C.c_int, C.c_int, C.c_int, _dp, _dp,
-                                      C.c_int, _ip, _ip, _ip, _dp, _dp, C.c_int, _dp,
-                                      C.c_int64, C.c_int, _up, _up, _dp, C.c_int64, _dp, C.c_int, C.c_int,
-                                      _dp, _ip, _dp, _dp, _dp, _dp]
-        L.oracle_spin_dets.argtypes = [C.c_int, C.c_int, C.c_int, C.c_int, _ip, _ip, _ip, _dp, _dp, _dp,
-                                       C.c_int, _dp, C.c_int64, C.c_int, _up, C.c_int64, _dp, C.c_int,
-                                       _dp, _ip, _dp]
-        _lib = L
+        _lib = load(_LIB)
     return _lib
 
 
@@ -131,6 +144,16 @@ def evaluate(wl, R=None, mode=0, n_threads=None, mo_coef=None, det_up=None, det_
     if rc != 0:
         raise ValueError("oracle_evaluate failed: %d" % rc)
     return out
+
+
+def potential(r, Z=(), X=()):
+    """V = -sum_iA Z_A / |r_i - X_A| + sum_{i<j} 1 / |r_i - r_j| + sum_{A<B} Z_A Z_B / |X_A - X_B|."""
+    r = _f64(r).reshape(-1, 3)
+    Z = _f64(Z).reshape(-1)
+    X = _f64(X).reshape(-1, 3)
+    assert X.shape[0] == Z.shape[0]
+    return lib().oracle_potential(r.shape[0], r, Z.shape[0], Z if Z.size else np.zeros(1),
+                                  X if X.size else np.zeros((1, 3)))
 
 
 def spin_dets(wl, spin, dets, R=None, mode=0, mo_coef=None):

@@ -338,6 +338,12 @@ static double potential(int n_e, const double* r, int n_nuc, const double* Z, co
   return nval(&v);
 }
 
+/* Potential energy of n_e electrons at r[n_e][3] and n_nuc point nuclei of
+ * charges Z at X[n_nuc][3] (the V of E_L, Sec. 4), exported for its pins. */
+double oracle_potential(int n_e, const double* r, int n_nuc, const double* Z, const double* X) {
+  return potential(n_e, r, n_nuc, Z, X);
+}
+
 static void* eval_job(void* arg) {
   job_t* J = (job_t*)arg;
   const int nu = J->n_up, nd = J->n_dn, ne = nu + nd, M = J->n_mo;

@@ -339,3 +339,149 @@ def test_local_energy_hydrogenic_closed_form():
     r2 = (R ** 2).sum(-1)[:, 0]
     np.testing.assert_allclose(o["e_local"], 3 * alpha - 2 * alpha ** 2 * r2 - Z / np.sqrt(r2), rtol=1e-13)
     np.testing.assert_allclose(o["grad"][:, 0], -2 * alpha * R[:, 0], rtol=1e-13)
+
+
+# ------------------------------------------------------- conditioning of the CI sum
+# kappa = sum_k |c_k D_up D_dn| / |Psi| (the factor by which a relative rounding
+# of each product of Eq. 1 can grow in the sum); the parity tests scale the
+# log|Psi| tolerance by it, so it gets pins of its own.
+def test_kappa_single_determinant_is_one():
+    """N_det = 1: the sum has one term, so sum |c D D| = |Psi| and kappa = 1 exactly."""
+    wl = synth.oxygen_like_1k(n_walk=7)
+    o = oracle.evaluate(wl, det_up=wl.det_up[5:6], det_dn=wl.det_dn[5:6], ci=np.array([-2.5]))
+    assert np.all(o["kappa"] == 1.0), o["kappa"]
+
+
+def _two_product_case():
+    """Two products with distinct up and down determinants and coefficients of
+    opposite sign, at walkers where the two terms partly cancel."""
+    wl = synth.oxygen_like_1k(n_walk=40, seed=77)
+    ks = [0, 9]
+    du, dd, c = wl.det_up[ks], wl.det_dn[ks], np.array([0.8, -0.55])
+    assert not np.array_equal(du[0], du[1]) and not np.array_equal(dd[0], dd[1])
+    terms = np.empty((wl.n_walk, 2))
+    for w in range(wl.n_walk):
+        phi = oracle.mo_eval(wl, wl.R[w])[:, 0, :]
+        for q in range(2):
+            up = leibniz_det(_slater(phi, _occ(du[q]), list(range(4))))
+            dn = leibniz_det(_slater(phi, _occ(dd[q]), list(range(4, 8))))
+            terms[w, q] = c[q] * up * dn
+    return wl, du, dd, c, terms
+
+
+def test_kappa_two_products_closed_form():
+    """kappa = (|t1| + |t2|) / |t1 + t2| with t_q = c_q D_up,q D_dn,q from Leibniz
+    determinants of the (pinned) orbital values; at least some walkers have
+    terms of opposite sign, so a numerator without |.|, or the reciprocal, fails."""
+    wl, du, dd, c, t = _two_product_case()
+    want = np.abs(t).sum(1) / np.abs(t.sum(1))
+    assert (want > 1.5).sum() >= 5, want
+    o = oracle.evaluate(wl, det_up=du, det_dn=dd, ci=c)
+    np.testing.assert_allclose(o["kappa"], want, rtol=1e-9)
+    np.testing.assert_array_equal(o["sign"], np.sign(t.sum(1)))
+
+
+def test_kappa_fci_cauchy_binet():
+    """Full CI with C_IJ = m_I m_J (m the N x N minors of an orthogonal U, as in the
+    Cauchy-Binet pin above): sum_IJ |C_IJ D_I D_J| factorises into
+    (sum_I |m_I D_up,I|) (sum_J |m_J D_dn,J|), and Psi = det(Phi_up U_:N) det(Phi_dn U_:N).
+    The determinants here are numpy's LU (an independent library routine)."""
+    M, N = 10, 4
+    wl = synth.oxygen_like_1k(n_walk=5)
+    wl.mo_coef = wl.mo_coef[:, :M].copy()
+    U, _ = np.linalg.qr(np.random.default_rng(11).normal(size=(M, M)))
+    subsets = list(combinations(range(M), N))
+    bits = np.array([[sum(1 << m for m in s)] for s in subsets], dtype=np.uint64)
+    minors = np.array([np.linalg.det(U[list(s), :N]) for s in subsets])
+    I, J = np.meshgrid(np.arange(len(subsets)), np.arange(len(subsets)), indexing="ij")
+    o = oracle.evaluate(wl, det_up=bits[I.ravel()], det_dn=bits[J.ravel()], ci=minors[I.ravel()] * minors[J.ravel()])
+    for w in range(wl.n_walk):
+        phi = oracle.mo_eval(wl, wl.R[w])[:, 0, :]
+        su = sum(abs(m * np.linalg.det(phi[:4][:, list(s)])) for m, s in zip(minors, subsets))
+        sd = sum(abs(m * np.linalg.det(phi[4:][:, list(s)])) for m, s in zip(minors, subsets))
+        psi = np.linalg.det(phi[:4] @ U[:, :N]) * np.linalg.det(phi[4:] @ U[:, :N])
+        assert abs(o["kappa"][w] - su * sd / abs(psi)) <= 1e-9 * su * sd / abs(psi), (w, o["kappa"][w])
+
+
+# ------------------------------------------------------------ potential energy
+# V of E_L (Sec. 4): electron-nucleus attraction, electron-electron and
+# nucleus-nucleus repulsion. Each pin below is a hand-evaluated configuration.
+def test_potential_two_electrons_one_nucleus():
+    """r1 = (0, 0, 1), r2 = (0, 3, 1), Z = 2 at the origin:
+    V = -2/1 - 2/sqrt(10) + 1/3 (the electron pair enters once, with a + sign)."""
+    v = oracle.potential([[0, 0, 1.0], [0, 3.0, 1.0]], [2.0], [[0, 0, 0]])
+    assert abs(v - (-2.0 - 2.0 / math.sqrt(10.0) + 1.0 / 3.0)) < 1e-15
+
+
+def test_potential_nucleus_pair():
+    """No electron: V = Z_A Z_B / R_AB = 3 * 5 / 2.5; one electron midway between
+    them adds -3/1.25 - 5/1.25."""
+    X = [[0, 0, 0], [1.5, 2.0, 0]]
+    assert abs(oracle.potential(np.zeros((0, 3)), [3.0, 5.0], X) - 6.0) < 1e-15
+    v = oracle.potential([[0.75, 1.0, 0]], [3.0, 5.0], X)
+    assert abs(v - (6.0 - 3.0 / 1.25 - 5.0 / 1.25)) < 1e-14
+
+
+def test_potential_three_electrons_count_pairs():
+    """Three electrons on a 3-4-5 right triangle, no nuclei: 1/3 + 1/4 + 1/5
+    (three pairs, each once); four electrons on a unit square: 4 + 2/sqrt(2)."""
+    v = oracle.potential([[0, 0, 0], [3.0, 0, 0], [0, 4.0, 0]])
+    assert abs(v - (1 / 3 + 1 / 4 + 1 / 5)) < 1e-15
+    v4 = oracle.potential([[0, 0, 0], [1.0, 0, 0], [1.0, 1.0, 0], [0, 1.0, 0]])
+    assert abs(v4 - (4.0 + 2.0 / math.sqrt(2.0))) < 1e-14
+
+
+def test_local_energy_two_electrons_two_nuclei_closed_form():
+    """E_L of Psi = e^{-alpha r1^2} e^{-alpha r2^2} (one up and one down electron in
+    the same 1s Gaussian on nucleus A) next to a second nucleus B:
+    E_L = sum_i (3 alpha - 2 alpha^2 r_i^2) - sum_iA Z_A / |r_i - X_A| + 1 / r12 + Z_A Z_B / R_AB,
+    which pins the kinetic term, all three potential sums and their signs in
+    evaluate itself."""
+    alpha, ZA, ZB = 0.45, 2.0, 1.0
+    wl = _one_shell_workload(0, alpha)
+    wl.n_up, wl.n_dn = 1, 1
+    wl.Z = np.array([ZA, ZB])
+    XB = np.array([0.3, -0.2, 1.4])
+    wl.nuc_xyz = np.array([[0.0, 0.0, 0.0], XB])
+    wl.mo_coef = np.ones((1, 1))
+    R = np.array([[[0.3, -0.4, 0.5], [-0.6, 0.1, 0.9]], [[1.1, 0.2, -0.3], [0.2, 0.2, 0.2]]])
+    one = np.array([[1]], np.uint64)
+    o = oracle.evaluate(wl, R=R, det_up=one, det_dn=one, ci=np.array([1.0]))
+    for w in range(R.shape[0]):
+        r1, r2 = R[w]
+        kin = sum(3 * alpha - 2 * alpha ** 2 * (r @ r) for r in (r1, r2))
+        ven = -sum(ZA / np.linalg.norm(r) + ZB / np.linalg.norm(r - XB) for r in (r1, r2))
+        want = kin + ven + 1.0 / np.linalg.norm(r1 - r2) + ZA * ZB / np.linalg.norm(XB)
+        assert abs(o["e_local"][w] - want) < 1e-13 * max(1.0, abs(want)), (w, o["e_local"][w], want)
+
+
+def test_local_energy_is_kinetic_plus_potential_many_electrons():
+    """For the 8-electron expansion, E_L + 1/2 sum_i Lap_i Psi / Psi (the kinetic
+    part, pinned by finite differences above) equals V by brute force over every
+    electron, pair and nucleus: 28 electron pairs."""
+    wl = synth.oxygen_like_1k(n_walk=3)
+    o = oracle.evaluate(wl)
+    for w in range(wl.n_walk):
+        r = wl.R[w]
+        v = -sum(wl.Z[A] / np.linalg.norm(r[i] - wl.nuc_xyz[A]) for i in range(8) for A in range(len(wl.Z)))
+        v += sum(1.0 / np.linalg.norm(r[i] - r[j]) for i, j in combinations(range(8), 2))
+        assert abs(o["e_local"][w] + 0.5 * o["lap"][w].sum() - v) < 1e-12 * max(1.0, abs(v))
+
+
+# ------------------------------------------------ row-replaced cross-check mode
+@pytest.mark.parametrize("name,n_walk", [("tiny", 6), ("oxygen_like_1k", 16)])
+def test_row_replaced_mode_matches_cofactor_mode(name, n_walk):
+    """The two derivative routes of the oracle: cofactors from the inverse (mode 0,
+    Eq. 8 read with (S^-1)_{a i}) and determinants of the Slater matrix with row i
+    replaced by d_mu phi(r_i) (mode 1, the definition of a derivative of a
+    determinant that is linear in row i) agree to rounding."""
+    wl = getattr(synth, name)(n_walk=n_walk)
+    o0 = oracle.evaluate(wl, mode=0)
+    o1 = oracle.evaluate(wl, mode=1)
+    np.testing.assert_array_equal(o0["sign"], o1["sign"])
+    np.testing.assert_allclose(o1["log_abs_psi"], o0["log_abs_psi"], rtol=0, atol=1e-13)
+    for k in ("grad", "lap"):
+        a, b = o0[k], o1[k]
+        scale = np.sqrt(np.mean(a.reshape(n_walk, -1) ** 2, axis=1)).reshape((-1,) + (1,) * (a.ndim - 1))
+        err = np.abs(a - b) / np.maximum(np.abs(a), scale)
+        assert err.max() < 1e-10, (k, err.max())
