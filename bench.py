@@ -25,11 +25,11 @@ sys.path.insert(0, ROOT)
 
 METRIC = "walker-steps/s (Ψ,∇Ψ,∇²Ψ), 17e⁻, N_det=750k: mixed vs FP64 at 1e-5 rel err"
 UNIT = "walker-steps/s"
-FP64_PEAK_TFLOPS = 1.25     # nominal dense FP64 rate of one GB300 (no measured FP64 peak is available)
 CPU_SAMPLE_WALKERS = 96     # bounded oracle sample for the CPU baseline (~10-30 s of CPU work)
+CPU_SINGLE_CORE_WALKERS = 8  # the same oracle on one core, for the per-core figure
 # dram__bytes_read.sum + dram__bytes_write.sum of the average k_spmm_wm launch on the 750k workload
-# with 8,192 walkers, by the number of walker chunks (ncu captures summarised in
-# profiles/mixed_chlorine_like_750k.md); null for a chunking that was not captured
+# with 8,192 walkers, by the number of walker chunks, from one ncu capture of the current kernel;
+# null for a chunking that was not captured
 SPMM_TRAFFIC_750K = {1: 746.8e6, 3: 227.8e6}
 
 
@@ -99,16 +99,56 @@ def _gpu_index(local_rank):
     return local_rank
 
 
-def cpu_baseline(wl, n_sample, threads=None):
-    """The FP64 oracle as it stands, on a bounded sample of walkers, all host cores."""
+def cpu_model():
+    """The host CPU's model name (lscpu, else /proc/cpuinfo, else the machine type)."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for l in out.splitlines():
+            if l.strip().lower().startswith("model name"):
+                return l.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    try:
+        for l in open("/proc/cpuinfo"):
+            if l.lower().startswith(("model name", "cpu model")):
+                return l.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    import platform
+    return platform.machine()
+
+
+def cpu_baseline(wl, n_sample, threads=None, single_core=CPU_SINGLE_CORE_WALKERS):
+    """The FP64 oracle as it stands, on a bounded sample of walkers, all host
+    cores; then on one core for a smaller sample (the per-core figure, the unit
+    the paper's timings use)."""
     import oracle
     threads = threads or os.cpu_count() or 1
     R = wl.R[:n_sample]
     t0 = time.perf_counter()
     ref = oracle.evaluate(wl, R=R, n_threads=threads)
     dt = time.perf_counter() - t0
-    return ref, {"value": n_sample / dt, "unit": UNIT, "cores": threads, "kind": "oracle",
-                 "sample": "%d of the %d walkers of one step (same expansion), %.1f s wall" % (n_sample, wl.n_walk, dt)}
+    cb = {"value": n_sample / dt, "unit": UNIT, "cores": threads, "kind": "oracle", "cpu_model": cpu_model(),
+          "sample": "%d of the %d walkers of one step (same expansion), %.1f s wall" % (n_sample, wl.n_walk, dt)}
+    if single_core:
+        t0 = time.perf_counter()
+        oracle.evaluate(wl, R=wl.R[:single_core], n_threads=1)
+        d1 = time.perf_counter() - t0
+        cb["single_core"] = {"value": single_core / d1, "unit": UNIT, "cores": 1,
+                             "ms_per_walker_step": d1 * 1e3 / single_core,
+                             "sample": "%d walkers on one thread, %.1f s" % (single_core, d1)}
+    return ref, cb
+
+
+def fp64_peak(device, clock_index=None):
+    """The FP64 FMA pipe's throughput, measured now on this device by the
+    library's probe (independent FMA chains on every SM), with the SM clocks seen
+    while it ran."""
+    import paper_1510_00730_gb300 as pkg
+    pkg.measure_fp64_rate(device, fma_per_thread=1 << 16, reps=2)  # warm the clocks
+    with ClockSampler(clock_index if clock_index is not None else device) as clk:
+        tf, ms = pkg.measure_fp64_rate(device, fma_per_thread=1 << 18, reps=12)
+    return tf, ms, clk.summary()
 
 
 def run_reference(args):
@@ -310,10 +350,13 @@ def run_ours(args):
     traffic = args.traffic
     if traffic is None and args.workload == "chlorine_like_750k" and W == 8192:
         traffic = SPMM_TRAFFIC_750K.get(main_chunks)
-    roofline = {"kernel": "k_spmm_wm", "bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS,
-                "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS, "traffic": traffic,
+    peak, peak_ms, peak_clocks = fp64_peak(local, _gpu_index(local))
+    roofline = {"kernel": "k_spmm_wm", "bound": "alu", "achieved": achieved, "peak": peak,
+                "unit": "TFLOP/s", "frac": achieved / peak, "traffic": traffic,
                 "traffic_unit": "bytes per launch (ncu dram read + write)",
-                "peak_source": "nominal FP64 of the recipe table (no measured FP64 peak)",
+                "peak_source": "measured in this run: FP64 FMA probe (mdet_measure_fp64_rate, 8 independent "
+                               "chains per thread, 32 warps per SM, fastest of 12 launches of %.1f ms)" % peak_ms,
+                "peak_clocks": peak_clocks, "peak_nominal": 1.25,
                 "flops_per_launch": flops_launch, "launch_ms": launch_ms}
 
     line = {"metric": METRIC, "value": main["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -341,6 +384,12 @@ def run_ours(args):
                           "kernels_ms": results[name]["kern"], "fallback_walkers": results[name]["n_fb"],
                           "fallback_tol": results[name]["fallback_tol"]}
 
+    if rank == 0 and world == 1 and args.batch and args.workload == "chlorine_like_750k":
+        # config 4 beside the headline: 64 uneven expansions, autotuned, one graph launch per step
+        b = measure_batched(primary, args.steps, args.warmup, args.streams, args.tune_ms)
+        line["batched_uneven_64"] = {k: b[k] for k in ("value", "unit", "ms_per_step", "sum_of_solo_ms", "batch_gain",
+                                                       "clocks", "gpu_launches", "tuning_histogram")}
+        line["batched_uneven_64"].update(b["config"])
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         from tests.parity import walker_quantiles
         ref, cb = cpu_baseline(wl, CPU_SAMPLE_WALKERS)
@@ -356,37 +405,36 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
-def run_batched(args):
+def measure_batched(precision, steps, warmup, streams=8, tune_ms=60.0, fallback_tol=None):
     """The 64-expansion uneven workload: every expansion autotuned, then all
     evaluations replayed as one CUDA-graph launch; value = walkers of all
-    expansions per second of graph time."""
+    expansions per second of graph time. Returns the JSON line (a dict)."""
     import numpy as np
     import torch
 
     import paper_1510_00730_gb300 as pkg
     from paper_1510_00730_gb300 import synth
-    torch.cuda.set_device(0)
-    dev = torch.device("cuda", 0)
-    prec = {"mixed": pkg.PRECISION_MIXED, "fp64": pkg.PRECISION_FP64}[args.precision]
+    dev = torch.device("cuda", torch.cuda.current_device())
+    prec = {"mixed": pkg.PRECISION_MIXED, "fp64": pkg.PRECISION_FP64}[precision]
     wls = synth.batched_uneven()
-    ctxs = [pkg.Context.from_workload(wl, device=0, precision=prec) for wl in wls]
-    if args.fallback_tol is not None:
+    ctxs = [pkg.Context.from_workload(wl, device=dev.index, precision=prec) for wl in wls]
+    if fallback_tol is not None:
         for c in ctxs:
-            c.set_fallback(args.fallback_tol)
+            c.set_fallback(fallback_tol)
     Rs = [torch.from_numpy(wl.R).to(dev) for wl in wls]
     t0 = time.perf_counter()
-    tunes = [c.autotune(R, budget_ms=args.tune_ms) for c, R in zip(ctxs, Rs)]
+    tunes = [c.autotune(R, budget_ms=tune_ms) for c, R in zip(ctxs, Rs)]
     tune_s = time.perf_counter() - t0
-    batch = pkg.Batch(ctxs, Rs, n_streams=args.streams)
+    batch = pkg.Batch(ctxs, Rs, n_streams=streams)
     batched_kernels = sum(c.last_kernels for c in ctxs)  # as enqueued by the batch (its warm-up pass)
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
     stream = torch.cuda.current_stream(dev)
-    for _ in range(args.warmup):
+    for _ in range(warmup):
         batch.launch()
     torch.cuda.synchronize()
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
-    with ClockSampler(_gpu_index(0)) as clk:
-        for s in range(args.steps):
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    with ClockSampler(_gpu_index(dev.index)) as clk:
+        for s in range(steps):
             flush.fill_(float(s))
             ev[s][0].record(stream)
             batch.launch()
@@ -406,11 +454,11 @@ def run_batched(args):
         torch.cuda.synchronize()
         solo += a.elapsed_time(b)
     line = {"metric": "walker-steps/s, 64 uneven expansions in one graph launch", "value": W / (ms / 1e3),
-            "unit": UNIT, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+            "unit": UNIT, "n_gpus": 1, "steps": steps, "warmup": warmup, "ms_per_step": ms,
             "higher_is_better": True, "dtype": "f64" if prec == pkg.PRECISION_FP64 else "f64+f32x2",
             "data": "synthetic",
-            "config": {"workload": "batched_uneven_64", "precision": args.precision, "walkers_total": W,
-                       "n_det_total": int(sum(wl.n_det for wl in wls)), "streams": args.streams,
+            "config": {"workload": "batched_uneven_64", "precision": precision, "walkers_total": W,
+                       "n_det_total": int(sum(wl.n_det for wl in wls)), "streams": streams,
                        "fallback_tol": ctxs[0].fallback[0],
                        "autotune_s": tune_s, "l2": "flushed between timed steps"},
             "sum_of_solo_ms": solo, "batch_gain": solo / ms,
@@ -419,10 +467,19 @@ def run_batched(args):
             "clocks": clk.summary(),
             # kernels per expansion as the library counts them (the solo runs above are not in a
             # batch, so the count of a batched evaluation is taken with the batch's choices)
-            "gpu_launches": batched_kernels * args.steps}
+            "gpu_launches": batched_kernels * steps}
     line["tuning_histogram"] = {k: {str(a): int(b) for a, b in v.items()} for k, v in line["tuning_histogram"].items()}
-    print(json.dumps(line), flush=True)
     batch.close()
+    for c in ctxs:
+        c.close()
+    return line
+
+
+def run_batched(args):
+    import torch
+    torch.cuda.set_device(0)
+    print(json.dumps(measure_batched(args.precision, args.steps, args.warmup, args.streams, args.tune_ms,
+                                     args.fallback_tol)), flush=True)
 
 
 def run_truncation(args):
@@ -628,6 +685,8 @@ def main():
     p.add_argument("--no-compare", dest="compare", action="store_false",
                    help="skip timing the other precision in the same run")
     p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-batch", dest="batch", action="store_false",
+                   help="skip the 64-expansion graph batch that the default line reports beside the headline")
     p.add_argument("--chunks", type=int, default=None, help="walker chunks of the mixed path (default: library's)")
     p.add_argument("--fallback-tol", type=float, default=None,
                    help="fallback tolerance of the timed contexts (default: the library's, 1e-5 mixed, 1e-8 FP64)")

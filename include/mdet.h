@@ -410,17 +410,21 @@ mdet_status mdet_get_profile(mdet_ctx* ctx, float* ms);
  * The paper has no counterpart: this entry point exists for callers that
  * cannot allocate device memory when they call it (a pooled or custom device
  * allocator that owns all of the GPU's memory, or a runtime that forbids
- * allocation after start-up). It runs the row-ordered contraction kernel of
- * mdet_evaluate on ratios the caller supplies, keeping the intermediate
- * v = C r_dn in a static device array of MDET_NOALLOC_SCRATCH_DOUBLES doubles
- * (32 MiB) that every GPU loading this library holds until the process exits.
+ * allocation after start-up). It runs a segmented product over the
+ * row-ordered copy of C whose output v = C r_dn is walker-minor like its input
+ * (a form of its own: mdet_evaluate's contraction writes v walker-major into
+ * the context's scratch) on ratios the caller supplies, keeping v in a static
+ * device array of MDET_NOALLOC_SCRATCH_DOUBLES doubles (32 MiB) that every GPU
+ * loading this library holds until the process exits.
  *   r          device, [n_det_up + n_det_dn][ld] walker-minor ratios D_I / D_ref
  *              of the distinct determinants in the context's order (up block,
  *              then down block; mdet_get_ratios gives them walker-major),
  *              16-byte aligned; ld a multiple of 128 and >= n_walk
  *   psi_tilde  device, [n_walk]: Psi / (D_ref_up D_ref_dn)
- * Asynchronous on `stream`. Fails with MDET_E_ARG when
- * (n_det_up + 1) * ld exceeds MDET_NOALLOC_SCRATCH_DOUBLES. The first call on
+ * Asynchronous on `stream`; the caller's current device is restored before
+ * return. Fails with MDET_E_ARG when (n_det_up + 1) * ld exceeds
+ * MDET_NOALLOC_SCRATCH_DOUBLES (checked without forming the product, so any ld
+ * is safe to pass). The first call on
  * a device looks up the array's device address (cudaGetSymbolAddress) and
  * should come before any stream capture on that device. Every call shares the
  * one array and leaves its contents behind; it clears what it uses before use,
@@ -429,6 +433,21 @@ mdet_status mdet_get_profile(mdet_ctx* ctx, float* ms);
 #define MDET_NOALLOC_SCRATCH_DOUBLES (4u * 1024u * 1024u)
 mdet_status mdet_psi_tilde_noalloc(mdet_ctx* ctx, int64_t n_walk, const double* r, int64_t ld,
                                    double* psi_tilde, void* stream);
+
+/*
+ * Measured FP64 FMA throughput of a device, the roofline denominator of the
+ * FP64 kernels (the CI contraction of Sec. 2.4 is bound by this pipe). The paper
+ * has no counterpart; it quotes CPU cycle counts instead (Sec. 5).
+ * Every thread of a grid of 4 blocks of 256 threads per SM runs 8 independent
+ * chains a <- fma(a, b, c) for fma_per_thread FMAs (a multiple of 32); one
+ * warm-up launch, then `reps` timed launches (CUDA events), the fastest kept.
+ *   tflops   out: 2 * FMAs / best time, in TFLOP/s
+ *   best_ms  out (nullable): the fastest launch's time
+ * Synchronous. Allocates a small output buffer for the chains' results and
+ * frees it; the caller's current device is restored. MDET_E_ARG on a null
+ * tflops, fma_per_thread < 32 or reps < 1; MDET_E_CUDA on any CUDA error.
+ */
+mdet_status mdet_measure_fp64_rate(int device, int64_t fma_per_thread, int reps, double* tflops, double* best_ms);
 
 /*
  * Diagnostic of the double-float arithmetic used by the mixed path: for n

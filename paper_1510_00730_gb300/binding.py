@@ -100,12 +100,13 @@ def load_library(build_if_missing: bool = True):
     L.mdet_batch_destroy.argtypes = [vp]
     L.mdet_batch_destroy.restype = None
     L.mdet_get_profile.argtypes = [vp, vp]
+    L.mdet_measure_fp64_rate.argtypes = [i32, i64, i32, vp, vp]
     for name in ("mdet_create", "mdet_set_system", "mdet_set_orbitals", "mdet_set_ci_expansion", "mdet_evaluate",
                  "mdet_evaluate_host", "mdet_get_ratios", "mdet_get_stats", "mdet_get_spin_dets",
                  "mdet_get_ci_matrix", "mdet_omega_sort", "mdet_truncate_norm", "mdet_sm_chain", "mdet_set_ci_expansion_device", "mdet_set_profiling", "mdet_get_profile",
                  "mdet_psi_tilde_noalloc", "mdet_set_walker_chunks", "mdet_get_last_launches", "mdet_set_escalation", "mdet_selftest_df32", "mdet_get_tuning",
                  "mdet_set_tuning", "mdet_autotune", "mdet_batch_evaluate", "mdet_batch_create", "mdet_batch_launch", "mdet_set_fallback", "mdet_get_fallback",
-                 "mdet_get_error_estimates"):
+                 "mdet_get_error_estimates", "mdet_measure_fp64_rate"):
         getattr(L, name).restype = i32
     # VMC moves and the learned proposal (include/mdet_vmc.h)
     u32p = C.POINTER(C.c_uint32)
@@ -221,6 +222,16 @@ def selftest_df32(x):
     if st:
         raise MdetError(st, "mdet_selftest_df32 failed")
     return y_df, y_ref, prod
+
+
+def measure_fp64_rate(device=0, fma_per_thread=1 << 18, reps=10):
+    """Measured FP64 FMA throughput of a device: (TFLOP/s, fastest launch in ms)."""
+    L = load_library()
+    tf, ms = C.c_double(), C.c_double()
+    st = L.mdet_measure_fp64_rate(int(device), int(fma_per_thread), int(reps), C.byref(tf), C.byref(ms))
+    if st:
+        raise MdetError(st, "mdet_measure_fp64_rate failed: %s" % L.mdet_status_string(st).decode())
+    return tf.value, ms.value
 
 
 class Context:

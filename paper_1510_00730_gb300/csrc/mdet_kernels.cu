@@ -815,12 +815,22 @@ cudaError_t launch_ratios_f64(const DevProblem& P, const DevScratch& S, int64_t 
   return cudaGetLastError();
 }
 
+// The contraction of an escalated re-evaluation (few walkers, live count on the
+// device): 4 walkers per lane and no magnitude sum, because the walkers keep the
+// sum of the evaluation that flagged them (gathered into psia). Decided in one
+// place for the zeroing and the launch, which must agree on whether psia is summed.
+static bool narrow_contraction(const DevProblem& P, const DevScratch& S) {
+  return S.live != nullptr && !(P.contract_impl == 1 && S.rdf && P.csr_val_df);
+}
+
 cudaError_t launch_zero_f64(const DevProblem& P, const DevScratch& S, int64_t n_walk, cudaStream_t st) {
   const int64_t ndt = (int64_t)P.n_det_sp[0] + P.n_det_sp[1];
   const int64_t npad = (n_walk + kWalkerPad - 1) / kWalkerPad * kWalkerPad;
   cudaError_t e = cudaMemsetAsync(S.vu, 0, sizeof(double) * ndt * npad, st);
   if (e != cudaSuccess) return e;
-  if (!S.live && (e = cudaMemsetAsync(S.psia, 0, sizeof(float) * npad, st)) != cudaSuccess) return e;
+  // the narrow contraction keeps the gathered magnitude sums; every other one accumulates them anew
+  if (!narrow_contraction(P, S) && (e = cudaMemsetAsync(S.psia, 0, sizeof(float) * npad, st)) != cudaSuccess)
+    return e;
   return cudaMemsetAsync(S.psit, 0, sizeof(double) * npad, st);
 }
 
@@ -829,7 +839,7 @@ cudaError_t launch_contract_f64(const DevProblem& P, const DevScratch& S, int64_
   const int chunk = P.spmm_chunk > 0 ? P.spmm_chunk : 512;
   const int64_t n_chunks = (P.nnz + chunk - 1) / chunk;
   // an escalated re-evaluation (few walkers, live count on the device) uses 4 walkers per lane
-  const bool narrow = S.live != nullptr && !(P.contract_impl == 1 && S.rdf && P.csr_val_df);
+  const bool narrow = narrow_contraction(P, S);
   const int64_t n_groups = narrow ? (n_walk + 127) / 128 : (n_walk + 255) / 256;
   const int64_t items = n_chunks * n_groups;
   // one work item per warp (full occupancy hides the L2 latency of the gathers), or a

@@ -42,6 +42,24 @@ cudaError_t scratch_address(int device, double** out) {
   return cudaSuccess;
 }
 
+// The work itself, with the caller's device already switched to the context's.
+mdet_status psi_tilde_on_device(const DevProblem* P, int device, int64_t n_walk, const double* r,
+                                int64_t ld, double* psi_tilde, cudaStream_t st) {
+  double* scratch = nullptr;
+  if (scratch_address(device, &scratch) != cudaSuccess) return MDET_E_CUDA;
+  const int64_t n_up = P->n_det_sp[0];
+  double* v = scratch;                 // [n_det_up][ld]
+  double* psit = scratch + n_up * ld;  // [ld]
+  // the kernel accumulates with atomics: clear what this call uses
+  if (cudaMemsetAsync(scratch, 0, sizeof(double) * (n_up + 1) * ld, st) != cudaSuccess) return MDET_E_CUDA;
+  const double* r_up = r;
+  const double* r_dn = r + n_up * ld;
+  if (launch_spmm_rows_f64(*P, r_dn, r_up, v, psit, ld, n_walk, st) != cudaSuccess) return MDET_E_CUDA;
+  if (cudaMemcpyAsync(psi_tilde, psit, sizeof(double) * n_walk, cudaMemcpyDeviceToDevice, st) != cudaSuccess)
+    return MDET_E_CUDA;
+  return MDET_OK;
+}
+
 }  // namespace
 
 extern "C" mdet_status mdet_psi_tilde_noalloc(mdet_ctx* ctx, int64_t n_walk, const double* r, int64_t ld,
@@ -52,28 +70,22 @@ extern "C" mdet_status mdet_psi_tilde_noalloc(mdet_ctx* ctx, int64_t n_walk, con
   if (n_walk < 0) return MDET_E_ARG;
   if (n_walk == 0) return MDET_OK;
   if (!r || !psi_tilde || ld < n_walk || ld % 128 != 0 || ((uintptr_t)r & 15) != 0) return MDET_E_ARG;
-  const int64_t need = ((int64_t)P->n_det_sp[0] + 1) * ld;
-  if (need > (int64_t)MDET_NOALLOC_SCRATCH_DOUBLES) {  // beyond the static scratch
-    char msg[200];
+  // (n_det_up + 1) * ld doubles must fit the static scratch; ld is compared with the
+  // quotient first, so that a huge ld cannot overflow the product
+  const int64_t rows = (int64_t)P->n_det_sp[0] + 1;
+  if (ld > (int64_t)MDET_NOALLOC_SCRATCH_DOUBLES / rows) {
+    char msg[240];
     snprintf(msg, sizeof msg,
-             "(n_det_up + 1) * ld = %lld doubles exceeds the static scratch of %u doubles; use a smaller ld "
+             "(n_det_up + 1) * ld = %lld * %lld doubles exceeds the static scratch of %u doubles; use a smaller ld "
              "(fewer walkers per call) or mdet_evaluate",
-             (long long)need, MDET_NOALLOC_SCRATCH_DOUBLES);
+             (long long)rows, (long long)ld, MDET_NOALLOC_SCRATCH_DOUBLES);
     ctx_set_error(ctx, msg);
     return MDET_E_ARG;
   }
-  if (cudaSetDevice(device) != cudaSuccess) return MDET_E_CUDA;
-  double* scratch = nullptr;
-  if (scratch_address(device, &scratch) != cudaSuccess) return MDET_E_CUDA;
-  cudaStream_t st = (cudaStream_t)stream;
-  double* v = scratch;                                  // [n_det_up][ld]
-  double* psit = scratch + (int64_t)P->n_det_sp[0] * ld;  // [ld]
-  // the kernel accumulates with atomics: clear what this call uses
-  if (cudaMemsetAsync(scratch, 0, sizeof(double) * need, st) != cudaSuccess) return MDET_E_CUDA;
-  const double* r_up = r;
-  const double* r_dn = r + (int64_t)P->n_det_sp[0] * ld;
-  if (launch_spmm_rows_f64(*P, r_dn, r_up, v, psit, ld, n_walk, st) != cudaSuccess) return MDET_E_CUDA;
-  if (cudaMemcpyAsync(psi_tilde, psit, sizeof(double) * n_walk, cudaMemcpyDeviceToDevice, st) != cudaSuccess)
-    return MDET_E_CUDA;
-  return MDET_OK;
+  int prev = -1;
+  if (cudaGetDevice(&prev) != cudaSuccess || cudaSetDevice(device) != cudaSuccess) return MDET_E_CUDA;
+  const mdet_status s = psi_tilde_on_device(P, device, n_walk, r, ld, psi_tilde, (cudaStream_t)stream);
+  // the caller's current device is left as it was
+  if (cudaSetDevice(prev) != cudaSuccess && s == MDET_OK) return MDET_E_CUDA;
+  return s;
 }

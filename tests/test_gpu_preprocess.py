@@ -10,8 +10,10 @@ import time
 import numpy as np
 import pytest
 
+import oracle
 import paper_1510_00730_gb300 as pkg
 from paper_1510_00730_gb300 import synth
+from tests.parity import compare
 
 pytestmark = pytest.mark.gpu
 torch = pytest.importorskip("torch")
@@ -66,6 +68,31 @@ def test_device_preprocessing_shuffled_and_uneven():
         _same_state(host, dev)
         host.close()
         dev.close()
+
+
+TOL = {pkg.PRECISION_FP64: dict(tol_psi=1e-10, tol_der=1e-8), pkg.PRECISION_MIXED: dict(tol_psi=1e-9, tol_der=1e-6)}
+
+
+@pytest.mark.parametrize("prec", [pkg.PRECISION_FP64, pkg.PRECISION_MIXED])
+@pytest.mark.parametrize("name", ["oxygen_like_1k", "chlorine_like_100k"])
+def test_device_preprocessed_context_matches_oracle(name, prec):
+    """A context whose expansion went through the device preprocessing, with the
+    products in shuffled order (so the sort, the deduplication and the reference
+    search do real work), against the oracle's evaluation of the same expansion:
+    all walkers of the 1k workload, 32 sampled walkers of the 10^5 one (two
+    64-bit words per determinant)."""
+    wl = synth.WORKLOADS[name]()
+    perm = np.random.default_rng(5).permutation(len(wl.ci_coef))
+    wl.det_up, wl.det_dn, wl.ci_coef = wl.det_up[perm], wl.det_dn[perm], wl.ci_coef[perm]
+    ctx = pkg.Context.from_workload(wl, device=0, precision=prec, on_device=True)
+    out = ctx.evaluate(torch.from_numpy(np.ascontiguousarray(wl.R)).to("cuda:0"))
+    torch.cuda.synchronize()
+    got = {k: v.cpu().numpy() for k, v in out.items()}
+    idx = np.arange(wl.n_walk) if wl.n_walk <= 64 else np.random.default_rng(8).choice(wl.n_walk, 32, replace=False)
+    ref = oracle.evaluate(wl, R=wl.R[idx])
+    rep = compare({k: v[idx] for k, v in got.items()}, ref, **TOL[prec])
+    assert rep["ok"], rep
+    ctx.close()
 
 
 def test_device_preprocessing_rejects_invalid_input():
