@@ -147,8 +147,10 @@ def fp64_peak(device, clock_index=None):
     import paper_1510_00730_gb300 as pkg
     pkg.measure_fp64_rate(device, fma_per_thread=1 << 16, reps=2)  # warm the clocks
     with ClockSampler(clock_index if clock_index is not None else device) as clk:
-        tf, ms = pkg.measure_fp64_rate(device, fma_per_thread=1 << 18, reps=12)
-    return tf, ms, clk.summary()
+        tf, ms, mhz = pkg.measure_fp64_rate(device, fma_per_thread=1 << 19, reps=12)
+    summ = clk.summary()
+    summ["in_kernel_sm_mhz"] = mhz
+    return tf, ms, summ
 
 
 def run_reference(args):
@@ -182,16 +184,19 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+PROFILED_STEPS = 3  # untimed steps with the library's stage events, after the timed ones
+
+
 def _time_steps(ctx, Rdev, out, flush, stream, steps, warmup, dist, clock_index=None):
     """Warm up, then time `steps` evaluations with CUDA events (L2 flushed between
-    steps outside the events). Returns per-step ms, per-stage ms and clocks."""
+    steps outside the events, the library's own stage events off). Then a few more
+    steps with the stage events on, for the per-stage times and the timeline of the
+    last one. Returns per-step ms, per-stage ms, clocks and that timeline."""
     import torch
     for s in range(warmup):
         ctx.evaluate(Rdev[s % len(Rdev)], out=out)
     torch.cuda.synchronize()
-    ctx.set_profiling(True)
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
-    stage_ms = []
     if dist is not None:
         dist.barrier()
     torch.cuda.synchronize()
@@ -203,16 +208,24 @@ def _time_steps(ctx, Rdev, out, flush, stream, steps, warmup, dist, clock_index=
         ev[s][0].record(stream)
         ctx.evaluate(Rdev[s % len(Rdev)], out=out)
         ev[s][1].record(stream)
-        stage_ms.append(ctx.profile())  # waits for this step's events
     torch.cuda.synchronize()
     if clk:
         clk.__exit__(None, None, None)
     if dist is not None:
         dist.barrier()
-    ctx.set_profiling(False)
     step_ms = [a.elapsed_time(b) for a, b in ev]
-    kern = {k: statistics.mean(d[k] for d in stage_ms) for k in stage_ms[0]}
-    return step_ms, kern, (clk.summary() if clk else None)
+    ctx.set_profiling(True)
+    stage_ms, prof_ms = [], []
+    for s in range(PROFILED_STEPS):
+        flush.fill_(float(s))
+        ctx.evaluate(Rdev[s % len(Rdev)], out=out)
+        stage_ms.append(ctx.profile())  # waits for this step's events
+        prof_ms.append(ctx.timeline()["end"])
+    timeline = ctx.timeline()
+    timeline["profiled_step_ms"] = statistics.median(prof_ms)
+    ctx.set_profiling(False)
+    kern = {k: statistics.median(d[k] for d in stage_ms) for k in stage_ms[0]}
+    return step_ms, kern, (clk.summary() if clk else None), timeline
 
 
 def rank_batches(wl, rank, n_batches=4):
@@ -273,14 +286,14 @@ def run_ours(args):
 
     def timed(name, ctx, clock_index=None):
         out = ctx.alloc_outputs(W)
-        step_ms, kern, clocks = _time_steps(ctx, Rdev, out, flush, stream, args.steps, args.warmup, dist,
-                                            clock_index)
+        step_ms, kern, clocks, timeline = _time_steps(ctx, Rdev, out, flush, stream, args.steps, args.warmup,
+                                                      dist, clock_index)
         n_fb = int(((out["status"] & pkg.WS_FALLBACK) != 0).sum().item())
         ms = _max_over_ranks(statistics.mean(step_ms), dist, dev)
         n_esc = int(((out["status"] & pkg.WS_ESCALATED) != 0).sum().item())
         results[name] = dict(ms=ms, value=whole_job_value(W, world, ms), kern=kern, clocks=clocks, n_fb=n_fb,
                              n_esc=n_esc, chunks=ctx.last_chunks, kernels=ctx.last_kernels,
-                             fallback_tol=ctx.fallback[0])
+                             fallback_tol=ctx.fallback[0], timeline=timeline)
 
     for pname in [primary] + others:
         ctx = pkg.Context.from_workload(wl, device=local, precision=prec_of[pname])
@@ -306,7 +319,7 @@ def run_ours(args):
         c = ctxs["mixed"]
         c.set_tuning(contract_impl=1)
         out = c.alloc_outputs(W)
-        step_ms, kern, _ = _time_steps(c, Rdev, out, flush, stream, args.steps, args.warmup, dist)
+        step_ms, kern, _, _ = _time_steps(c, Rdev, out, flush, stream, args.steps, args.warmup, dist)
         ms = _max_over_ranks(statistics.mean(step_ms), dist, dev)
         df_contract = dict(value=whole_job_value(W, world, ms), ms_per_step=ms, kernels_ms=kern)
         c.set_tuning(contract_impl=0)
@@ -355,7 +368,8 @@ def run_ours(args):
                 "unit": "TFLOP/s", "frac": achieved / peak, "traffic": traffic,
                 "traffic_unit": "bytes per launch (ncu dram read + write)",
                 "peak_source": "measured in this run: FP64 FMA probe (mdet_measure_fp64_rate, 8 independent "
-                               "chains per thread, 32 warps per SM, fastest of 12 launches of %.1f ms)" % peak_ms,
+                               "accumulators per thread fed from L1-resident tables, 16 warps per SM, fastest of "
+                               "12 launches of %.1f ms)" % peak_ms,
                 "peak_clocks": peak_clocks, "peak_nominal": 1.25,
                 "flops_per_launch": flops_launch, "launch_ms": launch_ms}
 
@@ -373,6 +387,13 @@ def run_ours(args):
                     "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms},
             "gpu_launches": st_launches * args.steps,
             "kernels_ms": kern,
+            "kernels_ms_note": "stage times (library CUDA events, summed over walker chunks) from %d profiled steps "
+                               "after the timed ones; the timed steps run with those events off" % PROFILED_STEPS,
+            "timeline_ms": {"chunks": [{k: [round(v[0], 3), round(v[1], 3)] for k, v in c.items()}
+                                       for c in main["timeline"]["chunks"]],
+                            "refine": [round(x, 3) for x in main["timeline"]["refine"]],
+                            "end": round(main["timeline"]["end"], 3),
+                            "profiled_step_ms_median": round(main["timeline"]["profiled_step_ms"], 3)},
             "fallback_walkers": main["n_fb"], "escalated_walkers": main["n_esc"],
             "roofline": roofline}
     if df_contract is not None:

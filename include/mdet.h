@@ -318,14 +318,16 @@ mdet_status mdet_get_last_launches(const mdet_ctx* ctx, int32_t* n_chunks, int32
  * contraction (0: one warp per work item with one chunk, 4 blocks per SM with
  * several; otherwise a persistent grid of at most that many 128-thread blocks
  * whose warps draw work items from a counter), mo_impl the mixed-precision
- * orbital product (1, the default: the compensated FP32 dot product on the
- * CUDA cores, accurate relative to each term; 0: BF16 tensor cores on exact
- * digit products, accurate to about 2^-55 of the row and column maxima),
+ * orbital product (2, the default: exact BF16 digit products on the tcgen05
+ * tensor cores with TMEM accumulators, accurate to about 2^-55 of the row and
+ * column maxima, for at most 112 AOs and 128 MOs, beyond which it falls back to
+ * 1; 1: the compensated FP32 dot product on the CUDA cores, accurate relative to
+ * each term; 0: the same digit products on warp-level mma.sync),
  * contract_impl the CI contraction of the mixed path (0, the default: FP64;
  * 1: double-float pairs on the FP32 pipe with a compensated dot product, an
  * option outside the FP64 contraction of the method's precision plan).
  * Defaults: spmm_chunk 512, mo_ec 4 (mixed) or 6 (FP64), walker_chunks 0,
- * spmm_blocks 0, mo_impl 1, contract_impl 0.
+ * spmm_blocks 0, mo_impl 2, contract_impl 0.
  * best_ms and trials are filled by mdet_autotune (the fastest step time seen
  * and the configurations timed).
  */
@@ -405,6 +407,20 @@ mdet_status mdet_set_profiling(mdet_ctx* ctx, int enable);
 mdet_status mdet_get_profile(mdet_ctx* ctx, float* ms);
 
 /*
+ * Timeline of the last profiled evaluation (tracing; no counterpart in the
+ * paper): ms[k][i][0..1] (k < MDET_MAX_CHUNKS, i < MDET_N_STAGES) are the start
+ * and end of stage i of walker chunk k, then ms[2 * MDET_MAX_CHUNKS *
+ * MDET_N_STAGES + 0..2] the start and end of the stability refinement and the
+ * end of the evaluation, all in milliseconds after the evaluation's first event
+ * on the caller's stream. *n_chunks receives the chunks used; entries of
+ * unused chunks are zero. ms must hold 2 * MDET_MAX_CHUNKS * MDET_N_STAGES + 3
+ * floats. Waits for the evaluation's last event. MDET_E_STATE when profiling
+ * was off for the last evaluation.
+ */
+#define MDET_MAX_CHUNKS 8
+mdet_status mdet_get_timeline(mdet_ctx* ctx, int32_t* n_chunks, float* ms);
+
+/*
  * Psi~ = r_up . (C r_dn) per walker, without any device allocation.
  *
  * The paper has no counterpart: this entry point exists for callers that
@@ -438,16 +454,22 @@ mdet_status mdet_psi_tilde_noalloc(mdet_ctx* ctx, int64_t n_walk, const double* 
  * Measured FP64 FMA throughput of a device, the roofline denominator of the
  * FP64 kernels (the CI contraction of Sec. 2.4 is bound by this pipe). The paper
  * has no counterpart; it quotes CPU cycle counts instead (Sec. 5).
- * Every thread of a grid of 4 blocks of 256 threads per SM runs 8 independent
- * chains a <- fma(a, b, c) for fma_per_thread FMAs (a multiple of 32); one
- * warm-up launch, then `reps` timed launches (CUDA events), the fastest kept.
+ * Every thread of a grid of 4 blocks of 128 threads per SM keeps 8 independent
+ * accumulators a_j <- fma(c, x_j, a_j), with a new multiplier c and operands x_j
+ * read each step from small L1-resident tables (the pattern of a sparse
+ * contraction, which fills the pipe better than register-only FMA streams),
+ * for fma_per_thread FMAs (a multiple of 32); one warm-up launch, then `reps`
+ * timed launches (CUDA events), the fastest kept.
  *   tflops   out: 2 * FMAs / best time, in TFLOP/s
  *   best_ms  out (nullable): the fastest launch's time
- * Synchronous. Allocates a small output buffer for the chains' results and
- * frees it; the caller's current device is restored. MDET_E_ARG on a null
- * tflops, fma_per_thread < 32 or reps < 1; MDET_E_CUDA on any CUDA error.
+ *   sm_mhz   out (nullable): SM clock during that launch (clock64 cycles over
+ *            global-timer nanoseconds of one block)
+ * Synchronous. Allocates small tables and output buffers and frees them; the
+ * caller's current device is restored. MDET_E_ARG on a null tflops,
+ * fma_per_thread < 32 or reps < 1; MDET_E_CUDA on any CUDA error.
  */
-mdet_status mdet_measure_fp64_rate(int device, int64_t fma_per_thread, int reps, double* tflops, double* best_ms);
+mdet_status mdet_measure_fp64_rate(int device, int64_t fma_per_thread, int reps, double* tflops, double* best_ms,
+                                   double* sm_mhz);
 
 /*
  * Diagnostic of the double-float arithmetic used by the mixed path: for n

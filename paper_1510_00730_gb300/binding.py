@@ -100,13 +100,14 @@ def load_library(build_if_missing: bool = True):
     L.mdet_batch_destroy.argtypes = [vp]
     L.mdet_batch_destroy.restype = None
     L.mdet_get_profile.argtypes = [vp, vp]
-    L.mdet_measure_fp64_rate.argtypes = [i32, i64, i32, vp, vp]
+    L.mdet_get_timeline.argtypes = [vp, vp, vp]
+    L.mdet_measure_fp64_rate.argtypes = [i32, i64, i32, vp, vp, vp]
     for name in ("mdet_create", "mdet_set_system", "mdet_set_orbitals", "mdet_set_ci_expansion", "mdet_evaluate",
                  "mdet_evaluate_host", "mdet_get_ratios", "mdet_get_stats", "mdet_get_spin_dets",
                  "mdet_get_ci_matrix", "mdet_omega_sort", "mdet_truncate_norm", "mdet_sm_chain", "mdet_set_ci_expansion_device", "mdet_set_profiling", "mdet_get_profile",
                  "mdet_psi_tilde_noalloc", "mdet_set_walker_chunks", "mdet_get_last_launches", "mdet_set_escalation", "mdet_selftest_df32", "mdet_get_tuning",
                  "mdet_set_tuning", "mdet_autotune", "mdet_batch_evaluate", "mdet_batch_create", "mdet_batch_launch", "mdet_set_fallback", "mdet_get_fallback",
-                 "mdet_get_error_estimates", "mdet_measure_fp64_rate"):
+                 "mdet_get_error_estimates", "mdet_measure_fp64_rate", "mdet_get_timeline"):
         getattr(L, name).restype = i32
     # VMC moves and the learned proposal (include/mdet_vmc.h)
     u32p = C.POINTER(C.c_uint32)
@@ -225,13 +226,14 @@ def selftest_df32(x):
 
 
 def measure_fp64_rate(device=0, fma_per_thread=1 << 18, reps=10):
-    """Measured FP64 FMA throughput of a device: (TFLOP/s, fastest launch in ms)."""
+    """Measured FP64 FMA throughput of a device: (TFLOP/s, fastest launch in ms, SM MHz during it)."""
     L = load_library()
-    tf, ms = C.c_double(), C.c_double()
-    st = L.mdet_measure_fp64_rate(int(device), int(fma_per_thread), int(reps), C.byref(tf), C.byref(ms))
+    tf, ms, mhz = C.c_double(), C.c_double(), C.c_double()
+    st = L.mdet_measure_fp64_rate(int(device), int(fma_per_thread), int(reps), C.byref(tf), C.byref(ms),
+                                  C.byref(mhz))
     if st:
         raise MdetError(st, "mdet_measure_fp64_rate failed: %s" % L.mdet_status_string(st).decode())
-    return tf.value, ms.value
+    return tf.value, ms.value, mhz.value
 
 
 class Context:
@@ -409,10 +411,14 @@ class Context:
                     trials=t.trials, spmm_blocks=t.spmm_blocks, mo_impl=t.mo_impl,
                     contract_impl=t.contract_impl)
 
-    def set_tuning(self, spmm_chunk=512, mo_ec=None, walker_chunks=0, spmm_blocks=0, mo_impl=1, contract_impl=0):
-        """Tile shapes and kernel choices (mdet_set_tuning); mo_ec None keeps the context's current value."""
+    def set_tuning(self, spmm_chunk=512, mo_ec=None, walker_chunks=0, spmm_blocks=0, mo_impl=None, contract_impl=0):
+        """Tile shapes and kernel choices (mdet_set_tuning); mo_ec and mo_impl None keep the
+        context's current values."""
+        cur = self.tuning()
         if mo_ec is None:
-            mo_ec = self.tuning()["mo_ec"]
+            mo_ec = cur["mo_ec"]
+        if mo_impl is None:
+            mo_impl = cur["mo_impl"]
         t = _Tuning(spmm_chunk, mo_ec, walker_chunks, 0.0, 0, spmm_blocks, mo_impl, contract_impl)
         self._check(self._L.mdet_set_tuning(self._h, C.byref(t)), "mdet_set_tuning")
 
@@ -480,6 +486,20 @@ class Context:
         ms = (C.c_float * len(self.STAGES))()
         self._check(self._L.mdet_get_profile(self._h, ms), "mdet_get_profile")
         return dict(zip(self.STAGES, [float(x) for x in ms]))
+
+    MAX_CHUNKS = 8
+
+    def timeline(self):
+        """Start and end (ms after the evaluation's first event) of every stage of every
+        walker chunk of the last profiled evaluation, and of the refinement."""
+        n = C.c_int32()
+        ms = (C.c_float * (2 * self.MAX_CHUNKS * len(self.STAGES) + 3))()
+        self._check(self._L.mdet_get_timeline(self._h, C.byref(n), ms), "mdet_get_timeline")
+        per = 2 * len(self.STAGES)
+        chunks = [{s: (float(ms[k * per + 2 * i]), float(ms[k * per + 2 * i + 1])) for i, s in enumerate(self.STAGES)}
+                  for k in range(n.value)]
+        tail = ms[self.MAX_CHUNKS * per:]
+        return dict(chunks=chunks, refine=(float(tail[0]), float(tail[1])), end=float(tail[2]))
 
     # -- introspection (host only) -------------------------------------------
     def stats(self):

@@ -57,6 +57,38 @@ static __device__ __forceinline__ df32 df_from_bits(long long b) {
 
 static __device__ __forceinline__ double df_to_double(df32 a) { return (double)a.hi + (double)a.lo; }
 
+// hi + lo as an FP64 number with integer instructions only (no FP64-pipe work):
+// the significand of hi goes to bits 29..52 of a 64-bit integer, lo is aligned
+// to the same unit (its bits below the unit truncated), the two are added and
+// the sum is renormalised by at most one position. The result is within one FP64
+// ulp of hi + lo (|lo| <= ulp(hi)/2). A zero, subnormal or non-finite hi takes
+// the conversions above.
+static __device__ __forceinline__ double df_to_double_int(df32 a) {
+  const unsigned uh = __float_as_uint(a.hi), ul = __float_as_uint(a.lo);
+  const int eh = (int)((uh >> 23) & 0xffu);
+  if (eh == 0 || eh == 0xff) return df_to_double(a);
+  long long x = (long long)((uh & 0x7fffffu) | 0x800000u) << 29;
+  if (uh >> 31) x = -x;
+  const int el = (int)((ul >> 23) & 0xffu);
+  if ((ul & 0x7fffffffu) != 0u && el != 0xff) {
+    const long long ml = (long long)((ul & 0x7fffffu) | (el ? 0x800000u : 0u));
+    const int sh = (el ? el : 1) - eh + 29;  // <= 5 since |lo| <= ulp(hi) / 2
+    long long l = sh >= 0 ? (ml << sh) : (sh > -40 ? (ml >> -sh) : 0LL);
+    x += (ul >> 31) ? -l : l;
+  }
+  const unsigned long long sgn = x < 0 ? 0x8000000000000000ULL : 0ULL;
+  unsigned long long m = (unsigned long long)(x < 0 ? -x : x);
+  int e = eh + 896;  // FP64 biased exponent of a significand in [2^52, 2^53)
+  if (m >> 53) {
+    m >>= 1;
+    e++;
+  } else if (!(m >> 52)) {
+    m <<= 1;
+    e--;
+  }
+  return __longlong_as_double((long long)(sgn | ((unsigned long long)e << 52) | (m & 0xfffffffffffffULL)));
+}
+
 static __device__ __forceinline__ df32 operator+(df32 x, df32 y) {
   float sh, sl, th, tl;
   two_sum(x.hi, y.hi, sh, sl);

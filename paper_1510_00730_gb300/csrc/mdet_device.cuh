@@ -8,6 +8,16 @@
 
 namespace mdet {
 
+// |x| as an FP32 value, taken from the high word of the FP64 number (its
+// exponent and 20 leading mantissa bits, so within 2^-20 relative), clamped to
+// [0, FLT_MAX]: integer operations only, no FP64-to-FP32 conversion, for the
+// magnitude sums of the error estimate.
+static __device__ __forceinline__ float abs_f32_of(double x) {
+  int t = (__double2hiint(x) & 0x7fffffff) - (896 << 20);  // rebias the exponent from 1023 to 127
+  t = min(max(t, 0), 0x0fefffff);
+  return __int_as_float(t << 3);
+}
+
 static __device__ __forceinline__ double ipow_d(double x, int n) {
   double r = 1.0;
   for (int i = 0; i < n; i++) r *= x;

@@ -38,6 +38,15 @@ struct mdet_ctx {
   std::vector<double> csr_val;
   // device residency
   std::vector<void*> dev_problem_allocs;
+  // work items of the contraction per item size (built on first use outside any stream
+  // capture and kept with the problem, so that captured graphs keep valid pointers)
+  struct ItemSet {
+    int chunk;
+    const int2* d[2];
+    int n[2];
+    const uint8_t* split;
+  };
+  std::vector<ItemSet> item_sets;
   DevProblem P{};
   DevScratch S{};
   // escalation of mixed-precision walkers (FP64 re-evaluation of the flagged ones):
@@ -53,7 +62,7 @@ struct mdet_ctx {
   // FP32-pipe stages of the chunks run in order on fstream, the FP64 contractions on
   // the higher-priority stream cstream, so one chunk's contraction overlaps the
   // orbitals, tables and ratios of the next chunk and the epilogue of the previous one
-  static constexpr int kMaxChunks = 8;
+  static constexpr int kMaxChunks = MDET_MAX_CHUNKS;
   int n_chunks_cfg = 0;  // 0: automatic
   double fallback_tol = 0.0;  // set from the precision in mdet_create
   int fallback_cap = 256;  // set from the precision in mdet_create
@@ -62,7 +71,7 @@ struct mdet_ctx {
   std::vector<int32_t> csr_ptr, csc_ptr;
   int spmm_chunk = 512;  // tile shapes (mdet_set_tuning / mdet_autotune)
   int spmm_blocks = 0;
-  int mo_impl = 1;  // the compensated CUDA-core product (faster here than the tensor-core digits)
+  int mo_impl = 2;  // mixed orbitals: exact digit products on the tcgen05 tensor cores
   int mo_ec = 4;
   int contract_impl = 0;  // FP64 contraction (the double-float one is an option of the mixed path)
   mdet_tuning last_tune{};
@@ -78,9 +87,15 @@ struct mdet_ctx {
   // different streams, after waits)
   static constexpr int kEvPerChunk = 2 * MDET_N_STAGES;
   cudaEvent_t ev[kMaxChunks][kEvPerChunk] = {};
+  // timeline: the start of the evaluation, the refinement's start and end, the end of the evaluation
+  cudaEvent_t ev_origin = nullptr, ev_refine[2] = {}, ev_done = nullptr;
 };
 
 namespace {
+
+// contraction work items of escalated re-evaluations (a few hundred walkers): short, so that
+// the FP64 chains stay short
+constexpr int kEscalationChunk = 64;
 
 size_t final_smem_bytes_host(int n_up, int n_dn, int n_mo, bool mixed) {
   DevProblem P{};
@@ -210,7 +225,66 @@ mdet_status upload(mdet_ctx* c, const std::vector<T>& v, const T** out) {
 void free_problem(mdet_ctx* c) {
   for (void* p : c->dev_problem_allocs) cudaFree(p);
   c->dev_problem_allocs.clear();
+  c->item_sets.clear();
   c->P = DevProblem{};
+}
+
+// Work items of the contraction for item size `chunk`: consecutive whole segments (rows of the
+// row-major copy of C, columns of the column-major one) packed while they hold at most `chunk`
+// nonzeros, and segments longer than `chunk` cut into pieces of at most `chunk` nonzeros, so
+// that every item costs about the same. A whole segment belongs to one item, whose warp stores
+// its (segment, walker) sums; the pieces of a cut segment add theirs atomically (flagged by a
+// negative end), into entries the ratio kernel has cleared (`split`).
+mdet_status ensure_items(mdet_ctx* c, int chunk) {
+  for (const auto& s : c->item_sets)
+    if (s.chunk == chunk) return MDET_OK;
+  mdet_ctx::ItemSet set{};
+  set.chunk = chunk;
+  std::vector<uint8_t> split;
+  for (int o = 0; o < 2; o++) {
+    const std::vector<int32_t>& ptr = o ? c->csc_ptr : c->csr_ptr;
+    const int64_t nseg = (int64_t)ptr.size() - 1;
+    std::vector<int2> it;
+    int32_t b = nseg > 0 ? ptr[0] : 0;  // start of the item being packed
+    for (int64_t q = 0; q < nseg; q++) {
+      const int32_t s0 = ptr[q], s1 = ptr[q + 1];
+      if (s1 - s0 > chunk) {  // a long segment: close the open item, then cut this one
+        if (s0 > b) it.push_back(make_int2(b, s0));
+        for (int32_t p = s0; p < s1; p += chunk) it.push_back(make_int2(p, (int32_t)(std::min(p + chunk, s1) | 0x80000000u)));
+        split.push_back(1);
+        b = s1;
+        continue;
+      }
+      split.push_back(0);
+      if (s0 > b && s1 - b > chunk) {
+        it.push_back(make_int2(b, s0));
+        b = s0;
+      }
+    }
+    if (nseg > 0 && ptr[nseg] > b) it.push_back(make_int2(b, ptr[nseg]));
+    mdet_status s = upload(c, it, &set.d[o]);
+    if (s != MDET_OK) return s;
+    set.n[o] = (int)it.size();
+  }
+  mdet_status s = upload(c, split, &set.split);
+  if (s != MDET_OK) return s;
+  c->item_sets.push_back(set);
+  return MDET_OK;
+}
+
+// The problem with its contraction items switched to item size `chunk` (which must have been built).
+bool use_items(const mdet_ctx* c, DevProblem& P, int chunk) {
+  for (const auto& s : c->item_sets)
+    if (s.chunk == chunk) {
+      P.spmm_chunk = chunk;
+      for (int o = 0; o < 2; o++) {
+        P.items[o] = s.d[o];
+        P.n_items[o] = s.n[o];
+      }
+      P.split = s.split;
+      return true;
+    }
+  return false;
 }
 
 void free_arrays(DevScratch& S) {
@@ -308,6 +382,8 @@ mdet_status upload_problem(mdet_ctx* c) {
   P.spmm_blocks = c->spmm_blocks;
   P.mo_ec = c->mo_ec;
   P.mo_impl = c->mo_impl;
+  P.n_sm = c->n_sm;
+  P.phi_df = c->precision == MDET_PRECISION_MIXED;
   P.contract_impl = c->contract_impl;
   P.fallback_tol = c->fallback_tol;
   P.fallback_cap = c->fallback_cap;
@@ -383,6 +459,12 @@ mdet_status upload_problem(mdet_ctx* c) {
   UP(occ, P.ref_occ);
   UP(c->exc[0], P.exc[0]);
   UP(c->exc[1], P.exc[1]);
+  for (int sp = 0; sp < 2; sp++) {  // the context orders each spin's list by degree
+    int cnt[kMaxExc + 1] = {};
+    for (int d : c->degree[sp]) cnt[d]++;
+    P.deg_start[sp][0] = 0;
+    for (int d = 0; d <= kMaxExc; d++) P.deg_start[sp][d + 1] = P.deg_start[sp][d] + cnt[d];
+  }
   UP(c->csr_row, P.csr_row);
   UP(c->csr_col, P.csr_col);
   UP(c->csr_val, P.csr_val);
@@ -396,6 +478,9 @@ mdet_status upload_problem(mdet_ctx* c) {
     UP(a, P.csr_val_df);
     UP(b, P.csc_val_df);
   }
+  // contraction work items for the tuned size and for the short items of escalated re-evaluations
+  if ((s = ensure_items(c, c->spmm_chunk)) != MDET_OK || (s = ensure_items(c, kEscalationChunk)) != MDET_OK) return s;
+  use_items(c, P, c->spmm_chunk);
   // the sequential chain of Sec. 2.2: distinct determinants in the order of the key of Eq. 3,
   // each with the substitutions from its predecessor (holes and particles ascending, paired in order)
   for (int sp = 0; sp < 2; sp++) {
@@ -556,6 +641,7 @@ mdet_status refine(mdet_ctx* c, bool table, int64_t n_walk, const double* R, dou
   CUDA_TRY(c, launch_esc_gather(S.fb_list, cap, 3 * N, R, c->e_R, c->e_live, S.psia, E.psia, st));
   DevProblem Pe = P;  // the FP64 orbital kernel's own best electron block
   Pe.mo_ec = 6;
+  if (!use_items(c, Pe, kEscalationChunk)) return fail(c, MDET_E_STATE, "internal: escalation items missing");
   CUDA_TRY(c, launch_mo_f64(Pe, E, cap, c->e_R, st));
   const EscOut& o = c->eo;
   if (!table) {
@@ -566,11 +652,9 @@ mdet_status refine(mdet_ctx* c, bool table, int64_t n_walk, const double* R, dou
     return MDET_OK;
   }
   CUDA_TRY(c, launch_ref_tables(P, E, cap, false, st));
-  CUDA_TRY(c, launch_ratios_f64(P, E, cap, st));
-  CUDA_TRY(c, launch_zero_f64(P, E, cap, st));
-  // few walkers: short work items (64 nonzeros) keep the contraction's chains short, and the
-  // epilogue spreads each walker's determinants over 512 threads
-  Pe.spmm_chunk = 64;
+  CUDA_TRY(c, launch_ratios_f64(Pe, E, cap, st));  // clears the cut segments of Pe's items
+  // few walkers: short work items keep the contraction's chains short, and the epilogue
+  // spreads each walker's determinants over 512 threads
   Pe.spmm_blocks = 0;
   CUDA_TRY(c, launch_contract_f64(Pe, E, cap, st));
   CUDA_TRY(c, launch_final(P, E, cap, c->e_R, o.log_abs_psi, o.sign, o.grad, o.lap, o.e_local, o.status, false, st,
@@ -668,6 +752,8 @@ void mdet_destroy(mdet_ctx* c) {
     cudaDeviceSynchronize();
     free_scratch(c);
     free_problem(c);
+    for (cudaEvent_t e : {c->ev_origin, c->ev_refine[0], c->ev_refine[1], c->ev_done})
+      if (e) cudaEventDestroy(e);
     for (int k = 0; k < mdet_ctx::kMaxChunks; k++) {
       for (int i = 0; i < mdet_ctx::kEvPerChunk; i++)
         if (c->ev[k][i]) cudaEventDestroy(c->ev[k][i]);
@@ -1009,20 +1095,28 @@ mdet_status mdet_evaluate(mdet_ctx* c, int64_t n_walk, const double* R, double* 
     nch = c->n_chunks_cfg > 0 ? c->n_chunks_cfg : auto_chunks(c, n_walk);
     nch = (int)std::min<int64_t>(std::min<int64_t>(nch, tiles), mdet_ctx::kMaxChunks);
   }
-  if (prof)
+  if (prof) {
     for (int k = 0; k < nch; k++)
       for (int i = 0; i < mdet_ctx::kEvPerChunk; i++)
         if (!c->ev[k][i]) CUDA_TRY(c, cudaEventCreate(&c->ev[k][i]));
+    for (cudaEvent_t* e : {&c->ev_origin, &c->ev_refine[0], &c->ev_refine[1], &c->ev_done})
+      if (!*e) CUDA_TRY(c, cudaEventCreate(e));
+    CUDA_TRY(c, cudaEventRecord(c->ev_origin, (cudaStream_t)stream));
+  }
   const int64_t N = P.n_elec;
-  // chunk k covers tiles [t0, t1): an even split, except that with three chunks the first and
-  // last take a quarter each (their orbitals and tables, and the last epilogue, run alone, so
-  // shorter end chunks expose less: 32.9 against 33.5 ms per step at 8,192 walkers)
+  // chunk k covers tiles [t0, t1): the first and the last chunk weigh 1, the others 2 (their
+  // orbitals and tables, and the last epilogue, run with no contraction beside them, so
+  // shorter end chunks expose less); an even split when there are too few tiles
   auto chunk_range = [&](int k, int64_t* off, int64_t* n) {
     int64_t t0 = tiles * k / nch, t1 = tiles * (k + 1) / nch;
-    if (nch == 3 && tiles >= 4) {
-      const int64_t b[4] = {0, tiles / 4, tiles - tiles / 4, tiles};
-      t0 = b[k];
-      t1 = b[k + 1];
+    const int64_t units = nch >= 3 ? 2 * nch - 2 : nch;
+    if (nch >= 3 && tiles >= units) {
+      auto edge = [&](int q) -> int64_t {  // tiles before chunk q
+        const int64_t u = q == 0 ? 0 : (q >= nch ? units : 2 * q - 1);
+        return tiles * u / units;
+      };
+      t0 = edge(k);
+      t1 = edge(k + 1);
     }
     *off = t0 * kWalkerPad;
     *n = std::min<int64_t>(t1 * kWalkerPad, n_walk) - *off;
@@ -1066,6 +1160,9 @@ mdet_status mdet_evaluate(mdet_ctx* c, int64_t n_walk, const double* R, double* 
     CUDA_TRY(c, cudaEventRecord(c->fork, st));
     CUDA_TRY(c, cudaStreamWaitEvent(fs, c->fork, 0));
     CUDA_TRY(c, cudaStreamWaitEvent(xs, c->fork, 0));
+    // each chunk's accumulators are cleared on xs right before its contraction: the contraction
+    // adds into them with atomics, which then find the freshly cleared lines in L2 (clearing the
+    // whole batch up front measured 33.1 against 30.6 ms per step at 8,192 walkers)
     auto enqueue = [&](int k) -> mdet_status {
       mdet_status m;
       for (int i = MDET_STAGE_ORBITALS; i < MDET_STAGE_ZERO; i++)
@@ -1094,6 +1191,7 @@ mdet_status mdet_evaluate(mdet_ctx* c, int64_t n_walk, const double* R, double* 
   // fallback 5 (list, dets, scale, rows, out); the mixed refinement adds its list, gather,
   // FP64 orbitals and scatter, and either the mark or the 5 FP64 table kernels
   c->last_kernels = 6 * nch;
+  if (prof) CUDA_TRY(c, cudaEventRecord(c->ev_refine[0], st));
   if (mixed && c->E.fb && P.fallback_tol > 0.0) {
     const bool table = escalation_on(c);
     mdet_status es = refine(c, table, n_walk, R, log_abs_psi, sign, grad, lap, e_local, status, st);
@@ -1102,6 +1200,10 @@ mdet_status mdet_evaluate(mdet_ctx* c, int64_t n_walk, const double* R, double* 
   } else {
     CUDA_TRY(c, launch_fallback(P, c->S, n_walk, R, log_abs_psi, sign, grad, lap, e_local, status, st));
     if (P.fallback_tol > 0.0 && c->S.fb && P.n_up <= MDET_FALLBACK_MAX_SPIN) c->last_kernels += 5;
+  }
+  if (prof) {
+    CUDA_TRY(c, cudaEventRecord(c->ev_refine[1], st));
+    CUDA_TRY(c, cudaEventRecord(c->ev_done, st));
   }
   c->have_profile = prof;
   c->last_stream = st;
@@ -1241,6 +1343,23 @@ mdet_status mdet_get_profile(mdet_ctx* c, float* ms) {
   return MDET_OK;
 }
 
+mdet_status mdet_get_timeline(mdet_ctx* c, int32_t* n_chunks, float* ms) {
+  if (!c || !n_chunks || !ms) return MDET_E_ARG;
+  if (!c->have_profile) return fail(c, MDET_E_STATE, "no profiled evaluation yet");
+  CUDA_TRY(c, cudaSetDevice(c->device));
+  CUDA_TRY(c, cudaEventSynchronize(c->ev_done));
+  for (int i = 0; i < MDET_MAX_CHUNKS * MDET_N_STAGES * 2 + 3; i++) ms[i] = 0.0f;
+  *n_chunks = c->prof_chunks;
+  for (int k = 0; k < c->prof_chunks; k++)
+    for (int i = 0; i < mdet_ctx::kEvPerChunk; i++)
+      CUDA_TRY(c, cudaEventElapsedTime(&ms[k * mdet_ctx::kEvPerChunk + i], c->ev_origin, c->ev[k][i]));
+  float* tail = ms + MDET_MAX_CHUNKS * mdet_ctx::kEvPerChunk;
+  CUDA_TRY(c, cudaEventElapsedTime(&tail[0], c->ev_origin, c->ev_refine[0]));
+  CUDA_TRY(c, cudaEventElapsedTime(&tail[1], c->ev_origin, c->ev_refine[1]));
+  CUDA_TRY(c, cudaEventElapsedTime(&tail[2], c->ev_origin, c->ev_done));
+  return MDET_OK;
+}
+
 mdet_status mdet_selftest_df32(int device, int64_t n, const double* x, double* y_df, double* y_ref,
                                double* prod_df) {
   if (n < 1 || !x || !y_df || !y_ref || !prod_df || device < 0) return MDET_E_ARG;
@@ -1268,7 +1387,7 @@ mdet_status mdet_set_tuning(mdet_ctx* c, const mdet_tuning* t) {
   if (t->mo_ec != 4 && t->mo_ec != 6 && t->mo_ec != 8) return fail(c, MDET_E_ARG, "mo_ec must be 4, 6 or 8");
   if (t->walker_chunks < 0) return fail(c, MDET_E_ARG, "walker_chunks < 0");
   if (t->spmm_blocks < 0) return fail(c, MDET_E_ARG, "spmm_blocks < 0");
-  if (t->mo_impl != 0 && t->mo_impl != 1) return fail(c, MDET_E_ARG, "mo_impl must be 0 or 1");
+  if (t->mo_impl < 0 || t->mo_impl > 2) return fail(c, MDET_E_ARG, "mo_impl must be 0, 1 or 2");
   if (t->contract_impl != 0 && t->contract_impl != 1) return fail(c, MDET_E_ARG, "contract_impl must be 0 or 1");
   if (t->contract_impl != c->contract_impl) {
     c->contract_impl = t->contract_impl;
@@ -1279,6 +1398,12 @@ mdet_status mdet_set_tuning(mdet_ctx* c, const mdet_tuning* t) {
   c->P.mo_impl = t->mo_impl;
   c->spmm_blocks = t->spmm_blocks;
   c->P.spmm_blocks = t->spmm_blocks;
+  if (c->has_ci && c->device >= 0) {
+    CUDA_TRY(c, cudaSetDevice(c->device));
+    mdet_status s = ensure_items(c, t->spmm_chunk);
+    if (s != MDET_OK) return s;
+    use_items(c, c->P, t->spmm_chunk);
+  }
   c->spmm_chunk = t->spmm_chunk;
   c->mo_ec = t->mo_ec;
   c->n_chunks_cfg = std::min(t->walker_chunks, (int)mdet_ctx::kMaxChunks);

@@ -62,13 +62,22 @@ struct DevProblem {
   int64_t nnz;            // products
   const struct SmStep* sm_steps[2];  // the sequential chain of each spin (mdet_sm_chain)
   int sm_n[2];
-  int spmm_chunk;         // tuning: nonzeros per warp in the contraction
+  int spmm_chunk;         // tuning: nonzeros per work item of the contraction (whole segments)
+  const int2* items[2];   // work items of the contraction over the row-major (0) and column-major (1)
+  int n_items[2];         //   copies of C: nonzero ranges [x, y & 0x7fffffff) of whole segments, or one
+                          //   piece of a longer segment (y < 0: its sums are added atomically)
+  const uint8_t* split;   // [n_det_up + n_det_dn] 1 for a segment cut into pieces (its v or u entries are
+                          //   cleared before the contraction, by the ratio kernel)
   int spmm_blocks;        // tuning: grid of the contraction (0: one warp per work item)
   int contract_impl;      // tuning: contraction in FP64 (0) or double-float on the FP32 pipe (1, mixed only)
   const float2* csr_val_df;  // C values as double-float pairs, row-major and column-major orders
   const float2* csc_val_df;
   int mo_ec;              // tuning: electrons per CTA in the orbital kernels (4, 6 or 8)
-  int mo_impl;            // tuning: mixed orbitals on the tensor cores (0) or the compensated FP32 dot product (1)
+  int mo_impl;            // tuning: mixed orbitals by exact digit products on the tensor cores with tcgen05 (2),
+                          // with warp-level mma.sync (0), or the compensated FP32 dot product (1)
+  int n_sm;               // multiprocessors of the device (persistent grids)
+  int phi_df;             // the context's orbital array holds double-float pairs (mixed precision); the
+                          // FP64 re-evaluation scratch of a mixed context always holds FP64
   const uint16_t* B_dig;  // [7][tc_mp][tc_kp] BF16 digits of the MO coefficients (column-scaled)
   const int* B_exp;       // [n_mo] column exponents of B_dig
   int tc_kp, tc_mp, tc_sx;  // K padded to 16, M padded to 8, shared row stride of the AO digits
@@ -91,6 +100,7 @@ struct DevProblem {
   const float2* nuc_df;
   const int* ref_occ;      // [2][kMaxSpin] ascending occupied MOs of each reference
   const Exc* exc[2];       // [n_det_sp[s]] excitation records
+  int deg_start[2][kMaxExc + 2];  // first index of each excitation degree 0..kMaxExc (and the end) per spin
   // C over the distinct determinants, two orderings (Sec. 2.1, Sec. 2.4)
   const int* csr_row;      // [nnz] row (up index) of each entry, sorted by row then column
   const int* csr_col;      // [nnz]
@@ -137,6 +147,12 @@ cudaError_t launch_mo_f64(const DevProblem& P, const DevScratch& S, int64_t n_wa
                           const double* R, cudaStream_t st);
 cudaError_t launch_mo_mixed(const DevProblem& P, const DevScratch& S, int64_t n_walk,
                             const double* R, cudaStream_t st);
+// The mixed orbitals on the tcgen05 tensor cores (mdet_mo_umma.cu): supported for
+// at most 112 AOs and 128 MOs; launch_mo_mixed takes it when mo_impl is 2.
+bool mo_umma_supported(const DevProblem& P);
+size_t mo_umma_smem_bytes(const DevProblem& P);
+cudaError_t launch_mo_umma(const DevProblem& P, const DevScratch& S, int64_t n_walk, const double* R, int n_sm,
+                           cudaStream_t st);
 cudaError_t launch_ref_tables(const DevProblem& P, const DevScratch& S, int64_t n_walk, bool mixed,
                               cudaStream_t st);
 cudaError_t launch_ratios_f64(const DevProblem& P, const DevScratch& S, int64_t n_walk,

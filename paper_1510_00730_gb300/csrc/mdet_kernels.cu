@@ -94,11 +94,14 @@ __global__ void __launch_bounds__(128) k_mo_f64(DevProblem P, double* __restrict
 // spin s by Gauss-Jordan elimination with partial pivoting on [S | I] (rows
 // stay in their lanes; the pivot order is a permutation whose parity enters
 // the sign of the determinant). Then every thread computes T and g.
-// With MIXED the table is also written as double-float pairs for the FP32-pipe kernels.
+// MIXED: the orbitals arrive as double-float pairs; the elimination and log|D_ref|
+// stay FP64, while A is rounded to double-float pairs (written to Ainv as pairs),
+// and T = A Phi and g are formed in double-float on the FP32 pipe (written to Tdf
+// and, as pairs, to g); the FP64 table is not written.
 template <bool MIXED>
 __global__ void __launch_bounds__(64) k_ref(DevProblem P, DevScratch S) {
   __shared__ double aug[2][kMaxSpin][2 * kMaxSpin];
-  __shared__ int rowof[2][kMaxSpin];  // lane whose right half holds row a of A
+  __shared__ int rowof[2][kMaxSpin];  // pivot row of column a: the row of R that holds row a of A
   __shared__ int bad[2];
   __shared__ uint32_t stf[2];
   const int64_t w = blockIdx.x;
@@ -106,97 +109,193 @@ __global__ void __launch_bounds__(64) k_ref(DevProblem P, DevScratch S) {
   const int N = P.n_elec, M = P.n_mo;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   {
+    // Gauss-Jordan elimination on [S | I] with partial pivoting, lanes owning columns: for
+    // column j the pivot row p_j is the unused row of largest |S[i][j]|, row p_j is scaled
+    // by 1/pivot and column j is eliminated from every other row. Rows stay in place, so
+    // at the end the left half is the permutation L[p_j][j] = 1, the right half R = L S^-1,
+    // row a of A = S^-1 is row p_a of R, and det S = sgn(j -> p_j) * prod of the pivots.
+    // Pivot magnitudes are compared in FP32 from the FP64 bits, and |prod of pivots| is
+    // carried as mantissa * 2^exponent with one log at the end, so the FP64 pipe only sees
+    // the elimination itself (n FMAs per lane and column step), one reciprocal per pivot
+    // and one product per pivot.
     const int sp = warp;
     const int n = sp ? P.n_dn : P.n_up, e0 = sp ? P.n_up : 0;
     const int* occ = P.ref_occ + sp * kMaxSpin;
-    if (lane < n) {
-      for (int a = 0; a < n; a++) {
-        aug[sp][lane][a] = S.phi[((w * 5 + 0) * N + e0 + lane) * M + occ[a]];
-        aug[sp][lane][n + a] = (a == lane) ? 1.0 : 0.0;
-      }
-    }
-    __syncwarp();
-    // |S|_1: largest absolute column sum (lane c sums column c)
-    double cs = 0.0;
-    if (lane < n)
-      for (int i = 0; i < n; i++) cs += fabs(aug[sp][i][lane]);
-#pragma unroll
-    for (int off = 16; off; off >>= 1) cs = fmax(cs, __shfl_xor_sync(0xffffffffu, cs, off));
-    const double normS = cs;
-    __syncwarp();
-    bool used = false;
-    int step = -1;
-    double logd = 0.0, sgn = 1.0, pmax = 0.0, pmin = DBL_MAX;
-    int singular = 0;
-    for (int j = 0; j < n; j++) {
-      double v = (lane < n && !used) ? fabs(aug[sp][lane][j]) : -1.0;
-      int idx = lane;
-#pragma unroll
-      for (int off = 16; off; off >>= 1) {
-        const double ov = __shfl_xor_sync(0xffffffffu, v, off);
-        const int oi = __shfl_xor_sync(0xffffffffu, idx, off);
-        if (ov > v || (ov == v && oi < idx)) {
-          v = ov;
-          idx = oi;
+    for (int c = lane; c < 2 * n; c += 32)
+      for (int i = 0; i < n; i++) {
+        double v = (c - n == i) ? 1.0 : 0.0;
+        if (c < n) {
+          const size_t ix = ((w * 5 + 0) * N + e0 + i) * M + occ[c];
+          if (MIXED) {
+            const float2 f = reinterpret_cast<const float2*>(S.phi)[ix];
+            v = df_to_double_int(df32(f.x, f.y));
+          } else {
+            v = S.phi[ix];
+          }
         }
+        aug[sp][i][c] = v;
       }
-      if (!(v > 0.0)) {  // zero pivot (or NaN input): singular reference
+    __syncwarp();
+    // |S|_1: the largest column sum (FP32 magnitudes suffice for a conditioning estimate)
+    float cs = 0.0f;
+    for (int c = lane; c < n; c += 32) {
+      float s = 0.0f;
+      for (int i = 0; i < n; i++) s += abs_f32_of(aug[sp][i][c]);
+      cs = fmaxf(cs, s);
+    }
+#pragma unroll
+    for (int off = 16; off; off >>= 1) cs = fmaxf(cs, __shfl_xor_sync(0xffffffffu, cs, off));
+    const float normS = cs;
+    uint32_t used = 0u;
+    double pm = 1.0;  // |prod of pivots| = pm 2^pe, pm in [0.5, 1)
+    int pe = 0, negs = 0, singular = 0;
+    float pmax = 0.0f, pmin = FLT_MAX;
+    for (int j = 0; j < n; j++) {
+      int p = -1;
+      if (lane == (j & 31)) {
+        float best = 0.0f;
+        for (int i = 0; i < n; i++) {  // integer and FP32 tests only
+          const long long xb = __double_as_longlong(aug[sp][i][j]);
+          const float v = abs_f32_of(aug[sp][i][j]);
+          if (!((used >> i) & 1u) && (v > best || (p < 0 && (xb << 1) != 0))) {
+            best = v;
+            p = i;
+          }
+        }
+        if (p >= 0 && ((__double_as_longlong(aug[sp][p][j]) >> 52) & 0x7ff) == 0x7ff) p = -1;  // Inf or NaN
+      }
+      p = __shfl_sync(0xffffffffu, p, j & 31);
+      if (p < 0) {  // no nonzero pivot (or a NaN input): singular reference
         singular = 1;
         break;
       }
-      const int p = idx;
+      used |= 1u << p;
+      if (lane == 0) rowof[sp][j] = p;
       const double piv = aug[sp][p][j];
-      logd += log(fabs(piv));
-      if (piv < 0) sgn = -sgn;
-      pmax = fmax(pmax, fabs(piv));
-      pmin = fmin(pmin, fabs(piv));
+      {
+        const long long b = __double_as_longlong(piv);
+        negs += (int)((unsigned long long)b >> 63);
+        const int ex = (int)((b >> 52) & 0x7ff);
+        // |piv| = m 2^(ex - 1022), m in [0.5, 1) (normal pivots; a subnormal one counts as tiny)
+        const double m = __longlong_as_double((b & 0x000fffffffffffffLL) | 0x3fe0000000000000LL);
+        pm *= m;
+        pe += ex - 1022;
+        const long long bm = __double_as_longlong(pm);  // back into [0.5, 1)
+        pe += (int)((bm >> 52) & 0x7ff) - 1022;
+        pm = __longlong_as_double((bm & 0x000fffffffffffffLL) | 0x3fe0000000000000LL);
+        const float a = abs_f32_of(piv);
+        pmax = fmaxf(pmax, a);
+        pmin = fminf(pmin, a);
+      }
+      const double inv = 1.0 / piv;
       __syncwarp();
-      if (lane == p) {
-        used = true;
-        step = j;
-        const double inv = 1.0 / piv;
-        for (int c = 0; c < 2 * n; c++) aug[sp][p][c] *= inv;
+      for (int c = lane; c < 2 * n; c += 32) {
+        if (c == j) continue;
+        const double apc = aug[sp][p][c] * inv;
+        aug[sp][p][c] = apc;
+        for (int i = 0; i < n; i++)
+          if (i != p) aug[sp][i][c] = fma(-aug[sp][i][j], apc, aug[sp][i][c]);
       }
       __syncwarp();
-      if (lane < n && lane != p) {
-        const double f = aug[sp][lane][j];
-        if (f != 0.0)
-          for (int c = 0; c < 2 * n; c++) aug[sp][lane][c] = fma(-f, aug[sp][p][c], aug[sp][lane][c]);
-      }
+      if (lane == (j & 31))
+        for (int i = 0; i < n; i++) aug[sp][i][j] = (i == p) ? 1.0 : 0.0;
       __syncwarp();
     }
-    // parity of the pivot order: lane i was the pivot of step step(i)
+    // sign: pivots' signs times the parity of j -> p_j (inversions counted by lane j)
     int inv_cnt = 0;
-    for (int q = 0; q < 32; q++) {
-      const int sq = __shfl_sync(0xffffffffu, step, q);
-      if (lane < n && q > lane && q < n && sq < step) inv_cnt++;
-    }
+    if (!singular)
+      for (int j = lane; j < n; j += 32)
+        for (int k = j + 1; k < n; k++) inv_cnt += rowof[sp][k] < rowof[sp][j];
 #pragma unroll
     for (int off = 16; off; off >>= 1) inv_cnt += __shfl_xor_sync(0xffffffffu, inv_cnt, off);
-    if (inv_cnt & 1) sgn = -sgn;
-    if (lane < n && !singular) rowof[sp][step] = lane;
-    // |A|_1 (the rows of A sit permuted across lanes; column sums do not care)
-    double ca = 0.0;
-    if (lane < n && !singular)
-      for (int i = 0; i < n; i++) ca += fabs(aug[sp][i][n + lane]);
+    const double sgn = ((negs + inv_cnt) & 1) ? -1.0 : 1.0;
+    // |A|_1: column sums of R (a row permutation of A)
+    float ca = 0.0f;
+    if (!singular)
+      for (int c = lane; c < n; c += 32) {
+        float s = 0.0f;
+        for (int i = 0; i < n; i++) s += abs_f32_of(aug[sp][i][n + c]);
+        ca = fmaxf(ca, s);
+      }
 #pragma unroll
-    for (int off = 16; off; off >>= 1) ca = fmax(ca, __shfl_xor_sync(0xffffffffu, ca, off));
-    const double kappa1 = normS * ca;
+    for (int off = 16; off; off >>= 1) ca = fmaxf(ca, __shfl_xor_sync(0xffffffffu, ca, off));
+    const double kappa1 = (double)normS * (double)ca;
     if (lane == 0) {
       bad[sp] = singular;
-      S.ld0[w * 2 + sp] = singular ? -INFINITY : logd;
+      S.ld0[w * 2 + sp] = singular ? -INFINITY : log(pm) + pe * 0.69314718055994530942;
       S.sg0[w * 2 + sp] = singular ? 0.0 : sgn;
       uint32_t st = singular ? MDET_WS_REF_SINGULAR : 0u;
-      if (!singular && pmin < 1e-13 * pmax) st |= MDET_WS_REF_ILLCOND;
+      if (!singular && pmin < 1e-13f * pmax) st |= MDET_WS_REF_ILLCOND;
       S.kap[w * 2 + sp] = singular ? INFINITY : kappa1;
       if (P.fallback_tol > 0.0 && P.n_up <= MDET_FALLBACK_MAX_SPIN && singular) st |= MDET_WS_FALLBACK;
       stf[sp] = st;
     }
   }
   __syncthreads();
-  if (threadIdx.x == 0) S.wstat[w] = stf[0] | stf[1];
-  // A to global, T = A Phi (walker-minor), g
+  if (threadIdx.x == 0) {
+    S.wstat[w] = stf[0] | stf[1];
+    // the contraction accumulates Psi~ and, except for an escalated re-evaluation (live count
+    // set: it keeps the magnitude sum of the evaluation that flagged it), sum |c r r|
+    S.psit[w] = 0.0;
+    if (!S.live) S.psia[w] = 0.0f;
+  }
   const int nu = P.n_up, nd = P.n_dn;
+  if (MIXED) {
+    // each row of A (the right half of its lane's row) as double-float pairs in the left half,
+    // which the elimination no longer needs
+    const int t = threadIdx.x, sp = t >> 5, lane = t & 31;
+    const int n = sp ? nd : nu;
+    if (lane < n && !bad[sp]) {
+      float2* dst = reinterpret_cast<float2*>(&aug[sp][lane][0]);
+      for (int i = 0; i < n; i++) {
+        const df32 d = df_from_bits(__double_as_longlong(aug[sp][lane][n + i]));
+        dst[i] = make_float2(d.hi, d.lo);
+      }
+    }
+    __syncthreads();
+    auto Adf = [&](int sp, int a, int i) {
+      const float2 v = reinterpret_cast<const float2*>(&aug[sp][rowof[sp][a]][0])[i];
+      return df32(v.x, v.y);
+    };
+    const float2* phi2 = reinterpret_cast<const float2*>(S.phi);
+    float2* Ag2 = reinterpret_cast<float2*>(S.Ainv) + w * (nu * nu + nd * nd);
+    const float2 fnan = make_float2(__int_as_float(0x7fc00000), 0.0f);
+    for (int t2 = threadIdx.x; t2 < nu * nu + nd * nd; t2 += blockDim.x) {
+      const int sp2 = t2 < nu * nu ? 0 : 1;
+      const int n2 = sp2 ? nd : nu;
+      const int tt = sp2 ? t2 - nu * nu : t2;
+      const df32 v = bad[sp2] ? df32(0.0f, 0.0f) : Adf(sp2, tt / n2, tt % n2);
+      Ag2[t2] = bad[sp2] ? fnan : make_float2(v.hi, v.lo);
+    }
+    for (int t2 = threadIdx.x; t2 < N * M; t2 += blockDim.x) {
+      const int row = t2 / M, m = t2 - row * M;
+      const int sp2 = row < nu ? 0 : 1;
+      const int n2 = sp2 ? nd : nu, e0 = sp2 ? nu : 0, a = row - e0;
+      df32 acc(0.0f, 0.0f);
+      if (!bad[sp2])
+        for (int i = 0; i < n2; i++) {
+          const float2 pv = phi2[((w * 5 + 0) * N + e0 + i) * M + m];
+          acc = acc + Adf(sp2, a, i) * df32(pv.x, pv.y);
+        }
+      S.Tdf[(size_t)t2 * S.wp + w] = bad[sp2] ? fnan : make_float2(acc.hi, acc.lo);
+    }
+    float2* g2 = reinterpret_cast<float2*>(S.g);
+    for (int t2 = threadIdx.x; t2 < N * 4; t2 += blockDim.x) {
+      const int e = t2 >> 2, mu = t2 & 3;
+      const int sp2 = e < nu ? 0 : 1;
+      const int n2 = sp2 ? nd : nu, e0 = sp2 ? nu : 0, i = e - e0;
+      const int* occ = P.ref_occ + sp2 * kMaxSpin;
+      df32 acc(0.0f, 0.0f);
+      if (!bad[sp2])
+        for (int a = 0; a < n2; a++) {
+          const float2 pv = phi2[((w * 5 + 1 + mu) * N + e) * M + occ[a]];
+          acc = acc + Adf(sp2, a, i) * df32(pv.x, pv.y);
+        }
+      g2[(w * N + e) * 4 + mu] = bad[sp2] ? fnan : make_float2(acc.hi, acc.lo);
+    }
+    return;
+  }
+  // A to global, T = A Phi (walker-minor), g
   // A[a][i] of spin sp
   auto Aat = [&](int sp, int a, int i) { return aug[sp][rowof[sp][a]][(sp ? nd : nu) + i]; };
   double* Ag = S.Ainv + w * (nu * nu + nd * nd);
@@ -215,10 +314,6 @@ __global__ void __launch_bounds__(64) k_ref(DevProblem P, DevScratch S) {
       for (int i = 0; i < n; i++) acc = fma(Aat(sp, a, i), S.phi[((w * 5 + 0) * N + e0 + i) * M + m], acc);
     if (bad[sp]) acc = NAN;
     S.T[(size_t)t * S.wp + w] = acc;
-    if (MIXED) {
-      const df32 d = df_from_double(acc);
-      S.Tdf[(size_t)t * S.wp + w] = make_float2(d.hi, d.lo);
-    }
   }
   for (int t = threadIdx.x; t < N * 4; t += blockDim.x) {
     const int e = t >> 2, mu = t & 3;
@@ -256,6 +351,7 @@ __global__ void __launch_bounds__(128) k_ratio_f64(DevProblem P, DevScratch S) {
         m[a][b] = (a < e.k && b < e.k) ? T[((size_t)e.h[a] * M + e.p[b]) * wp + w] : 0.0;
     const double d = small_det(e.k, m);
     S.r[(size_t)t * wp + w] = e.eps < 0 ? -d : d;
+    if (P.split[t]) S.vu[w * ntot + t] = 0.0;  // the contraction adds the pieces of a cut segment
   }
 }
 
@@ -309,53 +405,54 @@ __global__ void __launch_bounds__(256) k_spmm_f64(const int* __restrict__ seg, c
   flush(cur);
 }
 
-// |x| as an FP32 value, taken from the high word of the FP64 number (its
-// exponent and 20 leading mantissa bits, so within 2^-20 relative), clamped to
-// [0, FLT_MAX]: integer operations only, no FP64-to-FP32 conversion, for the
-// magnitude sums of the error estimate.
-__device__ __forceinline__ float abs_f32_of(double x) {
-  int t = (__double2hiint(x) & 0x7fffffff) - (896 << 20);  // rebias the exponent from 1023 to 127
-  t = min(max(t, 0), 0x0fefffff);
-  return __int_as_float(t << 3);
-}
 
 // ---------------------------------------------------------------------------
-// K5 (form used by mdet_evaluate): the same segmented product with 8 walkers
-// per lane (256 per warp). Work items are (chunk of nonzeros, group of 256
-// walkers), chunks fastest so that warps in flight share the same walker
-// columns of x in L2. Output y is walker-major: y[w * ldy + seg_off + seg], the
-// layout the epilogue reads.
-// QUEUE false: one item per warp of a full grid. QUEUE true: a persistent grid
-// whose warps take the next item from the counter *queue (zeroed before the
-// launch), so blocks that become resident late, while kernels of other streams
-// hold part of the SMs, simply take fewer items.
-// ABS (with rdot): psia[w] += |rdot[seg][w]| * sum |c| |x| in FP32, so that
-// psia = sum_ij |c_ij| |r_up,i| |r_dn,j|, the magnitude sum behind Psi~ (its
-// ratio to |Psi~| is the conditioning of the CI sum, used by the error estimate).
-// WPL walkers per lane (8, or 4 for the few walkers of an escalated re-evaluation,
-// where a 256-walker group would be mostly padding).
+// K5 (form used by mdet_evaluate): y[seg][w] = sum over segment seg of val_k x[gidx_k][w]
+// (v = C r_dn over the rows of the row-major copy of C, u = C^T r_up over the columns of
+// the column-major one, Sec. 2.4), x walker-minor with leading dimension wp, y walker-major
+// (y[w * ldy + seg_off + seg], the layout the epilogue reads contiguously). A work
+// item (`items`, built on the host) is a run of whole segments holding at most `spmm_chunk`
+// nonzeros, or one piece of at most that many of a longer segment, for one group of 32 WPL
+// walkers, WPL per lane; the nonzero's value and index are uniform across the warp. The sums
+// of a whole segment come from exactly one warp and are stored (no clearing, no atomics;
+// an item's consecutive segments fill whole sectors of each walker's row); the pieces of a
+// cut segment add theirs atomically into entries the ratio kernel cleared. Items run fastest
+// within a walker group, so the warps in flight share that group's columns of x in L2.
+// QUEUE false: one work item per warp of a full grid. QUEUE true: a persistent grid whose
+// warps take the next work item from the counter *queue (zeroed before the launch), so
+// blocks that become resident late, while kernels of other streams hold part of the SMs,
+// simply take fewer items.
+// With rdot: psit[w] += rdot[seg][w] y[seg][w] per segment (Psi~ = r_up . v; atomics on the
+// small, L2-resident psit, which keep the registers of a grid that shares every SM with the
+// other stages low). ABS: psia[w] += |rdot[seg][w]| sum |c| |x| in FP32 likewise, so that
+// psia = sum_ij |c_ij| |r_up,i| |r_dn,j|, the magnitude sum behind Psi~
+// (its ratio to |Psi~| is the conditioning of the CI sum, used by the error estimate).
+// WPL walkers per lane (8, or 4 for the few walkers of an escalated re-evaluation, where a
+// 256-walker group would be mostly padding); walker groups at or beyond the live count are skipped.
 template <bool QUEUE, bool ABS, int WPL>
-__global__ void __launch_bounds__(128) k_spmm_wm(const int* __restrict__ seg, const int* __restrict__ gidx,
-                                                 const double* __restrict__ val, int64_t nnz, int chunk,
-                                                 int64_t n_chunks, int64_t n_groups,
-                                                 const double* __restrict__ x, int64_t wp,
-                                                 double* __restrict__ y, int64_t ldy, int seg_off,
-                                                 const double* __restrict__ rdot, double* __restrict__ psit,
-                                                 float* __restrict__ psia, unsigned long long* __restrict__ queue,
-                                                 const int* __restrict__ live) {
-  constexpr int G = 32 * WPL;  // walkers per work item
+__global__ void __launch_bounds__(128) k_spmm_seg(const int* __restrict__ seg, const int* __restrict__ gidx,
+                                                  const double* __restrict__ val, const int2* __restrict__ items,
+                                                  int n_items, int64_t n_groups, const double* __restrict__ x,
+                                                  int64_t wp, double* __restrict__ y, int64_t ldy, int seg_off,
+                                                  const double* __restrict__ rdot, double* __restrict__ psit,
+                                                  float* __restrict__ psia, unsigned long long* __restrict__ queue,
+                                                  const int* __restrict__ live) {
+  constexpr int G = 32 * WPL;
   const int lane = threadIdx.x & 31;
-  // walker groups at or beyond the live count (escalated re-evaluations) are skipped
-  const int64_t n_items = n_chunks * (live ? min(n_groups, (int64_t)(*live + G - 1) / G) : n_groups);
+  const int64_t ng = live ? min(n_groups, (int64_t)(*live + G - 1) / G) : n_groups;
+  const int64_t n_work = (int64_t)n_items * ng;
   auto next_item = [&]() -> int64_t {
     unsigned long long t = 0;
     if (lane == 0) t = atomicAdd(queue, 1ULL);
     return (int64_t)__shfl_sync(0xffffffffu, t, 0);
   };
   const int64_t first = QUEUE ? next_item() : (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-  for (int64_t item = first; item < n_items; item = QUEUE ? next_item() : n_items) {
-    const int64_t ch = item % n_chunks, grp = item / n_chunks;
-    const int64_t k0 = ch * chunk, k1 = min(k0 + (int64_t)chunk, nnz);
+  for (int64_t q = first; q < n_work; q = QUEUE ? next_item() : n_work) {
+    const int it = (int)(q % n_items);
+    const int64_t grp = q / n_items;
+    const int2 r0 = __ldg(items + it);
+    const int2 r = make_int2(r0.x, r0.y & 0x7fffffff);
+    const bool piece = r0.y < 0;  // one piece of a longer segment: its sums are added, not stored
     const int64_t wb = grp * G + lane * WPL;
     double a[WPL];
     float aa[WPL];  // ABS: sum |c| |x| of the segment
@@ -364,20 +461,31 @@ __global__ void __launch_bounds__(128) k_spmm_wm(const int* __restrict__ seg, co
       a[j] = 0.0;
       aa[j] = 0.0f;
     }
-    int cur = __ldg(seg + k0);
+    int cur = __ldg(seg + r.x);
     auto flush = [&](int sg) {
+      double* yr = y + wb * ldy + seg_off + sg;
+      if (piece) {
 #pragma unroll
-      for (int j = 0; j < WPL; j++) atomicAdd(y + (wb + j) * ldy + seg_off + sg, a[j]);
+        for (int j = 0; j < WPL; j++) atomicAdd(yr + j * ldy, a[j]);
+      } else {
+#pragma unroll
+        for (int j = 0; j < WPL; j++) yr[j * ldy] = a[j];
+      }
       if (rdot) {
-        const double* rp = rdot + (size_t)sg * wp + wb;
+        const double2* rp = reinterpret_cast<const double2*>(rdot + (size_t)sg * wp + wb);
 #pragma unroll
-        for (int j = 0; j < WPL; j++) {
-          atomicAdd(psit + wb + j, rp[j] * a[j]);
-          if (ABS) atomicAdd(psia + wb + j, abs_f32_of(rp[j]) * aa[j]);
+        for (int h = 0; h < WPL / 2; h++) {
+          const double2 t = __ldg(rp + h);
+          atomicAdd(psit + wb + 2 * h, t.x * a[2 * h]);
+          atomicAdd(psit + wb + 2 * h + 1, t.y * a[2 * h + 1]);
+          if (ABS) {
+            atomicAdd(psia + wb + 2 * h, abs_f32_of(t.x) * aa[2 * h]);
+            atomicAdd(psia + wb + 2 * h + 1, abs_f32_of(t.y) * aa[2 * h + 1]);
+          }
         }
       }
     };
-    for (int64_t k = k0; k < k1; k++) {
+    for (int k = r.x; k < r.y; k++) {
       const int sg = __ldg(seg + k);
       if (sg != cur) {
         flush(cur);
@@ -415,38 +523,50 @@ __global__ void __launch_bounds__(128) k_spmm_wm(const int* __restrict__ seg, co
 // Oishi (TwoProd of the leading words, TwoSum into the running sum, cross terms
 // and all rounding errors into a second word), about 13 FP32 instructions per
 // nonzero instead of one FP64 FMA at 1/54 of the FP32 rate. Segment sums are
-// converted to FP64 at the flush.
+// converted to FP64 when stored; work items, layouts and the Psi~ sums as above
+// (8 walkers per lane, full grid).
 __global__ void __launch_bounds__(128) k_spmm_df(const int* __restrict__ seg, const int* __restrict__ gidx,
-                                                 const float2* __restrict__ val, int64_t nnz, int chunk,
-                                                 int64_t n_chunks, int64_t n_groups,
-                                                 const float2* __restrict__ x, int64_t wp,
-                                                 double* __restrict__ y, int64_t ldy, int seg_off,
+                                                 const float2* __restrict__ val, const int2* __restrict__ items,
+                                                 int n_items, int64_t n_groups, const float2* __restrict__ x,
+                                                 int64_t wp, double* __restrict__ y, int64_t ldy, int seg_off,
                                                  const double* __restrict__ rdot, double* __restrict__ psit,
                                                  float* __restrict__ psia) {
   const int lane = threadIdx.x & 31;
   const int64_t nwarps = (int64_t)gridDim.x * (blockDim.x >> 5);
-  for (int64_t item = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); item < n_chunks * n_groups;
-       item += nwarps) {
-    const int64_t ch = item % n_chunks, grp = item / n_chunks;
-    const int64_t k0 = ch * chunk, k1 = min(k0 + (int64_t)chunk, nnz);
+  for (int64_t q = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); q < (int64_t)n_items * n_groups;
+       q += nwarps) {
+    const int it = (int)(q % n_items);
+    const int64_t grp = q / n_items;
+    const int2 r0 = __ldg(items + it);
+    const int2 r = make_int2(r0.x, r0.y & 0x7fffffff);
+    const bool piece = r0.y < 0;
     const int64_t wb = grp * 256 + lane * 8;
     float s[8], e[8], aa[8];
 #pragma unroll
     for (int j = 0; j < 8; j++) s[j] = e[j] = aa[j] = 0.0f;
-    int cur = __ldg(seg + k0);
+    int cur = __ldg(seg + r.x);
     auto flush = [&](int sg) {
-      const double* rp = rdot ? rdot + (size_t)sg * wp + wb : nullptr;
+      double v[8];
 #pragma unroll
-      for (int j = 0; j < 8; j++) {
-        const double v = (double)s[j] + (double)e[j];
-        atomicAdd(y + (wb + j) * ldy + seg_off + sg, v);
-        if (rp) {
-          atomicAdd(psit + wb + j, rp[j] * v);
+      for (int j = 0; j < 8; j++) v[j] = (double)s[j] + (double)e[j];
+      double* yr = y + wb * ldy + seg_off + sg;
+      if (piece) {
+#pragma unroll
+        for (int j = 0; j < 8; j++) atomicAdd(yr + j * ldy, v[j]);
+      } else {
+#pragma unroll
+        for (int j = 0; j < 8; j++) yr[j * ldy] = v[j];
+      }
+      if (rdot) {
+        const double* rp = rdot + (size_t)sg * wp + wb;
+#pragma unroll
+        for (int j = 0; j < 8; j++) {
+          atomicAdd(psit + wb + j, rp[j] * v[j]);
           atomicAdd(psia + wb + j, abs_f32_of(rp[j]) * aa[j]);
         }
       }
     };
-    for (int64_t k = k0; k < k1; k++) {
+    for (int k = r.x; k < r.y; k++) {
       const int sg = __ldg(seg + k);
       if (sg != cur) {
         flush(cur);
@@ -458,12 +578,12 @@ __global__ void __launch_bounds__(128) k_spmm_df(const int* __restrict__ seg, co
       const float4* xp = reinterpret_cast<const float4*>(x + (size_t)__ldg(gidx + k) * wp + wb);
       float xs[16];
 #pragma unroll
-      for (int q = 0; q < 4; q++) {
-        const float4 v = __ldg(xp + q);
-        xs[4 * q] = v.x;
-        xs[4 * q + 1] = v.y;
-        xs[4 * q + 2] = v.z;
-        xs[4 * q + 3] = v.w;
+      for (int q4 = 0; q4 < 4; q4++) {
+        const float4 v = __ldg(xp + q4);
+        xs[4 * q4] = v.x;
+        xs[4 * q4 + 1] = v.y;
+        xs[4 * q4 + 2] = v.z;
+        xs[4 * q4 + 3] = v.w;
       }
 #pragma unroll
       for (int j = 0; j < 8; j++) {
@@ -482,6 +602,37 @@ __global__ void __launch_bounds__(128) k_spmm_df(const int* __restrict__ seg, co
   }
 }
 
+// Cofactors of one determinant of degree K (compile time) in double-float,
+// weighted by w (the FP64 bits of eps_I w_I), added into W: each addition is an
+// FP32 shared atomic on the high word whose returned old value gives, by
+// TwoSum, the rounding error of that addition, which goes with the low word
+// into a second atomic.
+template <int K>
+__device__ __forceinline__ void scatter_cof_df(const Exc& e, long long wb, const float2* __restrict__ Tdf, int toff,
+                                               int Mt, int off, int M, float* Whi, float* Wlo) {
+  df32 m[4][4], cof[4][4];
+#pragma unroll
+  for (int a = 0; a < 4; a++)
+#pragma unroll
+    for (int b = 0; b < 4; b++) {
+      const float2 v = (a < K && b < K) ? Tdf[toff + e.h[a] * Mt + e.p[b]] : make_float2(0.f, 0.f);
+      m[a][b] = df32(v.x, v.y);
+    }
+  small_cof(K, m, cof);
+  const df32 wd = df_from_bits(wb);
+#pragma unroll
+  for (int a = 0; a < K; a++)
+#pragma unroll
+    for (int b = 0; b < K; b++) {
+      const df32 x = cof[a][b] * wd;
+      const int slot = off + e.h[a] * M + e.p[b];
+      const float old = atomicAdd(Whi + slot, x.hi);
+      float s_, err;
+      two_sum(old, x.hi, s_, err);
+      atomicAdd(Wlo + slot, __fadd_rn(err, x.lo));
+    }
+}
+
 // ---------------------------------------------------------------------------
 // K6: per walker: W scatter over every determinant, Q = A^T W, Pm = T Q^T,
 // G_{i mu} = g Psi~ + sum_m d_mu phi[i][m] Q[i][m] - sum_b d_mu phi[i][o_b] Pm[b][i],
@@ -490,10 +641,12 @@ __global__ void __launch_bounds__(128) k_spmm_df(const int* __restrict__ seg, co
 // MIXED variant: cofactors in double-float on the FP32 pipe; W accumulated as
 // a compensated pair of FP32 shared atomics: the atomic returns the old value,
 // so TwoSum(old, x) recovers the rounding error of the addition it performed,
-// which goes into the low word. Q, Pm and G stay FP64.
+// which goes into the low word. Q, Pm and G are double-float too (orbitals,
+// A and g arrive as pairs), so the FP64 pipe is left to the contraction; the
+// sums G are converted to FP64 with integer instructions.
 // smem, FP64: T[N][M], W[N][M], Q[N][M], A blocks, Pm.
-// smem, MIXED: W[N][M] (hi/lo FP32 pairs during the scatter, then the FP64 T
-//       for Pm), Q[N][M], A blocks, Pm, Tdf[N][M] (then W in FP64).
+// smem, MIXED: W[N][M] as hi/lo FP32 arrays, Q[N][M], A blocks, Pm (all pairs),
+//       Tdf[N][M].
 template <bool MIXED, int NT>
 __global__ void __launch_bounds__(NT) k_final(DevProblem P, DevScratch S, const double* __restrict__ R,
                                                double* __restrict__ log_abs_psi, int8_t* __restrict__ sign,
@@ -504,12 +657,15 @@ __global__ void __launch_bounds__(NT) k_final(DevProblem P, DevScratch S, const 
   const int NM = N * M;
   const int64_t w = blockIdx.x, wp = S.wp;
   if (S.live && w >= *S.live) return;
-  double* Ts = MIXED ? nullptr : sm;    // [N][M]; MIXED: loaded into the W space after the scatter
-  double* Ws = MIXED ? sm : sm + NM;    // [N][M]
-  double* Qs = Ws + NM;                 // [N][M]
-  double* As = Qs + NM;                 // [nu*nu + nd*nd]
+  // MIXED keeps T and Q as pairs with rows padded to Mt = M + 1 entries, so that
+  // threads reading the same column of different rows hit different banks
+  const int Mt = MIXED ? M + 1 : M;
+  double* Ts = MIXED ? nullptr : sm;    // [N][M] (FP64 only)
+  double* Ws = MIXED ? sm : sm + NM;    // [N][M] (MIXED: hi words, then lo words)
+  double* Qs = Ws + NM;                 // [N][Mt]
+  double* As = Qs + N * Mt;             // [nu*nu + nd*nd]
   double* Pm = As + nu * nu + nd * nd;  // [nu*nu + nd*nd]  Pm[b][i] per spin
-  float2* Tdf = reinterpret_cast<float2*>(Pm + nu * nu + nd * nd);  // [N][M] (MIXED)
+  float2* Tdf = reinterpret_cast<float2*>(Pm + nu * nu + nd * nd);  // [N][Mt] (MIXED)
   float* Whi = reinterpret_cast<float*>(Ws);                          // MIXED: [N][M] hi words
   float* Wlo = Whi + NM;                                              //        [N][M] lo words
   constexpr int NW = NT / 32;  // warps per block
@@ -520,7 +676,7 @@ __global__ void __launch_bounds__(NT) k_final(DevProblem P, DevScratch S, const 
   __shared__ float rmsG[4], estw[2][4];
   for (int t = threadIdx.x; t < NM; t += blockDim.x) {
     if (MIXED) {
-      Tdf[t] = S.Tdf[(size_t)t * wp + w];
+      Tdf[(t / M) * Mt + t % M] = S.Tdf[(size_t)t * wp + w];
       Whi[t] = 0.0f;
       Wlo[t] = 0.0f;
     } else {
@@ -528,63 +684,64 @@ __global__ void __launch_bounds__(NT) k_final(DevProblem P, DevScratch S, const 
       Ws[t] = 0.0;
     }
   }
-  for (int t = threadIdx.x; t < nu * nu + nd * nd; t += blockDim.x) As[t] = S.Ainv[w * (nu * nu + nd * nd) + t];
+  for (int t = threadIdx.x; t < nu * nu + nd * nd; t += blockDim.x) {
+    if (MIXED)
+      reinterpret_cast<float2*>(As)[t] = reinterpret_cast<const float2*>(S.Ainv)[w * (nu * nu + nd * nd) + t];
+    else
+      As[t] = S.Ainv[w * (nu * nu + nd * nd) + t];
+  }
   __syncthreads();
   const int nu_det = P.n_det_sp[0], ntot = nu_det + P.n_det_sp[1];
-  // MIXED: determinant t = (q * stride) mod ntot for q = thread, thread + NT,
-  // ..., with a prime stride that does not divide ntot (a permutation): every
-  // thread gets a mix of excitation degrees, so the double-float cofactor work
-  // (k^2 per determinant) is balanced across the block. FP64: each thread walks
-  // its own contiguous block (sequential loads of records and weights; the
-  // FP64 pipe, not the balance, bounds that variant). Either way the lanes of a
-  // warp hold determinants far apart in the (degree, key) order, which rarely
-  // share a (hole, particle) slot of W.
-  const int64_t stride = (ntot % 7919) ? 7919 : ((ntot % 7927) ? 7927 : 7933);
   const int tid = threadIdx.x, nth = blockDim.x;
-  const int per = (ntot + nth - 1) / nth;
-  const int n_mine = MIXED ? (ntot - tid + nth - 1) / nth : max(0, min(per, ntot - tid * per));
-  // MIXED: t_j = (tid + j nth) stride mod ntot, advanced by (nth stride) mod ntot per step
-  const int step = (int)(((int64_t)nth * stride) % ntot);
-  int tq = (int)(((int64_t)tid * stride) % ntot);
-  for (int j = 0; j < n_mine; j++) {
-    const int t = MIXED ? tq : tid * per + j;
-    if (MIXED) {
-      tq += step;
-      if (tq >= ntot) tq -= ntot;
-    }
-    const int sp = t < nu_det ? 0 : 1;
-    const Exc e = P.exc[sp][sp ? t - nu_det : t];
-    if (e.k == 0) continue;
-    // the weight eps_I w_I: sign and zero test on the bits (no FP64 instructions)
-    long long wb = __double_as_longlong(S.vu[w * ntot + t]);
-    if ((wb & 0x7fffffffffffffffLL) == 0) continue;
-    if (e.eps < 0) wb ^= (long long)(1ULL << 63);
-    const double wgt = __longlong_as_double(wb);
-    const int off = sp ? nu * M : 0;
-    if (MIXED) {
-      df32 m[4][4], cof[4][4];
-#pragma unroll
-      for (int a = 0; a < 4; a++)
-#pragma unroll
-        for (int b = 0; b < 4; b++) {
-          const float2 v = (a < e.k && b < e.k) ? Tdf[off + e.h[a] * M + e.p[b]] : make_float2(0.f, 0.f);
-          m[a][b] = df32(v.x, v.y);
+  if constexpr (MIXED) {
+    // The determinants of one spin and excitation degree k at a time (the context orders
+    // each spin's list by degree), so every lane of a warp runs the same k x k cofactor
+    // code; within the group, determinant (q * stride) mod L for q = thread, thread + NT,
+    // ... with a prime stride that does not divide L (a permutation), so the lanes of a
+    // warp hold determinants far apart in key order, which rarely share a (hole,
+    // particle) slot of W, and every thread gets an even share of the group.
+    for (int grp = 0; grp < 2 * kMaxExc; grp++) {
+      const int sp = grp / kMaxExc, k = grp % kMaxExc + 1;
+      const int base = sp ? nu_det : 0;
+      const int s0 = P.deg_start[sp][k], L = P.deg_start[sp][k + 1] - s0;
+      if (L <= 0) continue;
+      const int stride = (L % 7919) ? 7919 : ((L % 7927) ? 7927 : 7933);
+      const int step = (int)(((int64_t)nth * stride) % L);
+      int tq = (int)(((int64_t)tid * stride) % L);
+      const int off = sp ? nu * M : 0;    // W
+      const int toff = sp ? nu * Mt : 0;  // the padded pairs of T
+      for (int j = tid; j < L; j += nth) {
+        const int t = s0 + tq;
+        tq += step;
+        if (tq >= L) tq -= L;
+        const Exc e = P.exc[sp][t];
+        // the weight eps_I w_I: sign and zero test on the bits (no FP64 instructions)
+        long long wb = __double_as_longlong(S.vu[w * ntot + base + t]);
+        if ((wb & 0x7fffffffffffffffLL) == 0) continue;
+        if (e.eps < 0) wb ^= (long long)(1ULL << 63);
+        switch (k) {
+          case 1: scatter_cof_df<1>(e, wb, Tdf, toff, Mt, off, M, Whi, Wlo); break;
+          case 2: scatter_cof_df<2>(e, wb, Tdf, toff, Mt, off, M, Whi, Wlo); break;
+          case 3: scatter_cof_df<3>(e, wb, Tdf, toff, Mt, off, M, Whi, Wlo); break;
+          default: scatter_cof_df<4>(e, wb, Tdf, toff, Mt, off, M, Whi, Wlo); break;
         }
-      small_cof(e.k, m, cof);
-      const df32 wd = df_from_bits(wb);
-#pragma unroll
-      for (int a = 0; a < 4; a++)
-#pragma unroll
-        for (int b = 0; b < 4; b++)
-          if (a < e.k && b < e.k) {
-            const df32 x = cof[a][b] * wd;
-            const int slot = off + e.h[a] * M + e.p[b];
-            const float old = atomicAdd(Whi + slot, x.hi);
-            float s_, err;
-            two_sum(old, x.hi, s_, err);
-            atomicAdd(Wlo + slot, __fadd_rn(err, x.lo));
-          }
-    } else {
+      }
+    }
+  } else {
+    // each thread walks its own contiguous block (sequential loads of records and weights;
+    // the FP64 pipe, not the balance, bounds this variant)
+    const int per = (ntot + nth - 1) / nth;
+    const int n_mine = max(0, min(per, ntot - tid * per));
+    for (int j = 0; j < n_mine; j++) {
+      const int t = tid * per + j;
+      const int sp = t < nu_det ? 0 : 1;
+      const Exc e = P.exc[sp][sp ? t - nu_det : t];
+      if (e.k == 0) continue;
+      long long wb = __double_as_longlong(S.vu[w * ntot + t]);
+      if ((wb & 0x7fffffffffffffffLL) == 0) continue;
+      if (e.eps < 0) wb ^= (long long)(1ULL << 63);
+      const double wgt = __longlong_as_double(wb);
+      const int off = sp ? nu * M : 0;
       double m[4][4], cof[4][4];
 #pragma unroll
       for (int a = 0; a < 4; a++)
@@ -599,69 +756,136 @@ __global__ void __launch_bounds__(NT) k_final(DevProblem P, DevScratch S, const 
     }
   }
   __syncthreads();
-  // MIXED: W as FP64 goes into the table pairs' space, which the scatter no longer needs
-  double* Wd = MIXED ? reinterpret_cast<double*>(Tdf) : Ws;
-  if (MIXED) {
-    for (int t = threadIdx.x; t < NM; t += blockDim.x) Wd[t] = (double)Whi[t] + (double)Wlo[t];
-    __syncthreads();
-    // the FP64 table for Pm, into the space of the hi/lo words (Q does not read it)
-    Ts = Ws;
-    for (int t = threadIdx.x; t < NM; t += blockDim.x) Ts[t] = S.T[(size_t)t * wp + w];
-  }
-  // Q[i][m] = sum_a A[a][i] W[a][m] (per spin block)
-  for (int t = threadIdx.x; t < NM; t += blockDim.x) {
-    const int row = t / M, m = t - row * M;
-    const int sp = row < nu ? 0 : 1;
-    const int n = sp ? nd : nu, e0 = sp ? nu : 0, i = row - e0;
-    const double* A = As + (sp ? nu * nu : 0);
-    const double* Wb = Wd + e0 * M;
-    double acc = 0.0;
-    for (int a = 0; a < n; a++) acc = fma(A[a * n + i], Wb[a * M + m], acc);
-    Qs[t] = acc;
-  }
-  __syncthreads();
-  // Pm[b][i] = sum_m T[b][m] Q[i][m]
-  for (int t = threadIdx.x; t < nu * nu + nd * nd; t += blockDim.x) {
-    const int sp = t < nu * nu ? 0 : 1;
-    const int n = sp ? nd : nu, e0 = sp ? nu : 0;
-    const int tt = sp ? t - nu * nu : t;
-    const int b = tt / n, i = tt - b * n;
-    const double* Tr = Ts + (e0 + b) * M;
-    const double* Qr = Qs + (e0 + i) * M;
-    double acc = 0.0;
-    for (int m = 0; m < M; m++) acc = fma(Tr[m], Qr[m], acc);
-    Pm[t] = acc;
-  }
-  __syncthreads();
   const double psit = S.psit[w];
   const double ld = S.ld0[w * 2] + S.ld0[w * 2 + 1];
   const double sg = S.sg0[w * 2] * S.sg0[w * 2 + 1];
-  for (int t = threadIdx.x; t < N * 4; t += blockDim.x) {
-    const int e = t >> 2, mu = t & 3;
-    const int sp = e < nu ? 0 : 1;
-    const int n = sp ? nd : nu, e0 = sp ? nu : 0, i = e - e0;
-    const int* occ = P.ref_occ + sp * kMaxSpin;
-    const double* dphi = S.phi + ((w * 5 + 1 + mu) * N + e) * M;
-    const double* Qr = Qs + e * M;
-    double acc = S.g[(w * N + e) * 4 + mu] * psit;
-    // magnitudes of the terms, for the error estimate (FP32 is plenty for an estimate)
-    float aab = fabsf((float)acc), aa2 = aab * aab;
-    for (int m = 0; m < M; m++) {
-      acc = fma(dphi[m], Qr[m], acc);
-      const float tm = fabsf((float)dphi[m] * (float)Qr[m]);
-      aab += tm;
-      aa2 = fmaf(tm, tm, aa2);
+  if constexpr (MIXED) {
+    // W normalised into (hi, lo) pairs in place
+    for (int t = threadIdx.x; t < NM; t += blockDim.x) {
+      float hi, lo;
+      two_sum(Whi[t], Wlo[t], hi, lo);
+      Whi[t] = hi;
+      Wlo[t] = lo;
     }
-    const double* Pb = Pm + (sp ? nu * nu : 0);
-    for (int b = 0; b < n; b++) {
-      acc = fma(-dphi[occ[b]], Pb[b * n + i], acc);
-      const float tm = fabsf((float)dphi[occ[b]] * (float)Pb[b * n + i]);
-      aab += tm;
-      aa2 = fmaf(tm, tm, aa2);
+    __syncthreads();
+    const float2* A2 = reinterpret_cast<const float2*>(As);
+    float2* Q2 = reinterpret_cast<float2*>(Qs);
+    float2* P2 = reinterpret_cast<float2*>(Pm);
+    // Q[i][m] = sum_a A[a][i] W[a][m] (per spin block)
+    for (int t = threadIdx.x; t < NM; t += blockDim.x) {
+      const int row = t / M, m = t - row * M;
+      const int sp = row < nu ? 0 : 1;
+      const int n = sp ? nd : nu, e0 = sp ? nu : 0, i = row - e0;
+      const float2* A = A2 + (sp ? nu * nu : 0);
+      df32 acc(0.0f, 0.0f);
+      for (int a = 0; a < n; a++) {
+        const float2 av = A[a * n + i];
+        const int wi = (e0 + a) * M + m;
+        acc = acc + df32(av.x, av.y) * df32(Whi[wi], Wlo[wi]);
+      }
+      Q2[row * Mt + m] = make_float2(acc.hi, acc.lo);
     }
-    Gs[e][mu] = acc;
-    Ga[e][mu] = aab;
-    G2[e][mu] = sqrtf(aa2);
+    __syncthreads();
+    // Pm[b][i] = sum_m T[b][m] Q[i][m]
+    for (int t = threadIdx.x; t < nu * nu + nd * nd; t += blockDim.x) {
+      const int sp = t < nu * nu ? 0 : 1;
+      const int n = sp ? nd : nu, e0 = sp ? nu : 0;
+      const int tt = sp ? t - nu * nu : t;
+      const int b = tt / n, i = tt - b * n;
+      const float2* Tr = Tdf + (e0 + b) * Mt;
+      const float2* Qr = Q2 + (e0 + i) * Mt;
+      df32 acc(0.0f, 0.0f);
+      for (int m = 0; m < M; m++) acc = acc + df32(Tr[m].x, Tr[m].y) * df32(Qr[m].x, Qr[m].y);
+      P2[t] = make_float2(acc.hi, acc.lo);
+    }
+    __syncthreads();
+    const df32 psit_df = df_from_bits(__double_as_longlong(psit));
+    const float2* phi2 = reinterpret_cast<const float2*>(S.phi);
+    const float2* g2 = reinterpret_cast<const float2*>(S.g);
+    for (int t = threadIdx.x; t < N * 4; t += blockDim.x) {
+      const int e = t >> 2, mu = t & 3;
+      const int sp = e < nu ? 0 : 1;
+      const int n = sp ? nd : nu, e0 = sp ? nu : 0, i = e - e0;
+      const int* occ = P.ref_occ + sp * kMaxSpin;
+      const float2* dphi = phi2 + ((w * 5 + 1 + mu) * N + e) * M;
+      const float2* Qr = Q2 + e * Mt;
+      const float2 gv = g2[(w * N + e) * 4 + mu];
+      df32 acc = df32(gv.x, gv.y) * psit_df;
+      // magnitudes of the terms, for the error estimate (FP32 is plenty for an estimate)
+      float aab = fabsf(acc.hi), aa2 = aab * aab;
+      for (int m = 0; m < M; m++) {
+        const float2 dv = dphi[m];
+        acc = acc + df32(dv.x, dv.y) * df32(Qr[m].x, Qr[m].y);
+        const float tm = fabsf(dv.x * Qr[m].x);
+        aab += tm;
+        aa2 = fmaf(tm, tm, aa2);
+      }
+      const float2* Pb = P2 + (sp ? nu * nu : 0);
+      for (int b = 0; b < n; b++) {
+        const float2 dv = dphi[occ[b]], pv = Pb[b * n + i];
+        acc = acc - df32(dv.x, dv.y) * df32(pv.x, pv.y);
+        const float tm = fabsf(dv.x * pv.x);
+        aab += tm;
+        aa2 = fmaf(tm, tm, aa2);
+      }
+      Gs[e][mu] = df_to_double_int(acc);
+      Ga[e][mu] = aab;
+      G2[e][mu] = sqrtf(aa2);
+    }
+  } else {
+    double* Wd = Ws;
+    // Q[i][m] = sum_a A[a][i] W[a][m] (per spin block)
+    for (int t = threadIdx.x; t < NM; t += blockDim.x) {
+      const int row = t / M, m = t - row * M;
+      const int sp = row < nu ? 0 : 1;
+      const int n = sp ? nd : nu, e0 = sp ? nu : 0, i = row - e0;
+      const double* A = As + (sp ? nu * nu : 0);
+      const double* Wb = Wd + e0 * M;
+      double acc = 0.0;
+      for (int a = 0; a < n; a++) acc = fma(A[a * n + i], Wb[a * M + m], acc);
+      Qs[t] = acc;
+    }
+    __syncthreads();
+    // Pm[b][i] = sum_m T[b][m] Q[i][m]
+    for (int t = threadIdx.x; t < nu * nu + nd * nd; t += blockDim.x) {
+      const int sp = t < nu * nu ? 0 : 1;
+      const int n = sp ? nd : nu, e0 = sp ? nu : 0;
+      const int tt = sp ? t - nu * nu : t;
+      const int b = tt / n, i = tt - b * n;
+      const double* Tr = Ts + (e0 + b) * M;
+      const double* Qr = Qs + (e0 + i) * M;
+      double acc = 0.0;
+      for (int m = 0; m < M; m++) acc = fma(Tr[m], Qr[m], acc);
+      Pm[t] = acc;
+    }
+    __syncthreads();
+    for (int t = threadIdx.x; t < N * 4; t += blockDim.x) {
+      const int e = t >> 2, mu = t & 3;
+      const int sp = e < nu ? 0 : 1;
+      const int n = sp ? nd : nu, e0 = sp ? nu : 0, i = e - e0;
+      const int* occ = P.ref_occ + sp * kMaxSpin;
+      const double* dphi = S.phi + ((w * 5 + 1 + mu) * N + e) * M;
+      const double* Qr = Qs + e * M;
+      double acc = S.g[(w * N + e) * 4 + mu] * psit;
+      // magnitudes of the terms, for the error estimate (FP32 is plenty for an estimate)
+      float aab = fabsf((float)acc), aa2 = aab * aab;
+      for (int m = 0; m < M; m++) {
+        acc = fma(dphi[m], Qr[m], acc);
+        const float tm = fabsf((float)dphi[m] * (float)Qr[m]);
+        aab += tm;
+        aa2 = fmaf(tm, tm, aa2);
+      }
+      const double* Pb = Pm + (sp ? nu * nu : 0);
+      for (int b = 0; b < n; b++) {
+        acc = fma(-dphi[occ[b]], Pb[b * n + i], acc);
+        const float tm = fabsf((float)dphi[occ[b]] * (float)Pb[b * n + i]);
+        aab += tm;
+        aa2 = fmaf(tm, tm, aa2);
+      }
+      Gs[e][mu] = acc;
+      Ga[e][mu] = aab;
+      G2[e][mu] = sqrtf(aa2);
+    }
   }
   __syncthreads();
   // potential energy: electron-nucleus, electron-electron, nucleus-nucleus
@@ -823,62 +1047,59 @@ static bool narrow_contraction(const DevProblem& P, const DevScratch& S) {
   return S.live != nullptr && !(P.contract_impl == 1 && S.rdf && P.csr_val_df);
 }
 
-cudaError_t launch_zero_f64(const DevProblem& P, const DevScratch& S, int64_t n_walk, cudaStream_t st) {
-  const int64_t ndt = (int64_t)P.n_det_sp[0] + P.n_det_sp[1];
-  const int64_t npad = (n_walk + kWalkerPad - 1) / kWalkerPad * kWalkerPad;
-  cudaError_t e = cudaMemsetAsync(S.vu, 0, sizeof(double) * ndt * npad, st);
-  if (e != cudaSuccess) return e;
-  // the narrow contraction keeps the gathered magnitude sums; every other one accumulates them anew
-  if (!narrow_contraction(P, S) && (e = cudaMemsetAsync(S.psia, 0, sizeof(float) * npad, st)) != cudaSuccess)
-    return e;
-  return cudaMemsetAsync(S.psit, 0, sizeof(double) * npad, st);
+cudaError_t launch_zero_f64(const DevProblem&, const DevScratch&, int64_t, cudaStream_t) {
+  // nothing left to clear here: the contraction stores whole segments, the ratio kernels clear
+  // the entries of cut segments and the reference kernel the Psi~ sums of its walker
+  return cudaSuccess;
 }
 
 cudaError_t launch_contract_f64(const DevProblem& P, const DevScratch& S, int64_t n_walk, cudaStream_t st,
                                 unsigned long long* queue, int persistent_blocks) {
-  const int chunk = P.spmm_chunk > 0 ? P.spmm_chunk : 512;
-  const int64_t n_chunks = (P.nnz + chunk - 1) / chunk;
   // an escalated re-evaluation (few walkers, live count on the device) uses 4 walkers per lane
   const bool narrow = narrow_contraction(P, S);
   const int64_t n_groups = narrow ? (n_walk + 127) / 128 : (n_walk + 255) / 256;
-  const int64_t items = n_chunks * n_groups;
+  const int64_t work_max = (int64_t)std::max(P.n_items[0], P.n_items[1]) * n_groups;
   // one work item per warp (full occupancy hides the L2 latency of the gathers), or a
   // persistent grid whose warps draw items from a queue (two counters, one per launch)
-  int64_t blocks = (items + 3) / 4;
-  int cap = P.spmm_blocks > 0 ? P.spmm_blocks : persistent_blocks;
-  const bool q = queue && cap > 0 && cap < blocks;
+  const int cap = P.spmm_blocks > 0 ? P.spmm_blocks : persistent_blocks;
+  const bool q = queue && cap > 0 && cap < (work_max + 3) / 4;
   if (q) {
-    blocks = cap;
     cudaError_t e = cudaMemsetAsync(queue, 0, 2 * sizeof(unsigned long long), st);
     if (e != cudaSuccess) return e;
   }
+  auto grid = [&](int o) -> unsigned {
+    const int64_t full = ((int64_t)P.n_items[o] * n_groups + 3) / 4;
+    return (unsigned)std::max<int64_t>(1, q ? std::min<int64_t>(full, cap) : full);
+  };
   const int64_t ndt = (int64_t)P.n_det_sp[0] + P.n_det_sp[1];
   const double* r_up = S.r;
   const double* r_dn = S.r + (size_t)P.n_det_sp[0] * S.wp;
   if (P.contract_impl == 1 && S.rdf && P.csr_val_df) {  // double-float option of the mixed path
     const float2* x_up = S.rdf;
     const float2* x_dn = S.rdf + (size_t)P.n_det_sp[0] * S.wp;
-    const int64_t b = P.spmm_blocks > 0 ? std::min<int64_t>((items + 3) / 4, P.spmm_blocks) : (items + 3) / 4;
-    k_spmm_df<<<(unsigned)b, 128, 0, st>>>(P.csr_row, P.csr_col, P.csr_val_df, P.nnz, chunk, n_chunks, n_groups,
-                                            x_dn, S.wp, S.vu, ndt, 0, r_up, S.psit, S.psia);
+    auto gdf = [&](int o) -> unsigned {
+      const int64_t full = ((int64_t)P.n_items[o] * n_groups + 3) / 4;
+      return (unsigned)std::max<int64_t>(1, P.spmm_blocks > 0 ? std::min<int64_t>(full, P.spmm_blocks) : full);
+    };
+    k_spmm_df<<<gdf(0), 128, 0, st>>>(P.csr_row, P.csr_col, P.csr_val_df, P.items[0], P.n_items[0], n_groups, x_dn,
+                                      S.wp, S.vu, ndt, 0, r_up, S.psit, S.psia);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    k_spmm_df<<<(unsigned)b, 128, 0, st>>>(P.csc_col, P.csc_row, P.csc_val_df, P.nnz, chunk, n_chunks, n_groups,
-                                            x_up, S.wp, S.vu, ndt, P.n_det_sp[0], nullptr, nullptr, nullptr);
+    k_spmm_df<<<gdf(1), 128, 0, st>>>(P.csc_col, P.csc_row, P.csc_val_df, P.items[1], P.n_items[1], n_groups, x_up,
+                                      S.wp, S.vu, ndt, P.n_det_sp[0], nullptr, nullptr, nullptr);
     return cudaGetLastError();
   }
   // v = C r_dn (rows = up determinants) with Psi~ = r_up . v and its magnitude sum (an escalated
   // re-evaluation reuses the magnitude sum of the evaluation that flagged it)
-  auto* kv = narrow ? k_spmm_wm<false, false, 4> : (q ? k_spmm_wm<true, true, 8> : k_spmm_wm<false, true, 8>);
-  kv<<<(unsigned)blocks, 128, 0, st>>>(P.csr_row, P.csr_col, P.csr_val, P.nnz, chunk, n_chunks, n_groups, r_dn, S.wp,
-                                       S.vu, ndt, 0, r_up, S.psit, narrow ? nullptr : S.psia, queue, S.live);
+  auto* kv = narrow ? k_spmm_seg<false, false, 4> : (q ? k_spmm_seg<true, true, 8> : k_spmm_seg<false, true, 8>);
+  kv<<<grid(0), 128, 0, st>>>(P.csr_row, P.csr_col, P.csr_val, P.items[0], P.n_items[0], n_groups, r_dn, S.wp, S.vu,
+                              ndt, 0, r_up, S.psit, narrow ? nullptr : S.psia, queue, S.live);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   // u = C^T r_up (columns = down determinants), in the paper's column-major order
-  auto* ku = narrow ? k_spmm_wm<false, false, 4> : (q ? k_spmm_wm<true, false, 8> : k_spmm_wm<false, false, 8>);
-  ku<<<(unsigned)blocks, 128, 0, st>>>(P.csc_col, P.csc_row, P.csc_val, P.nnz, chunk, n_chunks, n_groups, r_up, S.wp,
-                                       S.vu, ndt, P.n_det_sp[0], nullptr, nullptr, nullptr, q ? queue + 1 : nullptr,
-                                       S.live);
+  auto* ku = narrow ? k_spmm_seg<false, false, 4> : (q ? k_spmm_seg<true, false, 8> : k_spmm_seg<false, false, 8>);
+  ku<<<grid(1), 128, 0, st>>>(P.csc_col, P.csc_row, P.csc_val, P.items[1], P.n_items[1], n_groups, r_up, S.wp, S.vu,
+                              ndt, P.n_det_sp[0], nullptr, nullptr, nullptr, q ? queue + 1 : nullptr, S.live);
   return cudaGetLastError();
 }
 
@@ -886,7 +1107,6 @@ DevScratch scratch_view(const DevScratch& S, const DevProblem& P, int64_t off) {
   DevScratch V = S;
   if (off == 0) return V;
   const int64_t N = P.n_elec, M = P.n_mo;
-  const int64_t ndt = (int64_t)P.n_det_sp[0] + P.n_det_sp[1];
   V.phi = S.phi + off * 5 * N * M;
   V.Ainv = S.Ainv + off * (P.n_up * P.n_up + P.n_dn * P.n_dn);
   V.ld0 = S.ld0 + off * 2;
@@ -895,7 +1115,7 @@ DevScratch scratch_view(const DevScratch& S, const DevProblem& P, int64_t off) {
   V.kap = S.kap + off * 2;
   V.est = S.est + off * 2;
   V.wstat = S.wstat + off;
-  V.vu = S.vu + off * ndt;
+  V.vu = S.vu + off * ((int64_t)P.n_det_sp[0] + P.n_det_sp[1]);
   V.T = S.T + off;  // walker-minor: a column offset with the same stride
   if (S.Tdf) V.Tdf = S.Tdf + off;
   V.r = S.r + off;
@@ -916,9 +1136,10 @@ cudaError_t launch_spmm_rows_f64(const DevProblem& P, const double* r_dn, const 
 
 size_t final_smem_bytes(const DevProblem& P, bool mixed) {
   const size_t NM = (size_t)P.n_elec * P.n_mo;
-  // FP64: T, W, Q; MIXED: W (then T), Q, Tdf (then W); both: A blocks and Pm
-  return sizeof(double) * ((mixed ? 2 : 3) * NM + 2 * (size_t)(P.n_up * P.n_up + P.n_dn * P.n_dn)) +
-         (mixed ? 8 * NM : 0);
+  const size_t NMt = (size_t)P.n_elec * (P.n_mo + 1);  // rows padded by one pair (MIXED)
+  const size_t AB = 2 * (size_t)(P.n_up * P.n_up + P.n_dn * P.n_dn);
+  // FP64: T, W, Q, A blocks and Pm; MIXED: W (hi and lo words), Q and T pairs, A blocks and Pm
+  return mixed ? 8 * (NM + 2 * NMt + AB) : 8 * (3 * NM + AB);
 }
 
 cudaError_t launch_final(const DevProblem& P, const DevScratch& S, int64_t n_walk, const double* R,

@@ -25,9 +25,9 @@ namespace {
 // product xh*bh is made exact with an FMA (TwoProd), accumulated with TwoSum,
 // and the cross terms xh*bl + xl*bh plus all rounding errors go into a second
 // FP32 accumulator (the Dot2 scheme of Ogita, Rump and Oishi, extended to split
-// inputs). Phi = s + c is stored in FP64.
+// inputs). Phi = s + c is stored as a renormalised double-float pair.
 template <int kECm>
-__global__ void __launch_bounds__(128) k_mo_mixed(DevProblem P, double* __restrict__ phi,
+__global__ void __launch_bounds__(128) k_mo_mixed(DevProblem P, float2* __restrict__ phi,
                                                   const double* __restrict__ R) {
   extern __shared__ float smf[];
   __shared__ df32 rdf[kECm][3];
@@ -82,7 +82,11 @@ __global__ void __launch_bounds__(128) k_mo_mixed(DevProblem P, double* __restri
     for (int cc = 0; cc < 5; cc++)
 #pragma unroll
       for (int e = 0; e < kECm; e++)
-        if (e < ne) phi[((w * 5 + cc) * N + e_begin + e) * M + m] = (double)s[cc * kECm + e] + (double)c[cc * kECm + e];
+        if (e < ne) {
+          float hi, lo;
+          two_sum(s[cc * kECm + e], c[cc * kECm + e], hi, lo);
+          phi[((w * 5 + cc) * N + e_begin + e) * M + m] = make_float2(hi, lo);
+        }
   }
 }
 
@@ -116,7 +120,7 @@ __device__ __forceinline__ uint32_t ld_pair(const uint16_t* p) { return *reinter
 __device__ __forceinline__ uint16_t bf16_int(float d) { return (uint16_t)(__float_as_uint(d) >> 16); }
 
 template <int kECm>
-__global__ void __launch_bounds__(128) k_mo_tc(DevProblem P, double* __restrict__ phi, const double* __restrict__ R) {
+__global__ void __launch_bounds__(128) k_mo_tc(DevProblem P, float2* __restrict__ phi, const double* __restrict__ R) {
   constexpr int kRows = 5 * kECm, kMt = (kRows + 15) / 16, kRowsP = kMt * 16;
   extern __shared__ float smf[];
   __shared__ df32 rdf[kECm][3];
@@ -250,8 +254,8 @@ __global__ void __launch_bounds__(128) k_mo_tc(DevProblem P, double* __restrict_
           if (row >= kRows || col >= M) continue;
           const int cc = row / kECm, e = row - cc * kECm;
           if (e >= ne) continue;
-          const double v = (double)acc[u][mt][q].hi + (double)acc[u][mt][q].lo;
-          phi[((w * 5 + cc) * N + e_begin + e) * M + col] = ldexp(v, er[row] + P.B_exp[col]);
+          const int E = er[row] + P.B_exp[col];
+          phi[((w * 5 + cc) * N + e_begin + e) * M + col] = make_float2(ldexpf(acc[u][mt][q].hi, E), ldexpf(acc[u][mt][q].lo, E));
         }
     }
   }
@@ -280,9 +284,10 @@ __global__ void __launch_bounds__(128) k_ratio_df(DevProblem P, DevScratch S) {
         m[a][b] = df32(v.x, v.y);
       }
     const df32 dd = small_det(e.k, m);
-    const double d = df_to_double(dd);
+    const double d = df_to_double_int(dd);  // the FP64 ratio for the contraction, off the FP64 pipe
     S.r[(size_t)t * wp + w] = e.eps < 0 ? -d : d;
     if (S.rdf) S.rdf[(size_t)t * wp + w] = e.eps < 0 ? make_float2(-dd.hi, -dd.lo) : make_float2(dd.hi, dd.lo);
+    if (P.split[t]) S.vu[w * ntot + t] = 0.0;  // the contraction adds the pieces of a cut segment
   }
 }
 
@@ -310,7 +315,7 @@ static cudaError_t launch_mo_mixed_ec(const DevProblem& P, const DevScratch& S, 
   cudaError_t e = opt.ensure(k_mo_mixed<EC>, smem);
   if (e != cudaSuccess) return e;
   dim3 grid((unsigned)n_walk, (P.n_elec + EC - 1) / EC);
-  k_mo_mixed<EC><<<grid, 128, smem, st>>>(P, S.phi, R);
+  k_mo_mixed<EC><<<grid, 128, smem, st>>>(P, reinterpret_cast<float2*>(S.phi), R);
   return cudaGetLastError();
 }
 
@@ -327,13 +332,15 @@ static cudaError_t launch_mo_tc_ec(const DevProblem& P, const DevScratch& S, int
   cudaError_t e = opt.ensure(k_mo_tc<EC>, smem);
   if (e != cudaSuccess) return e;
   dim3 grid((unsigned)n_walk, (P.n_elec + EC - 1) / EC);
-  k_mo_tc<EC><<<grid, 128, smem, st>>>(P, S.phi, R);
+  k_mo_tc<EC><<<grid, 128, smem, st>>>(P, reinterpret_cast<float2*>(S.phi), R);
   return cudaGetLastError();
 }
 
 cudaError_t launch_mo_mixed(const DevProblem& P, const DevScratch& S, int64_t n_walk, const double* R,
                             cudaStream_t st) {
-  // tensor-core digit products unless asked otherwise or the digits do not fit in shared memory
+  // tcgen05 digit products by default; warp-level MMA digits (mo_impl 0) or the compensated
+  // CUDA-core product when asked for, or when the problem exceeds what the tcgen05 kernel holds
+  if (P.mo_impl == 2 && mo_umma_supported(P)) return launch_mo_umma(P, S, n_walk, R, P.n_sm, st);
   const size_t kSmemMax = 200 * 1024;
   if (P.mo_impl == 0 && P.B_dig && mo_tc_smem_bytes(P, P.mo_ec) <= kSmemMax) {
     switch (P.mo_ec) {

@@ -23,20 +23,26 @@ namespace {
 constexpr int kWarpsPerBlock = 4;
 constexpr double kSmMin = 1e-3;  // the paper's threshold on |ratio|
 
+// component 0 (the value) of the orbital array: FP64, or double-float pairs in a mixed context
 __device__ __forceinline__ double phi_val(const double* __restrict__ phi, int64_t w, int n_elec, int n_mo, int e,
-                                          int m) {
-  return phi[((w * 5 + 0) * n_elec + e) * n_mo + m];  // component 0: the value
+                                          int m, int df) {
+  const size_t ix = ((w * 5 + 0) * n_elec + e) * n_mo + m;
+  if (df) {
+    const float2 v = reinterpret_cast<const float2*>(phi)[ix];
+    return (double)v.x + (double)v.y;
+  }
+  return phi[ix];
 }
 
 // Gauss-Jordan inverse of S[i][a] = phi_{occ[a]}(r_{e0+i}) with partial
 // pivoting; A, B: [N][N+1] shared scratch (B = S^-1 on exit, B[a][i]).
 // Returns log|det| in *ld and the sign in *sg (0 when singular).
-__device__ void full_inverse(const double* __restrict__ phi, int64_t w, int n_elec, int n_mo, int e0, int N,
+__device__ void full_inverse(const double* __restrict__ phi, int df, int64_t w, int n_elec, int n_mo, int e0, int N,
                              const uint8_t* occ, double* A, double* B, double* ld, double* sg) {
   const int lane = threadIdx.x & 31, P = N + 1;
   if (lane < N) {
     for (int a = 0; a < N; a++) {
-      A[lane * P + a] = phi_val(phi, w, n_elec, n_mo, e0 + lane, occ[a]);
+      A[lane * P + a] = phi_val(phi, w, n_elec, n_mo, e0 + lane, occ[a], df);
       B[lane * P + a] = lane == a ? 1.0 : 0.0;
     }
   }
@@ -145,7 +151,7 @@ __global__ void k_sm_chain(DevProblem P, DevScratch S, int spin, const SmStep* _
             continue;
           }
           // w_a = sum_i S^-1[a][i] phi_part(r_i): one orbital value per lane, broadcast by shuffles
-          const double pv = lane < N ? phi_val(S.phi, w, P.n_elec, P.n_mo, e0 + lane, st.part[s]) : 0.0;
+          const double pv = lane < N ? phi_val(S.phi, w, P.n_elec, P.n_mo, e0 + lane, st.part[s], P.phi_df) : 0.0;
           double acc = 0.0;
           for (int i = 0; i < N; i++) acc += (lane < N ? B[lane * Pd + i] : 0.0) * __shfl_sync(0xffffffffu, pv, i);
           if (lane < N) wv[lane] = acc;
@@ -178,7 +184,7 @@ __global__ void k_sm_chain(DevProblem P, DevScratch S, int spin, const SmStep* _
       }
     }
     if (rebuild) {
-      full_inverse(S.phi, w, P.n_elec, P.n_mo, e0, N, st.occ, A, B, &logd, &sign);
+      full_inverse(S.phi, P.phi_df, w, P.n_elec, P.n_mo, e0, N, st.occ, A, B, &logd, &sign);
       if (lane < N) cols[lane] = st.occ[lane];
       __syncwarp();
       inv++;

@@ -58,8 +58,8 @@ def test_limits_are_enforced():
 def test_measured_fp64_rate_is_plausible():
     """The FP64 FMA throughput probe behind the contraction's roofline: positive,
     repeatable within 10 %, and within a factor of 4 of GB300's nominal 1.25 TFLOP/s."""
-    a, ms = pkg.measure_fp64_rate(0, fma_per_thread=1 << 16, reps=3)
-    b, _ = pkg.measure_fp64_rate(0, fma_per_thread=1 << 16, reps=3)
-    assert ms > 0
+    a, ms, mhz = pkg.measure_fp64_rate(0, fma_per_thread=1 << 16, reps=3)
+    b, _, _ = pkg.measure_fp64_rate(0, fma_per_thread=1 << 16, reps=3)
+    assert ms > 0 and 500 < mhz < 3000, (ms, mhz)
     assert 0.3 < a < 5.0, a
     assert abs(a - b) <= 0.1 * max(a, b), (a, b)

@@ -292,16 +292,19 @@ def test_chlorine_like_750k_full_size_sampled(cl750, prec):
     assert all(q[k]["p99"] < 1e-5 for k in q), q
 
 
-@pytest.mark.parametrize("ec", [4, 6, 8])
+@pytest.mark.parametrize("impl,ec", [(0, 4), (0, 6), (0, 8), (1, 4), (1, 8), (2, 4)])
 @pytest.mark.parametrize("name", ["oxygen_like_1k", "chlorine_like_100k"])
-def test_mixed_tensor_core_orbitals(name, ec):
-    """The optional orbital product on the BF16 tensor cores (exact digit
-    products, mo_impl = 0) against the oracle, every electron block size; the
-    10^5 expansion on 32 sampled walkers."""
+def test_mixed_orbital_products(name, impl, ec):
+    """Every orbital product of the mixed path against the oracle: exact BF16
+    digit products on the tcgen05 tensor cores (mo_impl 2, the default), the same
+    digits on warp-level mma.sync (0) and the compensated dot product on the CUDA
+    cores (1), with the electron blocks of the last two; the 10^5 expansion on 32
+    sampled walkers."""
     wl = synth.WORKLOADS[name]()
     ctx = pkg.Context.from_workload(wl, device=0, precision=pkg.PRECISION_MIXED)
-    ctx.set_tuning(mo_ec=ec, mo_impl=0)
-    assert ctx.tuning()["mo_impl"] == 0
+    assert ctx.tuning()["mo_impl"] == 2
+    ctx.set_tuning(mo_ec=ec, mo_impl=impl)
+    assert ctx.tuning()["mo_impl"] == impl
     got = _gpu_eval(ctx, wl.R)
     idx = np.arange(wl.n_walk) if wl.n_walk <= 64 else np.random.default_rng(2).choice(wl.n_walk, 32, replace=False)
     ref = oracle.evaluate(wl, R=wl.R[idx])
