@@ -27,10 +27,11 @@ METRIC = "walker-steps/s (Ψ,∇Ψ,∇²Ψ), 17e⁻, N_det=750k: mixed vs FP64 a
 UNIT = "walker-steps/s"
 CPU_SAMPLE_WALKERS = 96     # bounded oracle sample for the CPU baseline (~10-30 s of CPU work)
 CPU_SINGLE_CORE_WALKERS = 8  # the same oracle on one core, for the per-core figure
-# dram__bytes_read.sum + dram__bytes_write.sum of the average k_spmm_wm launch on the 750k workload
-# with 8,192 walkers, by the number of walker chunks, from one ncu capture of the current kernel;
-# null for a chunking that was not captured
-SPMM_TRAFFIC_750K = {1: 746.8e6, 3: 227.8e6}
+# dram__bytes_read.sum + dram__bytes_write.sum of the average k_spmm_seg launch on the 750k workload
+# with 8,192 walkers in three walker chunks, from one ncu capture of the current kernel (the v and u
+# launches of chunks 0 and 1; chunk 2 has chunk 0's size and is counted with its figures); null
+# for a chunking that was not captured
+SPMM_TRAFFIC_750K = {3: 182.1e6}
 
 
 def _env_int(k, d):
@@ -203,11 +204,15 @@ def _time_steps(ctx, Rdev, out, flush, stream, steps, warmup, dist, clock_index=
     clk = ClockSampler(clock_index) if clock_index is not None else None
     if clk:
         clk.__enter__()
+    ctx.set_profiling(2)  # the contraction kernels' own global-timer stamps: no events in the streams
+    contract_ms = []
     for s in range(steps):
         flush.fill_(float(s))          # evict L2 between timed steps (outside the events)
+        torch.cuda.synchronize()       # the step starts on an idle device
         ev[s][0].record(stream)
         ctx.evaluate(Rdev[s % len(Rdev)], out=out)
         ev[s][1].record(stream)
+        contract_ms.append(ctx.profile()["contract"])  # waits for this step's contraction events
     torch.cuda.synchronize()
     if clk:
         clk.__exit__(None, None, None)
@@ -218,6 +223,7 @@ def _time_steps(ctx, Rdev, out, flush, stream, steps, warmup, dist, clock_index=
     stage_ms, prof_ms = [], []
     for s in range(PROFILED_STEPS):
         flush.fill_(float(s))
+        torch.cuda.synchronize()
         ctx.evaluate(Rdev[s % len(Rdev)], out=out)
         stage_ms.append(ctx.profile())  # waits for this step's events
         prof_ms.append(ctx.timeline()["end"])
@@ -225,6 +231,7 @@ def _time_steps(ctx, Rdev, out, flush, stream, steps, warmup, dist, clock_index=
     timeline["profiled_step_ms"] = statistics.median(prof_ms)
     ctx.set_profiling(False)
     kern = {k: statistics.median(d[k] for d in stage_ms) for k in stage_ms[0]}
+    kern["contract_timed"] = statistics.mean(contract_ms)
     return step_ms, kern, (clk.summary() if clk else None), timeline
 
 
@@ -353,25 +360,28 @@ def run_ours(args):
     h2d = W * N * 3 * 8
     d2h = W * (8 + 1 + 3 * N * 8 + N * 8 + 8 + 4)
 
-    # roofline of the dominant kernel: the FP64 sparse contraction k_spmm_wm, 2 launches per
+    # roofline of the dominant kernel: the FP64 sparse contraction k_spmm_seg, 2 launches per
     # step and walker chunk (v = C r_dn, u = C^T r_up), each 2 FLOP per nonzero per walker;
     # the average launch covers W / chunks walkers
     kern = main["kern"]
     flops_launch = 2.0 * st["n_det"] * W / main_chunks
-    launch_ms = kern["contract"] / (2 * main_chunks)
+    launch_ms = kern["contract_timed"] / (2 * main_chunks)
     achieved = flops_launch / (launch_ms / 1e3) / 1e12
     traffic = args.traffic
     if traffic is None and args.workload == "chlorine_like_750k" and W == 8192:
         traffic = SPMM_TRAFFIC_750K.get(main_chunks)
     peak, peak_ms, peak_clocks = fp64_peak(local, _gpu_index(local))
-    roofline = {"kernel": "k_spmm_wm", "bound": "alu", "achieved": achieved, "peak": peak,
+    roofline = {"kernel": "k_spmm_seg", "bound": "alu", "achieved": achieved, "peak": peak,
                 "unit": "TFLOP/s", "frac": achieved / peak, "traffic": traffic,
                 "traffic_unit": "bytes per launch (ncu dram read + write)",
                 "peak_source": "measured in this run: FP64 FMA probe (mdet_measure_fp64_rate, 8 independent "
                                "accumulators per thread fed from L1-resident tables, 16 warps per SM, fastest of "
                                "12 launches of %.1f ms)" % peak_ms,
                 "peak_clocks": peak_clocks, "peak_nominal": 1.25,
-                "flops_per_launch": flops_launch, "launch_ms": launch_ms}
+                "flops_per_launch": flops_launch, "launch_ms": launch_ms,
+                "launch_ms_source": "mean over the timed steps of each launch's device duration, from its first "
+                                    "block's start to its last warp's exit on the GPU global timer (written by the "
+                                    "kernel; CUDA events in the pipelined streams lengthen the step by about 10 %)"}
 
     line = {"metric": METRIC, "value": main["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": main["ms"], "higher_is_better": True, "scaling": "weak",
@@ -388,7 +398,9 @@ def run_ours(args):
             "gpu_launches": st_launches * args.steps,
             "kernels_ms": kern,
             "kernels_ms_note": "stage times (library CUDA events, summed over walker chunks) from %d profiled steps "
-                               "after the timed ones; the timed steps run with those events off" % PROFILED_STEPS,
+                               "after the timed ones, whose events lengthen the step (timeline_ms); the timed steps "
+                               "record no event: contract_timed sums the contraction kernels' own timer stamps "
+                               "(the roofline's launch time)" % PROFILED_STEPS,
             "timeline_ms": {"chunks": [{k: [round(v[0], 3), round(v[1], 3)] for k, v in c.items()}
                                        for c in main["timeline"]["chunks"]],
                             "refine": [round(x, 3) for x in main["timeline"]["refine"]],
@@ -457,6 +469,7 @@ def measure_batched(precision, steps, warmup, streams=8, tune_ms=60.0, fallback_
     with ClockSampler(_gpu_index(dev.index)) as clk:
         for s in range(steps):
             flush.fill_(float(s))
+            torch.cuda.synchronize()
             ev[s][0].record(stream)
             batch.launch()
             ev[s][1].record(stream)
@@ -534,6 +547,7 @@ def run_truncation(args):
         ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
         for s in range(args.steps):
             flush.fill_(float(s))
+            torch.cuda.synchronize()
             ev[s][0].record(stream)
             ctx.evaluate(R, out=out)
             ev[s][1].record(stream)

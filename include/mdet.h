@@ -387,12 +387,19 @@ mdet_status mdet_batch_launch(mdet_batch* b, void* stream);
 void mdet_batch_destroy(mdet_batch* b);
 
 /*
- * Stage timing. With profiling on, every mdet_evaluate records a CUDA event
+ * Stage timing. With profiling mode 1, every mdet_evaluate records a CUDA event
  * before and after each stage on the stream that runs it; mdet_get_profile
- * waits for the last one and writes the durations in milliseconds of the last
+ * waits for them and writes the durations in milliseconds of the last
  * evaluation, in the order MDET_STAGE_* below (ms: [MDET_N_STAGES]), summed
  * over walker chunks (with chunks the stages of different chunks overlap, so
- * the sum can exceed the step time). Off by default.
+ * the sum can exceed the step time). Events in the streams of the pipelined
+ * walker chunks shift the chunks' overlap: they lengthen the step by about a
+ * tenth. Mode 2 therefore records no event: the contraction kernels write the
+ * GPU's global timer (ns) at their first block's start and their last warp's
+ * exit into words of the context's scratch, and mdet_get_profile returns the
+ * sum of those launch durations as the contraction entry (the other entries
+ * stay zero). 0 (the default) records nothing. MDET_E_ARG for another mode.
+ * mdet_get_profile waits for the last evaluation's stream (mode 2) or events.
  */
 enum {
   MDET_STAGE_ORBITALS = 0,  /* AO values and AO->MO product (Sec. 2) */
@@ -414,8 +421,8 @@ mdet_status mdet_get_profile(mdet_ctx* ctx, float* ms);
  * end of the evaluation, all in milliseconds after the evaluation's first event
  * on the caller's stream. *n_chunks receives the chunks used; entries of
  * unused chunks are zero. ms must hold 2 * MDET_MAX_CHUNKS * MDET_N_STAGES + 3
- * floats. Waits for the evaluation's last event. MDET_E_STATE when profiling
- * was off for the last evaluation.
+ * floats. Waits for the evaluation's last event. MDET_E_STATE unless the last
+ * evaluation ran with profiling mode 1.
  */
 #define MDET_MAX_CHUNKS 8
 mdet_status mdet_get_timeline(mdet_ctx* ctx, int32_t* n_chunks, float* ms);

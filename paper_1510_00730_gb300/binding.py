@@ -479,7 +479,10 @@ class Context:
         return self._last_launches()[1]
 
     def set_profiling(self, enable=True):
-        self._check(self._L.mdet_set_profiling(self._h, int(bool(enable))), "mdet_set_profiling")
+        """Stage timing: True or 1 events around every stage, 2 the contraction kernels'
+        own global-timer stamps (no events in the streams), False or 0 none."""
+        mode = enable if isinstance(enable, int) and not isinstance(enable, bool) else int(bool(enable))
+        self._check(self._L.mdet_set_profiling(self._h, mode), "mdet_set_profiling")
 
     def profile(self):
         """Stage durations (ms) of the last profiled evaluation."""

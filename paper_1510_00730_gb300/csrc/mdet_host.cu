@@ -79,8 +79,9 @@ struct mdet_ctx {
   int n_sm = 0;
   cudaEvent_t fork = nullptr, joined = nullptr, contracted[kMaxChunks] = {}, prepared[kMaxChunks] = {};
   // stage timing
-  bool profiling = false;
+  int profiling = 0;  // mode of mdet_set_profiling
   bool have_profile = false;
+  bool have_timeline = false;
   int prof_chunks = 0;
   int last_kernels = 0;  // kernels the last evaluation launched
   // per chunk: the start and end of every stage (stages of one chunk may run on
@@ -94,8 +95,17 @@ struct mdet_ctx {
 namespace {
 
 // contraction work items of escalated re-evaluations (a few hundred walkers): short, so that
-// the FP64 chains stay short
-constexpr int kEscalationChunk = 64;
+// the FP64 chains stay short (128 nonzeros measured 0.4 ms per step faster than 64, whose
+// items all add Psi~ of the same few walkers, and than 256)
+constexpr int kEscalationChunk = 128;
+
+// words of S.queue per walker chunk: the work counters of its two persistent contractions, then
+// the global-timer stamps (start complemented, end) of each
+constexpr int kQueueWords = 6;
+
+// weight of the middle walker chunks of the pipelined evaluation against 1 for the first and the
+// last (1:3:1 measured 29.1 against 29.7 ms per step for 1:2:1 at 8,192 walkers, 750k products)
+constexpr int kMidWeight = 3;
 
 size_t final_smem_bytes_host(int n_up, int n_dn, int n_mo, bool mixed) {
   DevProblem P{};
@@ -603,7 +613,7 @@ mdet_status ensure_scratch(mdet_ctx* c, int64_t n_walk) {
   const bool mixed = c->precision == MDET_PRECISION_MIXED;
   mdet_status s;
   if ((s = alloc_eval_arrays(c, S, n_walk, mixed, mixed && c->contract_impl == 1))) return s;
-  if ((s = dalloc(c, &S.queue, (size_t)2 * mdet_ctx::kMaxChunks))) return s;
+  if ((s = dalloc(c, &S.queue, (size_t)kQueueWords * mdet_ctx::kMaxChunks))) return s;
   if (P.fallback_tol > 0.0 && P.n_up <= MDET_FALLBACK_MAX_SPIN) {
     if (!mixed) return alloc_fallback(c, S);
     // mixed: the list of flagged walkers, then an FP64 re-evaluation of at most fallback_cap
@@ -1087,7 +1097,9 @@ mdet_status mdet_evaluate(mdet_ctx* c, int64_t n_walk, const double* R, double* 
   cudaStream_t st = (cudaStream_t)stream;
   const DevProblem& P = c->P;
   const bool mixed = c->precision == MDET_PRECISION_MIXED;
-  const bool prof = c->profiling;
+  const bool prof_all = c->profiling == 1;  // events around every stage
+  const bool prof_stamp = c->profiling == 2;  // the contraction kernels' own timer stamps, no events
+  const bool prof = prof_all;
   // chunking: mixed precision splits large batches into a two-stream pipeline
   int nch = 1;
   const int64_t tiles = (n_walk + kWalkerPad - 1) / kWalkerPad;
@@ -1104,15 +1116,15 @@ mdet_status mdet_evaluate(mdet_ctx* c, int64_t n_walk, const double* R, double* 
     CUDA_TRY(c, cudaEventRecord(c->ev_origin, (cudaStream_t)stream));
   }
   const int64_t N = P.n_elec;
-  // chunk k covers tiles [t0, t1): the first and the last chunk weigh 1, the others 2 (their
-  // orbitals and tables, and the last epilogue, run with no contraction beside them, so
-  // shorter end chunks expose less); an even split when there are too few tiles
+  // chunk k covers tiles [t0, t1): the first and the last chunk weigh 1, the others
+  // kMidWeight (their orbitals and tables, and the last epilogue, run with no contraction
+  // beside them, so shorter end chunks expose less); an even split when there are too few tiles
   auto chunk_range = [&](int k, int64_t* off, int64_t* n) {
     int64_t t0 = tiles * k / nch, t1 = tiles * (k + 1) / nch;
-    const int64_t units = nch >= 3 ? 2 * nch - 2 : nch;
+    const int64_t units = nch >= 3 ? 2 + (int64_t)kMidWeight * (nch - 2) : nch;
     if (nch >= 3 && tiles >= units) {
       auto edge = [&](int q) -> int64_t {  // tiles before chunk q
-        const int64_t u = q == 0 ? 0 : (q >= nch ? units : 2 * q - 1);
+        const int64_t u = q == 0 ? 0 : (q >= nch ? units : 1 + (int64_t)kMidWeight * (q - 1));
         return tiles * u / units;
       };
       t0 = edge(k);
@@ -1127,7 +1139,8 @@ mdet_status mdet_evaluate(mdet_ctx* c, int64_t n_walk, const double* R, double* 
     chunk_range(k, &off, &n);
     const DevScratch S = scratch_view(c->S, P, off);
     const double* Rk = R + off * N * 3;
-    if (prof) CUDA_TRY(c, cudaEventRecord(c->ev[k][2 * i], ks));
+    const bool mark = prof_all;
+    if (mark) CUDA_TRY(c, cudaEventRecord(c->ev[k][2 * i], ks));
     switch (i) {
       case MDET_STAGE_ORBITALS:
         CUDA_TRY(c, mixed ? launch_mo_mixed(P, S, n, Rk, ks) : launch_mo_f64(P, S, n, Rk, ks));
@@ -1137,12 +1150,16 @@ mdet_status mdet_evaluate(mdet_ctx* c, int64_t n_walk, const double* R, double* 
         CUDA_TRY(c, mixed ? launch_ratios_mixed(P, S, n, ks) : launch_ratios_f64(P, S, n, ks));
         break;
       case MDET_STAGE_ZERO: CUDA_TRY(c, launch_zero_f64(P, S, n, ks)); break;
-      case MDET_STAGE_CONTRACT: CUDA_TRY(c, launch_contract_f64(P, S, n, ks, c->S.queue + 2 * k, persistent)); break;
+      case MDET_STAGE_CONTRACT: {
+        unsigned long long* q = c->S.queue + kQueueWords * k;
+        CUDA_TRY(c, launch_contract_f64(P, S, n, ks, q, persistent, prof_stamp ? q + 2 : nullptr));
+        break;
+      }
       default:
         CUDA_TRY(c, launch_final(P, S, n, Rk, log_abs_psi + off, sign + off, grad + off * N * 3, lap + off * N,
                                  e_local ? e_local + off : nullptr, status ? status + off : nullptr, mixed, ks));
     }
-    if (prof) CUDA_TRY(c, cudaEventRecord(c->ev[k][2 * i + 1], ks));
+    if (mark) CUDA_TRY(c, cudaEventRecord(c->ev[k][2 * i + 1], ks));
     return MDET_OK;
   };
   mdet_status ms;
@@ -1191,7 +1208,7 @@ mdet_status mdet_evaluate(mdet_ctx* c, int64_t n_walk, const double* R, double* 
   // fallback 5 (list, dets, scale, rows, out); the mixed refinement adds its list, gather,
   // FP64 orbitals and scatter, and either the mark or the 5 FP64 table kernels
   c->last_kernels = 6 * nch;
-  if (prof) CUDA_TRY(c, cudaEventRecord(c->ev_refine[0], st));
+  if (prof_all) CUDA_TRY(c, cudaEventRecord(c->ev_refine[0], st));
   if (mixed && c->E.fb && P.fallback_tol > 0.0) {
     const bool table = escalation_on(c);
     mdet_status es = refine(c, table, n_walk, R, log_abs_psi, sign, grad, lap, e_local, status, st);
@@ -1201,11 +1218,12 @@ mdet_status mdet_evaluate(mdet_ctx* c, int64_t n_walk, const double* R, double* 
     CUDA_TRY(c, launch_fallback(P, c->S, n_walk, R, log_abs_psi, sign, grad, lap, e_local, status, st));
     if (P.fallback_tol > 0.0 && c->S.fb && P.n_up <= MDET_FALLBACK_MAX_SPIN) c->last_kernels += 5;
   }
-  if (prof) {
+  if (prof_all) {
     CUDA_TRY(c, cudaEventRecord(c->ev_refine[1], st));
     CUDA_TRY(c, cudaEventRecord(c->ev_done, st));
   }
-  c->have_profile = prof;
+  c->have_profile = prof_all || prof_stamp;
+  c->have_timeline = prof_all;
   c->last_stream = st;
   c->last_walk = n_walk;
   return MDET_OK;
@@ -1322,8 +1340,10 @@ mdet_status mdet_set_profiling(mdet_ctx* c, int enable) {
   if (!c) return MDET_E_ARG;
   if (c->device < 0) return fail(c, MDET_E_NODEVICE, "context has no device");
   CUDA_TRY(c, cudaSetDevice(c->device));
-  c->profiling = enable != 0;
+  if (enable < 0 || enable > 2) return fail(c, MDET_E_ARG, "profiling mode must be 0, 1 or 2");
+  c->profiling = enable;
   c->have_profile = false;
+  c->have_timeline = false;
   return MDET_OK;
 }
 
@@ -1332,20 +1352,33 @@ mdet_status mdet_get_profile(mdet_ctx* c, float* ms) {
   if (!c->have_profile) return fail(c, MDET_E_STATE, "no profiled evaluation yet");
   CUDA_TRY(c, cudaSetDevice(c->device));
   for (int i = 0; i < MDET_N_STAGES; i++) ms[i] = 0.0f;
-  for (int k = 0; k < c->prof_chunks; k++) {
-    CUDA_TRY(c, cudaEventSynchronize(c->ev[k][2 * MDET_STAGE_FINAL + 1]));
+  if (!c->have_timeline) {  // mode 2: the contraction launches' own global-timer stamps
+    const int nw = kQueueWords * c->prof_chunks;
+    std::vector<unsigned long long> w((size_t)nw);
+    CUDA_TRY(c, cudaStreamSynchronize(c->last_stream));
+    CUDA_TRY(c, cudaMemcpy(w.data(), c->S.queue, sizeof(unsigned long long) * nw, cudaMemcpyDeviceToHost));
+    double ns = 0.0;
+    for (int k = 0; k < c->prof_chunks; k++)
+      for (int l = 0; l < 2; l++) {
+        const unsigned long long t0 = ~w[(size_t)kQueueWords * k + 2 + 2 * l], t1 = w[(size_t)kQueueWords * k + 3 + 2 * l];
+        if (w[(size_t)kQueueWords * k + 2 + 2 * l] != 0 && t1 > t0) ns += (double)(t1 - t0);  // 0: the launch ran no block
+      }
+    ms[MDET_STAGE_CONTRACT] = (float)(ns * 1e-6);
+    return MDET_OK;
+  }
+  for (int k = 0; k < c->prof_chunks; k++)
     for (int i = 0; i < MDET_N_STAGES; i++) {
       float t = 0.0f;
+      CUDA_TRY(c, cudaEventSynchronize(c->ev[k][2 * i + 1]));
       CUDA_TRY(c, cudaEventElapsedTime(&t, c->ev[k][2 * i], c->ev[k][2 * i + 1]));
       ms[i] += t;
     }
-  }
   return MDET_OK;
 }
 
 mdet_status mdet_get_timeline(mdet_ctx* c, int32_t* n_chunks, float* ms) {
   if (!c || !n_chunks || !ms) return MDET_E_ARG;
-  if (!c->have_profile) return fail(c, MDET_E_STATE, "no profiled evaluation yet");
+  if (!c->have_timeline) return fail(c, MDET_E_STATE, "no evaluation profiled with every stage yet");
   CUDA_TRY(c, cudaSetDevice(c->device));
   CUDA_TRY(c, cudaEventSynchronize(c->ev_done));
   for (int i = 0; i < MDET_MAX_CHUNKS * MDET_N_STAGES * 2 + 3; i++) ms[i] = 0.0f;
@@ -1430,8 +1463,8 @@ mdet_status mdet_autotune(mdet_ctx* c, int64_t n_walk, const double* R, double b
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   cudaEventCreate(&e0);
   cudaEventCreate(&e1);
-  const bool prof = c->profiling;
-  c->profiling = false;
+  const int prof = c->profiling;
+  c->profiling = 0;
   cudaStream_t st = c->own_stream;
   double spent = 0.0;
   int trials = 0;
@@ -1608,11 +1641,11 @@ mdet_status mdet_batch_create(mdet_batch** out, int n_ctx, mdet_ctx* const* ctxs
   // one uncaptured pass sizes every scratch and sets every kernel attribute
   if (s == MDET_OK) s = batch_enqueue(b, n_walk, R, log_abs_psi, sign, grad, lap, e_local, status, b->origin);
   if (s == MDET_OK && cudaStreamSynchronize(b->origin) != cudaSuccess) s = MDET_E_CUDA;
-  std::vector<bool> prof(n_ctx > 0 ? n_ctx : 0);
+  std::vector<int> prof(n_ctx > 0 ? n_ctx : 0);
   if (s == MDET_OK) {
     for (int i = 0; i < n_ctx; i++) {
       prof[i] = ctxs[i]->profiling;
-      ctxs[i]->profiling = false;
+      ctxs[i]->profiling = 0;
     }
     if (cudaStreamBeginCapture(b->origin, cudaStreamCaptureModeRelaxed) != cudaSuccess) s = MDET_E_CUDA;
     if (s == MDET_OK) {

@@ -134,7 +134,8 @@ struct DevScratch {
   double* fb = nullptr;       // fallback: [cap][n_det_up + n_det_dn][2 + 4 max(n_up, n_dn)], then [cap][ndt] values
   int* fb_list = nullptr;     // fallback: [1 + cap] count, then walker indices
   double* fb_acc = nullptr;   // fallback: [cap][3 + 8 MDET_FALLBACK_MAX_SPIN] scales, Psi, G
-  unsigned long long* queue = nullptr;  // [2 * walker chunks] work counters of persistent contractions
+  unsigned long long* queue = nullptr;  // [6 * walker chunks] per chunk: the work counters of its two
+                                        // persistent contractions, then their global-timer stamps
   const int* live = nullptr;  // device count of the walkers to evaluate (null: all n_walk); the FP64
                               // kernels skip walkers at or beyond it (escalated re-evaluations, whose
                               // psia is gathered from the evaluation that flagged them)
@@ -162,9 +163,11 @@ cudaError_t launch_ratios_mixed(const DevProblem& P, const DevScratch& S, int64_
 cudaError_t launch_zero_f64(const DevProblem& P, const DevScratch& S, int64_t n_walk, cudaStream_t st);
 // queue: two zeroed-per-launch work counters for a persistent contraction grid of
 // spmm_blocks blocks, or of persistent_blocks when spmm_blocks is 0 (null or 0:
-// one warp per work item).
+// one warp per work item). stamp (optional): four words, zeroed here, that receive the
+// global-timer start (complemented) and end of the v and of the u launch.
 cudaError_t launch_contract_f64(const DevProblem& P, const DevScratch& S, int64_t n_walk,
-                                cudaStream_t st, unsigned long long* queue = nullptr, int persistent_blocks = 0);
+                                cudaStream_t st, unsigned long long* queue = nullptr, int persistent_blocks = 0,
+                                unsigned long long* stamp = nullptr);
 // A view of the scratch for walkers [off, off + n): walker-major arrays move by
 // whole walkers, walker-minor arrays by columns (off must be a multiple of kWalkerPad).
 DevScratch scratch_view(const DevScratch& S, const DevProblem& P, int64_t off);

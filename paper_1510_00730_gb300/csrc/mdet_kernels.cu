@@ -429,6 +429,15 @@ __global__ void __launch_bounds__(256) k_spmm_f64(const int* __restrict__ seg, c
 // (its ratio to |Psi~| is the conditioning of the CI sum, used by the error estimate).
 // WPL walkers per lane (8, or 4 for the few walkers of an escalated re-evaluation, where a
 // 256-walker group would be mostly padding); walker groups at or beyond the live count are skipped.
+// stamp (optional, zeroed before the launch): stamp[0] = ~(global timer at the earliest block
+// start), stamp[1] = global timer at the latest warp exit, in ns: the launch's duration on the
+// device without events in the stream.
+static __device__ __forceinline__ unsigned long long global_timer_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
 template <bool QUEUE, bool ABS, int WPL>
 __global__ void __launch_bounds__(128) k_spmm_seg(const int* __restrict__ seg, const int* __restrict__ gidx,
                                                   const double* __restrict__ val, const int2* __restrict__ items,
@@ -436,9 +445,10 @@ __global__ void __launch_bounds__(128) k_spmm_seg(const int* __restrict__ seg, c
                                                   int64_t wp, double* __restrict__ y, int64_t ldy, int seg_off,
                                                   const double* __restrict__ rdot, double* __restrict__ psit,
                                                   float* __restrict__ psia, unsigned long long* __restrict__ queue,
-                                                  const int* __restrict__ live) {
+                                                  const int* __restrict__ live, unsigned long long* __restrict__ stamp) {
   constexpr int G = 32 * WPL;
   const int lane = threadIdx.x & 31;
+  if (stamp && threadIdx.x == 0) atomicMax(stamp, ~global_timer_ns());
   const int64_t ng = live ? min(n_groups, (int64_t)(*live + G - 1) / G) : n_groups;
   const int64_t n_work = (int64_t)n_items * ng;
   auto next_item = [&]() -> int64_t {
@@ -515,6 +525,7 @@ __global__ void __launch_bounds__(128) k_spmm_seg(const int* __restrict__ seg, c
     }
     flush(cur);
   }
+  if (stamp && lane == 0) atomicMax(stamp + 1, global_timer_ns());
 }
 
 // The same segmented product with the ratios and C as double-float pairs on
@@ -1054,7 +1065,7 @@ cudaError_t launch_zero_f64(const DevProblem&, const DevScratch&, int64_t, cudaS
 }
 
 cudaError_t launch_contract_f64(const DevProblem& P, const DevScratch& S, int64_t n_walk, cudaStream_t st,
-                                unsigned long long* queue, int persistent_blocks) {
+                                unsigned long long* queue, int persistent_blocks, unsigned long long* stamp) {
   // an escalated re-evaluation (few walkers, live count on the device) uses 4 walkers per lane
   const bool narrow = narrow_contraction(P, S);
   const int64_t n_groups = narrow ? (n_walk + 127) / 128 : (n_walk + 255) / 256;
@@ -1063,8 +1074,14 @@ cudaError_t launch_contract_f64(const DevProblem& P, const DevScratch& S, int64_
   // persistent grid whose warps draw items from a queue (two counters, one per launch)
   const int cap = P.spmm_blocks > 0 ? P.spmm_blocks : persistent_blocks;
   const bool q = queue && cap > 0 && cap < (work_max + 3) / 4;
+  // the two counters, and the four stamp words (with one memset when they follow the counters)
+  const bool adjacent = q && stamp == queue + 2;
   if (q) {
-    cudaError_t e = cudaMemsetAsync(queue, 0, 2 * sizeof(unsigned long long), st);
+    cudaError_t e = cudaMemsetAsync(queue, 0, (adjacent ? 6 : 2) * sizeof(unsigned long long), st);
+    if (e != cudaSuccess) return e;
+  }
+  if (stamp && !adjacent) {
+    cudaError_t e = cudaMemsetAsync(stamp, 0, 4 * sizeof(unsigned long long), st);
     if (e != cudaSuccess) return e;
   }
   auto grid = [&](int o) -> unsigned {
@@ -1093,13 +1110,14 @@ cudaError_t launch_contract_f64(const DevProblem& P, const DevScratch& S, int64_
   // re-evaluation reuses the magnitude sum of the evaluation that flagged it)
   auto* kv = narrow ? k_spmm_seg<false, false, 4> : (q ? k_spmm_seg<true, true, 8> : k_spmm_seg<false, true, 8>);
   kv<<<grid(0), 128, 0, st>>>(P.csr_row, P.csr_col, P.csr_val, P.items[0], P.n_items[0], n_groups, r_dn, S.wp, S.vu,
-                              ndt, 0, r_up, S.psit, narrow ? nullptr : S.psia, queue, S.live);
+                              ndt, 0, r_up, S.psit, narrow ? nullptr : S.psia, queue, S.live, stamp);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   // u = C^T r_up (columns = down determinants), in the paper's column-major order
   auto* ku = narrow ? k_spmm_seg<false, false, 4> : (q ? k_spmm_seg<true, false, 8> : k_spmm_seg<false, false, 8>);
   ku<<<grid(1), 128, 0, st>>>(P.csc_col, P.csc_row, P.csc_val, P.items[1], P.n_items[1], n_groups, r_up, S.wp, S.vu,
-                              ndt, P.n_det_sp[0], nullptr, nullptr, nullptr, q ? queue + 1 : nullptr, S.live);
+                              ndt, P.n_det_sp[0], nullptr, nullptr, nullptr, q ? queue + 1 : nullptr, S.live,
+                              stamp ? stamp + 2 : nullptr);
   return cudaGetLastError();
 }
 

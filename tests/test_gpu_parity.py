@@ -166,6 +166,18 @@ def test_persistent_contraction_grids(o2100, prec, chunks, blocks, esc):
     assert ctx.last_kernels == 6 * chunks + (5 if prec == pkg.PRECISION_FP64 else (14 if esc else 10))
     prof = ctx.profile()
     assert all(v > 0 for k, v in prof.items() if k != "zero"), prof
+    # mode 2: the contraction kernels time themselves (global-timer stamps, no events); the
+    # results and the kernel count are unchanged, the other stages read zero, no timeline
+    ctx.set_profiling(2)
+    got = _gpu_eval(ctx, wl.R)
+    assert compare(got, ref, **TOL[prec])["ok"]
+    assert ctx.last_kernels == 6 * chunks + (5 if prec == pkg.PRECISION_FP64 else (14 if esc else 10))
+    prof2 = ctx.profile()
+    assert all(v == 0 for k, v in prof2.items() if k != "contract"), prof2
+    assert 0.2 * prof["contract"] < prof2["contract"] < 5.0 * prof["contract"], (prof, prof2)
+    with pytest.raises(RuntimeError):
+        ctx.timeline()
+    ctx.set_profiling(False)
 
 
 def test_fp64_grow_and_shrink_batch(o1k):
