@@ -28,10 +28,10 @@ UNIT = "walker-steps/s"
 CPU_SAMPLE_WALKERS = 96     # bounded oracle sample for the CPU baseline (~10-30 s of CPU work)
 CPU_SINGLE_CORE_WALKERS = 8  # the same oracle on one core, for the per-core figure
 # dram__bytes_read.sum + dram__bytes_write.sum of the average k_spmm_seg launch on the 750k workload
-# with 8,192 walkers in three walker chunks, from one ncu capture of the current kernel (the v and u
-# launches of chunks 0 and 1; chunk 2 has chunk 0's size and is counted with its figures); null
-# for a chunking that was not captured
-SPMM_TRAFFIC_750K = {3: 182.1e6}
+# with 8,192 walkers, from one ncu capture of the current kernel per (precision, walker chunks):
+# mixed in three chunks (the v and u launches of chunks 0 and 1; chunk 2 has chunk 0's size and is
+# counted with its figures), FP64 in one; null for a configuration that was not captured
+SPMM_TRAFFIC_750K = {("mixed", 3): 176.3e6, ("fp64", 1): 602.1e6}
 
 
 def _env_int(k, d):
@@ -369,7 +369,7 @@ def run_ours(args):
     achieved = flops_launch / (launch_ms / 1e3) / 1e12
     traffic = args.traffic
     if traffic is None and args.workload == "chlorine_like_750k" and W == 8192:
-        traffic = SPMM_TRAFFIC_750K.get(main_chunks)
+        traffic = SPMM_TRAFFIC_750K.get((primary, main_chunks))
     peak, peak_ms, peak_clocks = fp64_peak(local, _gpu_index(local))
     roofline = {"kernel": "k_spmm_seg", "bound": "alu", "achieved": achieved, "peak": peak,
                 "unit": "TFLOP/s", "frac": achieved / peak, "traffic": traffic,
