@@ -448,10 +448,10 @@ mdet_status mdet_get_timeline(mdet_ctx* ctx, int32_t* n_chunks, float* ms);
  * return. Fails with MDET_E_ARG when (n_det_up + 1) * ld exceeds
  * MDET_NOALLOC_SCRATCH_DOUBLES (checked without forming the product, so any ld
  * is safe to pass). The first call on
- * a device looks up the array's device address (cudaGetSymbolAddress) and
- * should come before any stream capture on that device. Every call shares the
- * one array and leaves its contents behind; it clears what it uses before use,
- * and calls that overlap on the GPU (other streams, other threads) race.
+ * a device looks up the array's device address (cudaGetSymbolAddress). Every
+ * call shares the one array and leaves its contents behind; it clears what it
+ * uses before use, and calls that overlap on the GPU (other streams, other
+ * threads) race.
  */
 #define MDET_NOALLOC_SCRATCH_DOUBLES (4u * 1024u * 1024u)
 mdet_status mdet_psi_tilde_noalloc(mdet_ctx* ctx, int64_t n_walk, const double* r, int64_t ld,
