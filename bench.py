@@ -659,54 +659,38 @@ def run_learned(args):
     number of steps from the same walkers. value = autocorrelation-corrected
     samples/s of <E_L> with the learned move (walker-steps/s / tau_int(E_L),
     Sokal window c = 5); the drift-diffusion chain is reported beside it."""
-    import math
-
     import torch
 
     import paper_1510_00730_gb300 as pkg
-    from paper_1510_00730_gb300 import binding as B
     from paper_1510_00730_gb300 import synth
-    from paper_1510_00730_gb300.vmc import VMC, measure_chain, train_esjd
+    from paper_1510_00730_gb300.vmc import learned_vs_drift_diffusion
     torch.cuda.set_device(0)
     wl = synth.chlorine_like_100k(n_walk=8192)
     prec = {"mixed": pkg.PRECISION_MIXED, "fp64": pkg.PRECISION_FP64}[args.precision]
     ctx = pkg.Context.from_workload(wl, device=0, precision=prec)
     tau = 3e-5
     n_chain = max(args.steps, 100)
-    dd = VMC(ctx, wl.R, seed=2, drift_tau=tau)
-    dd.run(500, tau=tau, record=False)
-    R_eq = dd.cur["R"].clone()
-    t0 = time.perf_counter()
-    R_data, lp_data, F_data = dd.collect_configs(tau, (1 << 20) // wl.n_walk)
-    torch.cuda.synchronize()
-    collect_s = time.perf_counter() - t0
-    mlp = B.MLP(0, wl.n_elec, hidden=256, seed=3, mu_max=1.0, s0=0.5 * math.log(tau), s_span=3.0)
-    t0 = time.perf_counter()
-    hist = train_esjd(mlp, ctx, R_data, lp_data, F_data, tau, epochs=3, batch=8192, lr=1e-4, speed_beta=0.1,
-                      target_acc=0.5)
-    torch.cuda.synchronize()
-    train_s = time.perf_counter() - t0
     with ClockSampler(_gpu_index(0)) as clk:
-        # the plain method: drift-diffusion without drift capping, tau at ~50 % acceptance
-        base = measure_chain(ctx, R_eq, n_chain, tau, seed=5, warmup=args.warmup, drift_a=0.0)
-        limited = measure_chain(ctx, R_eq, n_chain, tau, seed=5, warmup=args.warmup, drift_a=1.0)
-        learned = measure_chain(ctx, R_eq, n_chain, tau, mlp=mlp, seed=6, warmup=args.warmup, drift_a=1.0)
+        r = learned_vs_drift_diffusion(ctx, wl.R, tau, n_chain, warmup=args.warmup)
+    learned = r["learned"]
     line = {"metric": "autocorrelation-corrected samples/s of <E_L>, learned proposal vs drift-diffusion",
             "value": learned["samples_per_s"], "unit": "samples/s", "n_gpus": 1, "steps": n_chain,
             "warmup": args.warmup, "ms_per_step": learned["ms_per_step"], "higher_is_better": True,
             "dtype": "f64+f32x2" if prec == pkg.PRECISION_MIXED else "f64", "data": "synthetic",
             "config": {"workload": "learned_proposal_100k", "walkers": wl.n_walk, "n_det": int(wl.n_det),
-                       "tau": tau, "drift_limit_a": 1.0, "training_configs": int(R_data.shape[0]),
-                       "mlp": "51-256-256-68 tanh, BF16 weights, FP32 accumulation",
-                       "objective": "generalised speed measure, target acceptance 0.4"},
-            "learned": learned, "drift_diffusion": base, "drift_diffusion_limited": limited,
-            "gain": learned["samples_per_s"] / base["samples_per_s"],
-            "gain_vs_limited": learned["samples_per_s"] / limited["samples_per_s"],
-            "training": {"collect_s": collect_s, "train_s": train_s,
-                         "objective_acceptance_per_epoch": hist},
+                       "tau": tau, "drift_limit_a": 1.0, "training_configs": r["training_configs"],
+                       "mlp": "51-256-256-68 tanh on tcgen05 tensor cores: BF16 weights and activations, "
+                              "FP32 accumulation",
+                       "objective": "generalised speed measure, target acceptance 0.5"},
+            "learned": learned, "drift_diffusion": r["drift_diffusion"],
+            "drift_diffusion_limited": r["drift_diffusion_limited"],
+            "gain": r["gain"], "gain_err": r["gain_err"], "gain_vs_limited": r["gain_vs_limited"],
+            "gain_vs_limited_err": r["gain_vs_limited_err"],
+            "training": {"collect_s": r["collect_s"], "train_s": r["train_s"],
+                         "objective_acceptance_per_epoch": r["objective_acceptance_per_epoch"]},
             "clocks": clk.summary()}
     print(json.dumps(line), flush=True)
-    mlp.close()
+    ctx.close()
 
 
 def main():

@@ -95,13 +95,31 @@ mdet_status mdet_vmc_r2(int64_t n_walk, int n_elec, const double* R, double* r2,
 
 /* ---- the learned proposal ---------------------------------------------- */
 
+/*
+ * The perceptron's matrix product, exposed for testing and reuse (no paper
+ * counterpart): D[m][n] = sum_k bf16(A[m][k]) bf16(B[n][k]) for m < M, n < N,
+ * k < K on the tcgen05 tensor cores (operands rounded to BF16, nearest even;
+ * FP32 accumulation in tensor memory). A is M x K row-major with leading
+ * dimension lda, B is N x K row-major with ldb, D is M x N with ldd; all FP32
+ * and on the device. accumulate = 0: D is overwritten (k_split is ignored);
+ * 1: the product is added to D with FP32 atomics, the K range split over CTAs
+ * of k_split (rounded up to 64) each. Asynchronous on `stream`. MDET_E_ARG on a
+ * negative size, a null pointer with a nonzero size or a leading dimension
+ * below the row length; MDET_E_CUDA on a launch error.
+ */
+mdet_status mdet_gemm_bf16(int64_t M, int64_t N, int64_t K, const float* A, int64_t lda, const float* B, int64_t ldb,
+                           float* D, int64_t ldd, int accumulate, int64_t k_split, void* stream);
+
 typedef struct mdet_mlp mdet_mlp;
 
 /*
  * A 3-layer perceptron n_in -> hidden -> hidden -> n_out with tanh after the
  * two hidden layers, for n_in = 3 n_elec and n_out = 4 n_elec. Master weights
- * are FP32 (Adam state alongside); forward and backward use BF16 copies of the
- * weights with FP32 accumulation. Weights are drawn from U(-a, a) with
+ * are FP32 (Adam state alongside). Every product of the forward and backward
+ * passes runs on the tcgen05 tensor cores (mdet_gemm_bf16 below): BF16 copies of
+ * the weights, the activations and back-propagated deltas rounded to BF16 as
+ * they enter a product, FP32 accumulation; the tanh derivatives and the bias
+ * gradients use the unrounded FP32 values. Weights are drawn from U(-a, a) with
  * a = sqrt(6 / (fan_in + fan_out)) (Glorot) by Philox with `seed`, biases 0.
  * Parameter order everywhere: W1 [n_in][hidden], b1 [hidden], W2 [hidden][hidden],
  * b2 [hidden], W3 [hidden][n_out], b3 [n_out] (W[k][j]: input k, output j).

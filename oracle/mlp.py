@@ -45,16 +45,24 @@ def bf16_round(a):
     return b.astype(np.uint32).view(np.float32).astype(np.float64)
 
 
-def forward(p, R, n_elec, H, coord_scale, weights_bf16=True):
+def forward(p, R, n_elec, H, coord_scale, weights_bf16=True, acts_bf16=False):
+    """Network output [B][4N] and the intermediates (x, h1, h2, W1, W2, W3).
+
+    weights_bf16: the weights enter the products rounded to BF16 (the stored copy).
+    acts_bf16: every product's other operand is rounded to BF16 too (x, h1, h2 here),
+    which is the arithmetic of a BF16 x BF16 tensor-core product with FP32 accumulation;
+    the tanh derivatives use the unrounded activations.
+    """
     n_in, n_out = 3 * n_elec, 4 * n_elec
     W1, b1, W2, b2, W3, b3 = unpack(p, n_in, H, n_out)
     if weights_bf16:
         W1, W2, W3 = bf16_round(W1), bf16_round(W2), bf16_round(W3)
+    rnd = bf16_round if acts_bf16 else (lambda a: a)
     x = np.asarray(R, dtype=np.float64).reshape(len(R), n_in) / coord_scale
     x = x.astype(np.float32).astype(np.float64)
-    h1 = np.tanh(x @ W1 + b1)
-    h2 = np.tanh(h1 @ W2 + b2)
-    out = h2 @ W3 + b3
+    h1 = np.tanh(rnd(x) @ W1 + b1)
+    h2 = np.tanh(rnd(h1) @ W2 + b2)
+    out = rnd(h2) @ W3 + b3
     return out, (x, h1, h2, W1, W2, W3)
 
 
@@ -78,10 +86,13 @@ def log_q(R_to, R_from, out_from, n_elec, mu_max, s0, s_span, F_from=None):
     return -0.5 * (d ** 2).sum(1) - 3.0 * s.sum(1)
 
 
-def nll_and_grad(p, R0, R1, n_elec, H, coord_scale, mu_max, s0, s_span, weights_bf16=True):
-    """Loss and its gradient with respect to the parameter vector (backpropagation)."""
+def nll_and_grad(p, R0, R1, n_elec, H, coord_scale, mu_max, s0, s_span, weights_bf16=True, acts_bf16=False):
+    """Loss and its gradient with respect to the parameter vector (backpropagation).
+    acts_bf16: as in forward, and in the backward products both operands (activations,
+    deltas) are rounded to BF16 as well; the bias gradients sum the unrounded deltas."""
     B = len(R0)
-    out, (x, h1, h2, W1, W2, W3) = forward(p, R0, n_elec, H, coord_scale, weights_bf16)
+    rnd = bf16_round if acts_bf16 else (lambda a: a)
+    out, (x, h1, h2, W1, W2, W3) = forward(p, R0, n_elec, H, coord_scale, weights_bf16, acts_bf16)
     tm = np.tanh(out[:, :3 * n_elec])
     ts = np.tanh(out[:, 3 * n_elec:])
     s = s0 + s_span * ts
@@ -97,13 +108,13 @@ def nll_and_grad(p, R0, R1, n_elec, H, coord_scale, mu_max, s0, s_span, weights_
     dmu = -d * np.repeat(iv, 3, axis=1)
     ds = 3 - (d2 + dmu_s) * iv
     dout = np.concatenate([dmu * sig3 * mu_max * (1 - tm ** 2), ds * s_span * (1 - ts ** 2)], axis=1) / B
-    gW3 = h2.T @ dout
+    gW3 = rnd(h2).T @ rnd(dout)
     gb3 = dout.sum(0)
-    dh2 = (dout @ W3.T) * (1 - h2 ** 2)
-    gW2 = h1.T @ dh2
+    dh2 = (rnd(dout) @ W3.T) * (1 - h2 ** 2)
+    gW2 = rnd(h1).T @ rnd(dh2)
     gb2 = dh2.sum(0)
-    dh1 = (dh2 @ W2.T) * (1 - h1 ** 2)
-    gW1 = x.T @ dh1
+    dh1 = (rnd(dh2) @ W2.T) * (1 - h1 ** 2)
+    gW1 = rnd(x).T @ rnd(dh1)
     gb1 = dh1.sum(0)
     g = np.concatenate([gW1.ravel(), gb1, gW2.ravel(), gb2, gW3.ravel(), gb3])
     return loss, g, dout

@@ -137,7 +137,8 @@ def load_library(build_if_missing: bool = True):
     L.mdet_mlp_esjd_grad.argtypes = [vp, i64, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp, C.c_int, C.c_double,
                                      C.c_double, vp, vp, vp, vp]
     L.mdet_vmc_reverse_mlp.argtypes = [vp, i64, vp, vp, vp, vp, vp, vp]
-    for n in ("mdet_vmc_propose_drift", "mdet_vmc_reverse_drift", "mdet_vmc_accept", "mdet_vmc_r2",
+    L.mdet_gemm_bf16.argtypes = [i64, i64, i64, vp, i64, vp, i64, vp, i64, i32, i64, vp]
+    for n in ("mdet_gemm_bf16", "mdet_vmc_propose_drift", "mdet_vmc_reverse_drift", "mdet_vmc_accept", "mdet_vmc_r2",
               "mdet_vmc_select_rows", "mdet_vmc_limit_drift",
               "mdet_mlp_create", "mdet_mlp_get_params", "mdet_mlp_set_params", "mdet_mlp_get_grads",
               "mdet_mlp_forward", "mdet_mlp_backward", "mdet_mlp_zero_grad", "mdet_mlp_adam", "mdet_mlp_nll_grad",
@@ -629,6 +630,28 @@ def _sp(stream, dev):
 def _chk(st, what):
     if st:
         raise MdetError(st, "%s failed: %s" % (what, load_library().mdet_status_string(st).decode()))
+
+
+def gemm_bf16(A, B, D=None, accumulate=False, k_split=1024, stream=None):
+    """D = bf16(A) bf16(B)^T on the tcgen05 tensor cores (FP32 accumulation): A [M][K] and
+    B [N][K] FP32 CUDA tensors with unit inner stride; D [M][N] FP32, allocated when None.
+    accumulate adds into D (atomics, K split over CTAs of k_split)."""
+    import torch
+    L = load_library()
+    if A.dim() != 2 or B.dim() != 2 or A.shape[1] != B.shape[1]:
+        raise ValueError("A [M][K] and B [N][K] expected")
+    for t, name in ((A, "A"), (B, "B")):
+        if t.dtype != torch.float32 or not t.is_cuda or t.stride(1) != 1:
+            raise ValueError("%s: FP32 CUDA tensor with unit inner stride expected" % name)
+    M, K = A.shape
+    N = B.shape[0]
+    if D is None:
+        D = torch.zeros(M, N, dtype=torch.float32, device=A.device)
+    elif D.shape != (M, N) or D.dtype != torch.float32 or D.stride(1) != 1 or D.device != A.device:
+        raise ValueError("D: FP32 [M][N] tensor with unit inner stride on A's device expected")
+    _chk(L.mdet_gemm_bf16(M, N, K, A.data_ptr(), A.stride(0), B.data_ptr(), B.stride(0), D.data_ptr(), D.stride(0),
+                          int(bool(accumulate)), int(k_split), _sp(stream, A.device)), "mdet_gemm_bf16")
+    return D
 
 
 def philox4x32_10(ctr, key):

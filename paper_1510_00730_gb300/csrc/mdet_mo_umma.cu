@@ -36,6 +36,7 @@
 #include "df32.cuh"
 #include "mdet_device.cuh"
 #include "mdet_internal.h"
+#include "umma.cuh"
 
 namespace mdet {
 
@@ -47,71 +48,7 @@ constexpr int kMaxKp = 112;        // AOs (padded to 16) for which the order sum
 constexpr int kThreads = 256;
 constexpr int kWaitLimit = 1 << 26;        // polls of an mbarrier before a CTA gives up
 
-__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
-
-// Shared-memory matrix descriptor of tcgen05: K-major operand of 8-row x 16-byte
-// core matrices without swizzle; lbo = byte distance between core matrices along K,
-// sbo = between 8-row groups; bits 46-48 hold the descriptor version 1.
-__device__ __forceinline__ uint64_t umma_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
-  return (uint64_t)((saddr & 0x3FFFFu) >> 4) | ((uint64_t)((lbo >> 4) & 0x3FFFu) << 16) |
-         ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | ((uint64_t)1 << 46);
-}
-
-// Instruction descriptor of kind::f16: FP32 accumulator, BF16 A and B, both K-major.
-__host__ __device__ constexpr uint32_t umma_idesc_bf16(int m, int n) {
-  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(m >> 4) << 24);
-}
-
-__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
-}
-
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
-  uint32_t done = 0;
-  for (int it = 0; it < kWaitLimit && !done; it++)
-    asm volatile(
-        "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}"
-        : "=r"(done)
-        : "r"(smem_u32(bar)), "r"(parity)
-        : "memory");
-  return done != 0;
-}
-
-__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
-  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
-}
-
-__device__ __forceinline__ void tc_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
-__device__ __forceinline__ void tc_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
-
-__device__ __forceinline__ void tmem_st8(uint32_t taddr, const uint32_t (&v)[8]) {
-  asm volatile("tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8};" ::"r"(taddr), "r"(v[0]),
-               "r"(v[1]), "r"(v[2]), "r"(v[3]), "r"(v[4]), "r"(v[5]), "r"(v[6]), "r"(v[7])
-               : "memory");
-}
-
-__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&v)[16]) {
-  asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
-      : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]), "=r"(v[8]),
-        "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
-      : "r"(taddr)
-      : "memory");
-  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-}
-
-// D (+)= A B with A in tensor memory and B described in shared memory.
-__device__ __forceinline__ void umma_tmem_a(uint32_t d, uint32_t a, uint64_t bdesc, uint32_t idesc, uint32_t acc) {
-  asm volatile(
-      "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\ntcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, %3, p;\n}" ::"r"(d),
-      "r"(a), "l"(bdesc), "r"(idesc), "r"(acc)
-      : "memory");
-}
-
-__device__ __forceinline__ void umma_commit(uint64_t* bar) {
-  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
-               : "memory");
-}
+using umma::smem_u32;
 
 // acc + x (x a single float) in double-float
 __device__ __forceinline__ df32 df_add_f(df32 a, float x) {
@@ -144,23 +81,20 @@ __global__ void __maxnreg__(96) k_mo_umma(DevProblem P, float2* __restrict__ phi
   const int q = warp & 3, h = warp >> 2;  // TMEM lane quarter (MOs 32q..32q+31) and column half of the drains
 
   if (warp == 0) {
-    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tbase)),
-                 "r"(ncols)
-                 : "memory");
-    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    umma::tmem_alloc(&tbase, ncols);
   }
   if (tid == 0) {
-    mbar_init(&full[0], 1);
-    mbar_init(&full[1], 1);
-    mbar_init(&empty[0], kThreads / 32);
-    mbar_init(&empty[1], kThreads / 32);
-    mbar_init(&fin, 1);
+    umma::mbar_init(&full[0], 1);
+    umma::mbar_init(&full[1], 1);
+    umma::mbar_init(&empty[0], kThreads / 32);
+    umma::mbar_init(&empty[1], kThreads / 32);
+    umma::mbar_init(&fin, 1);
     *stop = 0;
   }
   for (int i = tid; i < 5 * Kp * kNE; i += kThreads) X[i] = make_float2(0.0f, 0.0f);  // AO padding stays zero
-  tc_before();
+  umma::fence_before();
   __syncthreads();
-  tc_after();
+  umma::fence_after();
   const uint32_t tb = tbase;
   const uint32_t lane_q = (uint32_t)(32 * q) << 16;
   // MO digit planes into TMEM (warps q and q + 4 share a lane quarter and split the planes)
@@ -173,15 +107,15 @@ __global__ void __maxnreg__(96) k_mo_umma(DevProblem P, float2* __restrict__ phi
         for (int x = 0; x < 8; x++)
           v[x] = m < Mp ? __ldg(reinterpret_cast<const unsigned int*>(P.B_dig + ((size_t)j * Mp + m) * Kp + 2 * (c0 + x)))
                         : 0u;
-        tmem_st8(tb + lane_q + (uint32_t)(j * (Kp / 2) + c0), v);
+        umma::tmem_st8(tb + lane_q + (uint32_t)(j * (Kp / 2) + c0), v);
       }
     asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
   }
-  tc_before();
+  umma::fence_before();
   __syncthreads();
-  tc_after();
+  umma::fence_after();
 
-  const uint32_t idesc = umma_idesc_bf16(128, kNE);
+  const uint32_t idesc = umma::idesc_bf16(128, kNE);
   const uint32_t planes_s = smem_u32(planes);
   uint32_t u = 0;  // orders issued so far by this CTA (the same count in every thread)
   // the MMAs of order t into accumulator (uu & 1), after its previous use has been drained
@@ -189,22 +123,22 @@ __global__ void __maxnreg__(96) k_mo_umma(DevProblem P, float2* __restrict__ phi
     const int b = uu & 1;
     if (*stop) return;
     if (uu >= 2) {
-      if (!mbar_wait(&empty[b], ((uu - 2) >> 1) & 1)) {
+      if (!umma::mbar_wait(&empty[b], ((uu - 2) >> 1) & 1, kWaitLimit)) {
         *stop = 1;
         return;
       }
-      tc_after();
+      umma::fence_after();
     }
     uint32_t acc = 0;
     for (int i = max(1, t - kDigits); i <= min(kDigits, t - 1); i++) {
       const int j = t - i;
       for (int ks = 0; ks < Kp / 16; ks++) {
-        const uint64_t bd = umma_desc(planes_s + (uint32_t)((i - 1) * plane_bytes + ks * 256), 128, (uint32_t)sbo);
-        umma_tmem_a(tb + dcol0 + 32u * b, tb + (uint32_t)((j - 1) * (Kp / 2) + ks * 8), bd, idesc, acc);
+        const uint64_t bd = umma::desc(planes_s + (uint32_t)((i - 1) * plane_bytes + ks * 256), 128, (uint32_t)sbo);
+        umma::mma_tmem_a(tb + dcol0 + 32u * b, tb + (uint32_t)((j - 1) * (Kp / 2) + ks * 8), bd, idesc, acc);
         acc = 1;
       }
     }
-    umma_commit(&full[b]);
+    umma::commit(&full[b]);
   };
 
   for (int64_t tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
@@ -278,9 +212,9 @@ __global__ void __maxnreg__(96) k_mo_umma(DevProblem P, float2* __restrict__ phi
           *reinterpret_cast<uint4*>(dst + i * plane_bytes) = make_uint4(w[i][0], w[i][1], w[i][2], w[i][3]);
       }
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-      tc_before();
+      umma::fence_before();
       __syncthreads();
-      tc_after();
+      umma::fence_after();
       // orders t = 2..8: MMAs of t + 1 in flight while every warp drains t
       df32 acc[16];
 #pragma unroll
@@ -291,19 +225,19 @@ __global__ void __maxnreg__(96) k_mo_umma(DevProblem P, float2* __restrict__ phi
         if (tid == 0 && t < 8) issue(t + 1, u + 1);
         __syncwarp();
         const int b = u & 1;
-        const bool ok = !*stop && mbar_wait(&full[b], (u >> 1) & 1);
+        const bool ok = !*stop && umma::mbar_wait(&full[b], (u >> 1) & 1, kWaitLimit);
         if (!ok) *stop = 1;
-        tc_after();
+        umma::fence_after();
         if (32 * q < M && __all_sync(0xffffffffu, ok)) {  // lane quarters beyond the MOs hold zeros
           uint32_t v[16];
-          tmem_ld16(tb + lane_q + dcol0 + 32u * b + 16 * h, v);
+          umma::tmem_ld16(tb + lane_q + dcol0 + 32u * b + 16 * h, v);
           const float scale = __uint_as_float((uint32_t)(127 - 8 * t) << 23);  // 2^(-8 t)
 #pragma unroll
           for (int j = 0; j < 16; j++) acc[j] = df_add_f(acc[j], __fmul_rn(__uint_as_float(v[j]), scale));
         }
-        tc_before();
+        umma::fence_before();
         __syncwarp();
-        if (lane == 0) mbar_arrive(&empty[b]);
+        if (lane == 0) umma::mbar_arrive(&empty[b]);
       }
       // Phi[w][c][e][m] = 2^(er + f_m) acc as a double-float pair
       const int m = 32 * q + lane;
@@ -319,19 +253,19 @@ __global__ void __maxnreg__(96) k_mo_umma(DevProblem P, float2* __restrict__ phi
               *stop ? make_float2(__int_as_float(0x7fc00000), 0.0f) : make_float2(ldexpf(acc[j].hi, E), ldexpf(acc[j].lo, E));
         }
       }
-      tc_before();
+      umma::fence_before();
       __syncthreads();  // digit planes and row exponents are rewritten by the next quantity
-      tc_after();
+      umma::fence_after();
     }
   }
-  tc_before();
+  umma::fence_before();
   __syncthreads();
   if (*stop && tid == 0) {  // after a wait ran out: let the MMAs in flight finish (bounded) before the release
-    umma_commit(&fin);
-    mbar_wait(&fin, 0);
+    umma::commit(&fin);
+    umma::mbar_wait(&fin, 0, kWaitLimit);
   }
   __syncthreads();
-  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tb), "r"(ncols) : "memory");
+  if (warp == 0) umma::tmem_dealloc(tb, ncols);
 }
 
 }  // namespace

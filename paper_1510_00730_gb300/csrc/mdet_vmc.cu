@@ -8,6 +8,7 @@
 // Normal variates by the Box-Muller transform of two uniforms in (0, 1).
 #include <cuda_bf16.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstring>
 #include <new>
@@ -15,6 +16,14 @@
 
 #include "../../include/mdet_vmc.h"
 #include "mdet_internal.h"
+
+using mdet::GemmEpilogue;
+using mdet::GemmOperand;
+using mdet::kEpiAtomic;
+using mdet::kEpiBias;
+using mdet::kEpiDtanh;
+using mdet::kEpiTanhBias;
+using mdet::launch_gemm_bf16;
 
 namespace {
 
@@ -171,193 +180,39 @@ struct mdet_mlp {
   float *p = nullptr, *g = nullptr, *m1 = nullptr, *m2 = nullptr;
   __nv_bfloat16* pb = nullptr;
   int64_t cap = 0;
-  float *x = nullptr, *h1 = nullptr, *h2 = nullptr;
+  // per walker: input, hidden activations (FP32, kept for the backward pass) and the
+  // back-propagated deltas of the two hidden layers
+  float *x = nullptr, *h1 = nullptr, *h2 = nullptr, *d1 = nullptr, *d2 = nullptr;
 };
 
 namespace {
 
-constexpr int kTW = 32;  // walkers per block in the network kernels
+constexpr int kCapRound = 128;  // scratch rows are allocated in multiples of one GEMM tile
 
-struct MlpView {
-  int n_in, H, n_out;
-  float inv_scale;
-  const float* p;
-  const __nv_bfloat16* pb;
-  float* g;
-  int64_t oW1, ob1, oW2, ob2, oW3, ob3;
-  float *x, *h1, *h2;
+// x = R / coord_scale in FP32, the network's input, kept for the backward pass.
+__global__ void k_mlp_input(int64_t n, const double* __restrict__ R, float inv_scale, float* __restrict__ x) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) x[i] = (float)R[i] * inv_scale;
+}
+
+// Bias gradients: gb[n] += sum over walkers of d[w][n] for up to three (d, width, gb) jobs
+// (blockIdx.z); each thread sums one column over a slice of the walkers.
+struct ColSumJob {
+  const float* d;
+  int width;
+  float* gb;
 };
-
-MlpView view(const mdet_mlp* m) {
-  return MlpView{m->n_in, m->H, m->n_out, (float)(1.0 / m->coord_scale), m->p, m->pb, m->g,
-                 m->oW1, m->ob1, m->oW2, m->ob2, m->oW3, m->ob3, m->x, m->h1, m->h2};
-}
-
-__device__ __forceinline__ float wt(const __nv_bfloat16* pb, int64_t i) { return __bfloat162float(pb[i]); }
-
-// Forward: block = H threads (one per hidden unit), kTW walkers per block.
-// smem: xs[kTW][n_in], h1s[kTW][H], h2s[kTW][H].
-__global__ void k_mlp_fwd(MlpView V, int64_t n_walk, const double* __restrict__ R, float* __restrict__ out) {
-  extern __shared__ float sm[];
-  const int n_in = V.n_in, H = V.H, n_out = V.n_out;
-  float* xs = sm;
-  float* h1s = xs + kTW * n_in;
-  float* h2s = h1s + kTW * H;
-  const int64_t w0 = (int64_t)blockIdx.x * kTW;
-  const int tw = (int)min((int64_t)kTW, n_walk - w0);
-  for (int t = threadIdx.x; t < kTW * n_in; t += blockDim.x) {
-    const int r = t / n_in, k = t - r * n_in;
-    const float v = r < tw ? (float)R[(w0 + r) * n_in + k] * V.inv_scale : 0.0f;
-    xs[t] = v;
-    if (r < tw) V.x[(w0 + r) * n_in + k] = v;
-  }
-  __syncthreads();
-  const int j = threadIdx.x;
-  float acc[kTW];
-  // layer 1
-  if (j < H) {
-#pragma unroll
-    for (int r = 0; r < kTW; r++) acc[r] = V.p[V.ob1 + j];
-    for (int k = 0; k < n_in; k++) {
-      const float wv = wt(V.pb, V.oW1 + (int64_t)k * H + j);
-#pragma unroll
-      for (int r = 0; r < kTW; r++) acc[r] = fmaf(wv, xs[r * n_in + k], acc[r]);
-    }
-#pragma unroll
-    for (int r = 0; r < kTW; r++) {
-      const float h = tanhf(acc[r]);
-      h1s[r * H + j] = h;
-      if (r < tw) V.h1[(w0 + r) * H + j] = h;
-    }
-  }
-  __syncthreads();
-  // layer 2
-  if (j < H) {
-#pragma unroll
-    for (int r = 0; r < kTW; r++) acc[r] = V.p[V.ob2 + j];
-    for (int k = 0; k < H; k++) {
-      const float wv = wt(V.pb, V.oW2 + (int64_t)k * H + j);
-#pragma unroll
-      for (int r = 0; r < kTW; r++) acc[r] = fmaf(wv, h1s[r * H + k], acc[r]);
-    }
-#pragma unroll
-    for (int r = 0; r < kTW; r++) {
-      const float h = tanhf(acc[r]);
-      h2s[r * H + j] = h;
-      if (r < tw) V.h2[(w0 + r) * H + j] = h;
-    }
-  }
-  __syncthreads();
-  // layer 3 (linear)
-  for (int jo = threadIdx.x; jo < n_out; jo += blockDim.x) {
-#pragma unroll
-    for (int r = 0; r < kTW; r++) acc[r] = V.p[V.ob3 + jo];
-    for (int k = 0; k < H; k++) {
-      const float wv = wt(V.pb, V.oW3 + (int64_t)k * n_out + jo);
-#pragma unroll
-      for (int r = 0; r < kTW; r++) acc[r] = fmaf(wv, h2s[r * H + k], acc[r]);
-    }
-    for (int r = 0; r < tw; r++) out[(w0 + r) * n_out + jo] = acc[r];
-  }
-}
-
-// Backward: block = H threads, kTW walkers. Weight gradients are summed over
-// the block's walkers, then added to the global gradient with one atomic per
-// weight. smem: xs, h1s, h2s, dos[kTW][n_out], d2s[kTW][H], d1s[kTW][H].
-__global__ void k_mlp_bwd(MlpView V, int64_t n_walk, const float* __restrict__ dout) {
-  extern __shared__ float sm[];
-  const int n_in = V.n_in, H = V.H, n_out = V.n_out;
-  float* xs = sm;
-  float* h1s = xs + kTW * n_in;
-  float* h2s = h1s + kTW * H;
-  float* dos = h2s + kTW * H;
-  float* d2s = dos + kTW * n_out;
-  float* d1s = d2s + kTW * H;
-  const int64_t w0 = (int64_t)blockIdx.x * kTW;
-  const int tw = (int)min((int64_t)kTW, n_walk - w0);
-  for (int t = threadIdx.x; t < kTW * n_in; t += blockDim.x) {
-    const int r = t / n_in;
-    xs[t] = r < tw ? V.x[w0 * n_in + t] : 0.0f;
-  }
-  for (int t = threadIdx.x; t < kTW * H; t += blockDim.x) {
-    const int r = t / H;
-    h1s[t] = r < tw ? V.h1[w0 * H + t] : 0.0f;
-    h2s[t] = r < tw ? V.h2[w0 * H + t] : 0.0f;
-  }
-  for (int t = threadIdx.x; t < kTW * n_out; t += blockDim.x) {
-    const int r = t / n_out;
-    dos[t] = r < tw ? dout[w0 * n_out + t] : 0.0f;
-  }
-  __syncthreads();
-  const int k = threadIdx.x;  // hidden unit
-  // layer 3: dW3[k][j] = sum_r h2[r][k] dout[r][j]; db3; dh2 = W3 dout (1 - h2^2)
-  if (k < H) {
-    for (int j = 0; j < n_out; j++) {
-      float s = 0.0f;
-#pragma unroll 8
-      for (int r = 0; r < kTW; r++) s = fmaf(h2s[r * H + k], dos[r * n_out + j], s);
-      if (s != 0.0f) atomicAdd(V.g + V.oW3 + (int64_t)k * n_out + j, s);
-    }
-    float acc[kTW];
-#pragma unroll
-    for (int r = 0; r < kTW; r++) acc[r] = 0.0f;
-    for (int j = 0; j < n_out; j++) {
-      const float wv = wt(V.pb, V.oW3 + (int64_t)k * n_out + j);
-#pragma unroll
-      for (int r = 0; r < kTW; r++) acc[r] = fmaf(wv, dos[r * n_out + j], acc[r]);
-    }
-#pragma unroll
-    for (int r = 0; r < kTW; r++) {
-      const float h = h2s[r * H + k];
-      d2s[r * H + k] = acc[r] * (1.0f - h * h);
-    }
-  }
-  for (int j = threadIdx.x; j < n_out; j += blockDim.x) {
-    float s = 0.0f;
-    for (int r = 0; r < kTW; r++) s += dos[r * n_out + j];
-    if (s != 0.0f) atomicAdd(V.g + V.ob3 + j, s);
-  }
-  __syncthreads();
-  // layer 2: dW2[k][j] = sum_r h1[r][k] d2[r][j] (thread j), db2; dh1 = W2 d2 (1 - h1^2) (thread k)
-  if (k < H) {
-    const int j = k;
-    float sb = 0.0f;
-    for (int r = 0; r < kTW; r++) sb += d2s[r * H + j];
-    if (sb != 0.0f) atomicAdd(V.g + V.ob2 + j, sb);
-    for (int kk = 0; kk < H; kk++) {
-      float s = 0.0f;
-#pragma unroll 8
-      for (int r = 0; r < kTW; r++) s = fmaf(h1s[r * H + kk], d2s[r * H + j], s);
-      if (s != 0.0f) atomicAdd(V.g + V.oW2 + (int64_t)kk * H + j, s);
-    }
-    float acc[kTW];
-#pragma unroll
-    for (int r = 0; r < kTW; r++) acc[r] = 0.0f;
-    for (int jj = 0; jj < H; jj++) {
-      const float wv = wt(V.pb, V.oW2 + (int64_t)k * H + jj);
-#pragma unroll
-      for (int r = 0; r < kTW; r++) acc[r] = fmaf(wv, d2s[r * H + jj], acc[r]);
-    }
-#pragma unroll
-    for (int r = 0; r < kTW; r++) {
-      const float h = h1s[r * H + k];
-      d1s[r * H + k] = acc[r] * (1.0f - h * h);
-    }
-  }
-  __syncthreads();
-  // layer 1: dW1[kk][j] = sum_r x[r][kk] d1[r][j] (thread j), db1
-  if (k < H) {
-    const int j = k;
-    float sb = 0.0f;
-    for (int r = 0; r < kTW; r++) sb += d1s[r * H + j];
-    if (sb != 0.0f) atomicAdd(V.g + V.ob1 + j, sb);
-    for (int kk = 0; kk < n_in; kk++) {
-      float s = 0.0f;
-#pragma unroll 8
-      for (int r = 0; r < kTW; r++) s = fmaf(xs[r * n_in + kk], d1s[r * H + j], s);
-      if (s != 0.0f) atomicAdd(V.g + V.oW1 + (int64_t)kk * H + j, s);
-    }
-  }
+struct ColSumJobs {
+  ColSumJob j[3];
+};
+__global__ void k_bias_grad(ColSumJobs jobs, int64_t n_walk, int64_t per) {
+  const ColSumJob J = jobs.j[blockIdx.z];
+  const int n = blockIdx.x * blockDim.x + threadIdx.x;
+  if (n >= J.width) return;
+  const int64_t w0 = (int64_t)blockIdx.y * per, w1 = min(n_walk, w0 + per);
+  float s = 0.0f;
+  for (int64_t w = w0; w < w1; w++) s += J.d[w * J.width + n];
+  if (s != 0.0f) atomicAdd(J.gb + n, s);
 }
 
 __global__ void k_adam(int64_t n, float* __restrict__ p, const float* __restrict__ g, float* __restrict__ m1,
@@ -580,12 +435,16 @@ mdet_status ensure_mlp_scratch(mdet_mlp* m, int64_t n_walk) {
   cudaFree(m->x);
   cudaFree(m->h1);
   cudaFree(m->h2);
-  m->x = m->h1 = m->h2 = nullptr;
+  cudaFree(m->d1);
+  cudaFree(m->d2);
+  m->x = m->h1 = m->h2 = m->d1 = m->d2 = nullptr;
   m->cap = 0;
-  const int64_t cap = (n_walk + kTW - 1) / kTW * kTW;
+  const int64_t cap = (n_walk + kCapRound - 1) / kCapRound * kCapRound;
   if (cudaMalloc((void**)&m->x, sizeof(float) * cap * m->n_in) != cudaSuccess ||
       cudaMalloc((void**)&m->h1, sizeof(float) * cap * m->H) != cudaSuccess ||
-      cudaMalloc((void**)&m->h2, sizeof(float) * cap * m->H) != cudaSuccess)
+      cudaMalloc((void**)&m->h2, sizeof(float) * cap * m->H) != cudaSuccess ||
+      cudaMalloc((void**)&m->d1, sizeof(float) * cap * m->H) != cudaSuccess ||
+      cudaMalloc((void**)&m->d2, sizeof(float) * cap * m->H) != cudaSuccess)
     return MDET_E_OOM;
   m->cap = cap;
   return MDET_OK;
@@ -725,6 +584,8 @@ void mdet_mlp_destroy(mdet_mlp* m) {
   cudaFree(m->x);
   cudaFree(m->h1);
   cudaFree(m->h2);
+  cudaFree(m->d1);
+  cudaFree(m->d2);
   delete m;
 }
 
@@ -759,21 +620,59 @@ mdet_status mdet_mlp_forward(mdet_mlp* m, int64_t n_walk, const double* R, float
   if (cudaSetDevice(m->device) != cudaSuccess) return MDET_E_CUDA;
   mdet_status s = ensure_mlp_scratch(m, n_walk);
   if (s != MDET_OK) return s;
-  const size_t smem = sizeof(float) * kTW * (m->n_in + 2 * m->H);
-  if (cudaFuncSetAttribute(k_mlp_fwd, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
-    return MDET_E_CUDA;
-  k_mlp_fwd<<<blocks(n_walk, kTW), m->H, smem, (cudaStream_t)stream>>>(view(m), n_walk, R, out);
-  return cuda_status(cudaGetLastError());
+  const cudaStream_t st = (cudaStream_t)stream;
+  const int64_t ni = m->n_in, H = m->H, no = m->n_out;
+  k_mlp_input<<<blocks(n_walk * ni, 256), 256, 0, st>>>(n_walk * ni, R, (float)(1.0 / m->coord_scale), m->x);
+  cudaError_t e = cudaGetLastError();
+  // layer l: A = the walkers' activations [n_walk][K], B = W_l^T read from the BF16 copy
+  // W_l[K][width] (row n of B is column n of W_l)
+  const __nv_bfloat16* pb = m->pb;
+  auto layer = [&](const float* a, int64_t K, int64_t oW, int64_t width, int kind, int64_t ob, float* o) {
+    const GemmOperand A{a, K, 1, n_walk, K, 0};
+    const GemmOperand B{pb + oW, 1, width, width, K, 1};
+    const GemmEpilogue E{kind, o, width, 1, m->p + ob, nullptr, 0};
+    return launch_gemm_bf16(A, B, K, E, st);
+  };
+  if (e == cudaSuccess) e = layer(m->x, ni, m->oW1, H, kEpiTanhBias, m->ob1, m->h1);
+  if (e == cudaSuccess) e = layer(m->h1, H, m->oW2, H, kEpiTanhBias, m->ob2, m->h2);
+  if (e == cudaSuccess) e = layer(m->h2, H, m->oW3, no, kEpiBias, m->ob3, out);
+  return cuda_status(e);
 }
 
 mdet_status mdet_mlp_backward(mdet_mlp* m, int64_t n_walk, const float* dout, void* stream) {
   if (!m || n_walk < 0 || !dout || n_walk > m->cap) return MDET_E_ARG;
   if (n_walk == 0) return MDET_OK;
   if (cudaSetDevice(m->device) != cudaSuccess) return MDET_E_CUDA;
-  const size_t smem = sizeof(float) * kTW * (m->n_in + 4 * m->H + m->n_out);
-  if (cudaFuncSetAttribute(k_mlp_bwd, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
-    return MDET_E_CUDA;
-  k_mlp_bwd<<<blocks(n_walk, kTW), m->H, smem, (cudaStream_t)stream>>>(view(m), n_walk, dout);
+  const cudaStream_t st = (cudaStream_t)stream;
+  const int64_t ni = m->n_in, H = m->H, no = m->n_out;
+  const __nv_bfloat16* pb = m->pb;
+  // deltas: d2 = (dout W3^T) (1 - h2^2), d1 = (d2 W2^T) (1 - h1^2); B = W_l itself, row n of
+  // W_l[n][.] over its width
+  const GemmOperand Dout{dout, no, 1, n_walk, no, 0};
+  cudaError_t e = launch_gemm_bf16(Dout, GemmOperand{pb + m->oW3, no, 1, H, no, 1}, no,
+                                   GemmEpilogue{kEpiDtanh, m->d2, H, 1, nullptr, m->h2, H}, st);
+  if (e == cudaSuccess)
+    e = launch_gemm_bf16(GemmOperand{m->d2, H, 1, n_walk, H, 0}, GemmOperand{pb + m->oW2, H, 1, H, H, 1}, H,
+                         GemmEpilogue{kEpiDtanh, m->d1, H, 1, nullptr, m->h1, H}, st);
+  // weight gradients, summed over the walkers (the GEMMs' K), 1,024 walkers per CTA:
+  // gW3[k][j] = sum_w h2[w][k] dout[w][j], gW2[k][j] = sum_w h1[w][k] d2[w][j],
+  // gW1[i][j] = sum_w x[w][i] d1[w][j] (computed as its transpose: rows j, columns i)
+  const int64_t kpc = 1024;
+  if (e == cudaSuccess)
+    e = launch_gemm_bf16(GemmOperand{m->h2, 1, H, H, n_walk, 0}, GemmOperand{dout, 1, no, no, n_walk, 0}, kpc,
+                         GemmEpilogue{kEpiAtomic, m->g + m->oW3, no, 1, nullptr, nullptr, 0}, st);
+  if (e == cudaSuccess)
+    e = launch_gemm_bf16(GemmOperand{m->h1, 1, H, H, n_walk, 0}, GemmOperand{m->d2, 1, H, H, n_walk, 0}, kpc,
+                         GemmEpilogue{kEpiAtomic, m->g + m->oW2, H, 1, nullptr, nullptr, 0}, st);
+  if (e == cudaSuccess)
+    e = launch_gemm_bf16(GemmOperand{m->d1, 1, H, H, n_walk, 0}, GemmOperand{m->x, 1, ni, ni, n_walk, 0}, kpc,
+                         GemmEpilogue{kEpiAtomic, m->g + m->oW1, 1, H, nullptr, nullptr, 0}, st);
+  if (e != cudaSuccess) return cuda_status(e);
+  // bias gradients from the unrounded deltas
+  const ColSumJobs jobs{{{dout, (int)no, m->g + m->ob3}, {m->d2, (int)H, m->g + m->ob2}, {m->d1, (int)H, m->g + m->ob1}}};
+  const int64_t per = 256;
+  const dim3 grid(blocks(std::max(no, H), 128), (unsigned)((n_walk + per - 1) / per), 3);
+  k_bias_grad<<<grid, 128, 0, st>>>(jobs, n_walk, per);
   return cuda_status(cudaGetLastError());
 }
 

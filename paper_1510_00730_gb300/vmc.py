@@ -306,12 +306,71 @@ def measure_chain(ctx, R0, n_steps, tau, mlp=None, mix_drift=0.0, seed=11, warmu
     r2, el, acc, _ = v.run(n_steps, tau=tau, mlp=mlp, mix_drift=mix_drift)
     k = min(n_steps, 200)
     _, _, _, dt = v.run(k, tau=tau, mlp=mlp, mix_drift=mix_drift, record=False)
-    t_el, _ = tau_int(el)
+    t_el, win = tau_int(el)
     t_r2, _ = tau_int(r2)
     m, e = mean_and_error(r2, t_r2)
     sps = dt / k
-    return {"acceptance": acc, "tau_int": t_el, "tau_int_r2": t_r2, "ms_per_step": 1e3 * sps,
-            "samples_per_s": v.W / sps / t_el, "r2": m, "r2_err": e, "steps": n_steps}
+    t_err = tau_int_error(t_el, win, *np.asarray(el).shape)
+    sp = v.W / sps / t_el
+    return {"acceptance": acc, "tau_int": t_el, "tau_int_err": t_err, "tau_window": win, "tau_int_r2": t_r2,
+            "ms_per_step": 1e3 * sps, "samples_per_s": sp, "samples_per_s_err": sp * t_err / t_el,
+            "r2": m, "r2_err": e, "steps": n_steps}
+
+
+def tau_int_error(tau, M, n_steps, n_walkers):
+    """Statistical error of tau_int from Sokal's window estimate, var(tau) ~ 2 (2M + 1) / N tau^2
+    for one series of N steps (Madras and Sokal, J. Stat. Phys. 50, 109 (1988)); the
+    autocorrelation here is averaged over independent walkers, which divides the variance
+    by their number."""
+    return float(tau * np.sqrt(2.0 * (2 * M + 1) / (n_steps * max(n_walkers, 1))))
+
+
+def learned_vs_drift_diffusion(ctx, R, tau, n_chain, warmup=100, n_configs=1 << 20, hidden=256, seed=3):
+    """The learned proposal against drift-diffusion on one context (config 5 of the brief,
+    run by `bench.py --workload learned_proposal_100k` and by the GPU tests):
+    1. 500 steps of drift-diffusion with the drift limiter equilibrate the walkers R;
+    2. the same chain collects about n_configs configurations;
+    3. the perceptron is trained on them on the GPU (generalised speed measure, target
+       acceptance 0.5, 3 epochs);
+    4. three chains of n_chain recorded steps run from the same equilibrated walkers:
+       plain drift-diffusion (no drift capping), drift-diffusion with the limiter, and the
+       learned move with the limiter.
+    Returns the three chains' measurements, the gains of the learned move in
+    autocorrelation-corrected samples/s of <E_L> with their errors (relative errors of the
+    two samples/s added in quadrature), and the training record."""
+    import torch
+    W = len(R)
+    dd = VMC(ctx, R, seed=2, drift_tau=tau)
+    dd.run(500, tau=tau, record=False)
+    R_eq = dd.cur["R"].clone()
+    t0 = time.perf_counter()
+    R_data, lp_data, F_data = dd.collect_configs(tau, max(1, n_configs // W))
+    torch.cuda.synchronize()
+    collect_s = time.perf_counter() - t0
+    mlp = B.MLP(ctx.device, ctx.n_up + ctx.n_dn, hidden=hidden, seed=seed, mu_max=1.0, s0=0.5 * math.log(tau), s_span=3.0)
+    try:
+        t0 = time.perf_counter()
+        hist = train_esjd(mlp, ctx, R_data, lp_data, F_data, tau, epochs=3, batch=min(W, 8192), lr=1e-4,
+                          speed_beta=0.1, target_acc=0.5)
+        torch.cuda.synchronize()
+        train_s = time.perf_counter() - t0
+        base = measure_chain(ctx, R_eq, n_chain, tau, seed=5, warmup=warmup, drift_a=0.0)
+        limited = measure_chain(ctx, R_eq, n_chain, tau, seed=5, warmup=warmup, drift_a=1.0)
+        learned = measure_chain(ctx, R_eq, n_chain, tau, mlp=mlp, seed=6, warmup=warmup, drift_a=1.0)
+    finally:
+        mlp.close()
+
+    def gain(a, b):
+        g = a["samples_per_s"] / b["samples_per_s"]
+        r = math.hypot(a["samples_per_s_err"] / a["samples_per_s"], b["samples_per_s_err"] / b["samples_per_s"])
+        return g, g * r
+
+    g_plain, e_plain = gain(learned, base)
+    g_lim, e_lim = gain(learned, limited)
+    return {"learned": learned, "drift_diffusion": base, "drift_diffusion_limited": limited,
+            "gain": g_plain, "gain_err": e_plain, "gain_vs_limited": g_lim, "gain_vs_limited_err": e_lim,
+            "training_configs": int(R_data.shape[0]), "collect_s": collect_s, "train_s": train_s,
+            "objective_acceptance_per_epoch": hist}
 
 
 def tau_int(x, c=5.0):

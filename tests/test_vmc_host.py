@@ -56,6 +56,48 @@ def test_reference_mlp_gradient_vs_finite_differences():
         assert abs(fd - g[i]) <= 1e-6 * max(1.0, abs(g[i])), (i, fd, g[i])
 
 
+def _one_unit_net():
+    """n_elec = 1 (3 inputs, 4 outputs), one hidden unit per layer: W1 = e_0, W2 = 1,
+    W3 = e_0, zero biases, so out[0] = tanh(tanh(x_0)) along a single path."""
+    W1 = [1.0, 0.0, 0.0]
+    W3 = [1.0, 0.0, 0.0, 0.0]
+    return np.array(W1 + [0.0] + [1.0] + [0.0] + W3 + [0.0] * 4)
+
+
+def test_bf16_activation_rounding_points():
+    """The tensor-core arithmetic (acts_bf16): each product's activation operand is
+    rounded to BF16, 8 significant bits, nearest even. Hand-worked on x_0 = 1 + 2^-10:
+    - x_0 rounds to 1.0, so h1 = tanh(1) = 0.76159415595..., 194.968 units of 2^-8;
+    - h1 rounds to 195 * 2^-8 = 0.76171875, so h2 = tanh(0.76171875) = 0.64208822...,
+      164.375 units of 2^-8;
+    - h2 rounds to 164 * 2^-8 = 0.640625, which is the output exactly.
+    Without the rounding the output is tanh(tanh(1 + 2^-10))."""
+    p = _one_unit_net()
+    R = np.array([[[1.0 + 2.0 ** -10, 0.0, 0.0]]])
+    out, (x, h1, h2, *_) = omlp.forward(p, R, 1, 1, 1.0, weights_bf16=True, acts_bf16=True)
+    assert out[0, 0] == 0.640625 and np.all(out[0, 1:] == 0.0)
+    assert h1[0, 0] == np.tanh(1.0)  # x rounded before the first product
+    assert h2[0, 0] == np.tanh(0.76171875)  # h1 rounded before the second
+    plain, _ = omlp.forward(p, R, 1, 1, 1.0, weights_bf16=True, acts_bf16=False)
+    assert plain[0, 0] == np.tanh(np.tanh(1.0 + 2.0 ** -10))
+
+
+def test_bf16_activation_gradient_stays_near_the_exact_one():
+    """Rounding every product's operands to BF16 moves the backpropagated gradient by a
+    few 2^-9 relative rounding errors, never by more than a percent of its norm."""
+    rng = np.random.default_rng(4)
+    n_e, H = 3, 16
+    n_in, n_out = 3 * n_e, 4 * n_e
+    p = rng.normal(scale=0.4, size=n_in * H + H + H * H + H + H * n_out + n_out)
+    R0 = rng.normal(scale=1.2, size=(64, n_e, 3))
+    R1 = R0 + rng.normal(scale=0.2, size=R0.shape)
+    args = (R0, R1, n_e, H, 2.0, 0.8, -2.0, 1.5)
+    l0, g0, _ = omlp.nll_and_grad(p, *args)
+    l1, g1, _ = omlp.nll_and_grad(p, *args, acts_bf16=True)
+    assert abs(l1 - l0) <= 1e-2 * abs(l0)
+    assert 0.0 < np.linalg.norm(g1 - g0) <= 1e-2 * np.linalg.norm(g0)
+
+
 def test_tau_int_ar1_closed_form():
     """For an AR(1) series x_t = phi x_{t-1} + noise, tau_int = (1 + phi) / (1 - phi)."""
     rng = np.random.default_rng(2)
