@@ -114,6 +114,33 @@ static __device__ __forceinline__ df32 operator*(df32 x, df32 y) {
   return {s, t};
 }
 
+// Compensated sum of products of double-float numbers: the dot product Dot2 of Ogita,
+// Rump and Oishi (SIAM J. Sci. Comput. 26, 2005) with double-float inputs. Each term
+// x y adds its leading product hi_x hi_y into the running FP32 sum s through TwoSum; the
+// product's rounding error (from FMA), the cross terms hi_x lo_y + lo_x hi_y and TwoSum's
+// error go into a second FP32 word c. The pair (s, c) carries the sum with an error of
+// order n^2 2^-48 sum |x y| like the double-float operations above, at about 12 FP32
+// instructions per term instead of 27 for a double-float product and sum.
+struct df_dot {
+  float s = 0.0f, c = 0.0f;
+  __device__ __forceinline__ void add(df32 x, df32 y) {
+    const float p = __fmul_rn(x.hi, y.hi);
+    const float pe = __fmaf_rn(x.hi, y.hi, -p);
+    const float cross = __fmaf_rn(x.hi, y.lo, __fmul_rn(x.lo, y.hi));
+    float t, e;
+    two_sum(s, p, t, e);
+    s = t;
+    c = __fadd_rn(c, __fadd_rn(e, __fadd_rn(pe, cross)));
+  }
+  __device__ __forceinline__ void sub(df32 x, df32 y) { add(df32(-x.hi, -x.lo), y); }
+  // the sum as a normalised double-float pair
+  __device__ __forceinline__ df32 value() const {
+    float h, l;
+    two_sum(s, c, h, l);
+    return {h, l};
+  }
+};
+
 // exp(t) for t <= 0 in double-float. Cody-Waite reduction t = k ln2 + r with
 // ln2 split into three floats of 16, 24 and 24 significant bits (k * kLn2a is
 // exact for |k| < 256 and k * kLn2b is made exact with TwoProd), so r carries

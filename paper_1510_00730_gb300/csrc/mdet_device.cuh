@@ -111,6 +111,73 @@ static __device__ __forceinline__ void small_cof(int k, const F (&m)[4][4], F (&
 }
 
 
+// Cofactors of a K x K double-float matrix (K <= 4, compile time), as small_cof: the
+// 2 x 2 minors and the expansions of the 3 x 3 ones are compensated dot products
+// (df_dot) instead of double-float products and sums.
+template <int K>
+static __device__ __forceinline__ void small_cof_dot(const df32 (&m)[4][4], df32 (&cof)[4][4]) {
+  auto minor2 = [](df32 a, df32 b, df32 c, df32 d) {  // a d - b c
+    df_dot t;
+    t.add(a, d);
+    t.sub(b, c);
+    return t.value();
+  };
+  if constexpr (K == 1) {
+    cof[0][0] = df32(1.0f, 0.0f);
+  } else if constexpr (K == 2) {
+    cof[0][0] = m[1][1];
+    cof[0][1] = -m[1][0];
+    cof[1][0] = -m[0][1];
+    cof[1][1] = m[0][0];
+  } else if constexpr (K == 3) {
+#pragma unroll
+    for (int a = 0; a < 3; a++)
+#pragma unroll
+      for (int b = 0; b < 3; b++) {
+        const int r0 = a == 0 ? 1 : 0, r1 = a == 2 ? 1 : 2;
+        const int c0 = b == 0 ? 1 : 0, c1 = b == 2 ? 1 : 2;
+        const df32 d = minor2(m[r0][c0], m[r0][c1], m[r1][c0], m[r1][c1]);
+        cof[a][b] = ((a + b) & 1) ? -d : d;
+      }
+  } else {
+    // 2 x 2 minors of rows (0,1) and (2,3) for column pairs (x < y), then each 3 x 3 minor
+    // expanded along the row that shares its pair with the removed row
+    df32 top[4][4], bot[4][4];
+#pragma unroll
+    for (int x = 0; x < 4; x++)
+#pragma unroll
+      for (int y = x + 1; y < 4; y++) {
+        top[x][y] = minor2(m[0][x], m[0][y], m[1][x], m[1][y]);
+        bot[x][y] = minor2(m[2][x], m[2][y], m[3][x], m[3][y]);
+      }
+#pragma unroll
+    for (int a = 0; a < 4; a++) {
+      const int rho = a < 2 ? 1 - a : 5 - a;
+#pragma unroll
+      for (int b = 0; b < 4; b++) {
+        int cols[3];
+        int q = 0;
+#pragma unroll
+        for (int x = 0; x < 4; x++)
+          if (x != b) cols[q++] = x;
+        df_dot d;
+#pragma unroll
+        for (int t = 0; t < 3; t++) {
+          const int x = t == 0 ? cols[1] : cols[0];
+          const int y = t == 2 ? cols[1] : cols[2];
+          const df32 d2 = a < 2 ? bot[x][y] : top[x][y];
+          if (t & 1)
+            d.sub(m[rho][cols[t]], d2);
+          else
+            d.add(m[rho][cols[t]], d2);
+        }
+        const df32 v = d.value();
+        cof[a][b] = ((a + b) & 1) ? -v : v;
+      }
+    }
+  }
+}
+
 // Values, gradient and Laplacian of the (l+1)(l+2)/2 Cartesian AOs of one shell
 // at one point (FP64). AO chi = P(x, y, z) f(r^2) with P = x^a y^b z^c of degree
 // l and f(s) = sum_p c_p exp(-alpha_p s):
