@@ -103,9 +103,13 @@ constexpr int kEscalationChunk = 128;
 // the global-timer stamps (start complemented, end) of each
 constexpr int kQueueWords = 6;
 
-// weight of the middle walker chunks of the pipelined evaluation against 1 for the first and the
-// last (1:3:1 measured 29.1 against 29.7 ms per step for 1:2:1 at 8,192 walkers, 750k products)
-constexpr int kMidWeight = 3;
+// weights of the first, each middle and the last walker chunk of the pipelined evaluation. The
+// first chunk's orbitals and tables run before any contraction, and the last chunk's epilogue
+// after all of them, so both are kept short; but the epilogue of the chunk before the last runs
+// beside the last contraction, which must stay long enough to hide it. At 8,192 walkers (32
+// tiles), 750k products, 6:21:5 tiles measured 28.62 ms per step against 28.73 for 6:19:7,
+// 29.1-29.3 for 6:22:4 and 5:22:5, and 29.6-29.8 for four chunks.
+constexpr int kFirstWeight = 6, kMidWeight = 21, kLastWeight = 5;
 
 size_t final_smem_bytes_host(int n_up, int n_dn, int n_mo, bool mixed) {
   DevProblem P{};
@@ -1116,16 +1120,17 @@ mdet_status mdet_evaluate(mdet_ctx* c, int64_t n_walk, const double* R, double* 
     CUDA_TRY(c, cudaEventRecord(c->ev_origin, (cudaStream_t)stream));
   }
   const int64_t N = P.n_elec;
-  // chunk k covers tiles [t0, t1): the first and the last chunk weigh 1, the others
-  // kMidWeight (their orbitals and tables, and the last epilogue, run with no contraction
-  // beside them, so shorter end chunks expose less); an even split when there are too few tiles
+  // chunk k covers tiles [t0, t1) in the proportions kFirstWeight : kMidWeight ... : kLastWeight
+  // (with at least one tile each), an even split with fewer than 3 chunks
   auto chunk_range = [&](int k, int64_t* off, int64_t* n) {
     int64_t t0 = tiles * k / nch, t1 = tiles * (k + 1) / nch;
-    const int64_t units = nch >= 3 ? 2 + (int64_t)kMidWeight * (nch - 2) : nch;
-    if (nch >= 3 && tiles >= units) {
+    const int64_t units = kFirstWeight + (int64_t)kMidWeight * (nch - 2) + kLastWeight;
+    if (nch >= 3 && tiles >= nch) {
       auto edge = [&](int q) -> int64_t {  // tiles before chunk q
-        const int64_t u = q == 0 ? 0 : (q >= nch ? units : 1 + (int64_t)kMidWeight * (q - 1));
-        return tiles * u / units;
+        if (q <= 0) return 0;
+        if (q >= nch) return tiles;
+        const int64_t u = kFirstWeight + (int64_t)kMidWeight * (q - 1);
+        return std::min(std::max(tiles * u / units, (int64_t)q), tiles - (nch - q));
       };
       t0 = edge(k);
       t1 = edge(k + 1);
