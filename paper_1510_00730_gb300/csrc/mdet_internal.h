@@ -148,8 +148,6 @@ cudaError_t launch_mo_f64(const DevProblem& P, const DevScratch& S, int64_t n_wa
                           const double* R, cudaStream_t st);
 cudaError_t launch_mo_mixed(const DevProblem& P, const DevScratch& S, int64_t n_walk,
                             const double* R, cudaStream_t st);
-// The mixed orbitals on the tcgen05 tensor cores (mdet_mo_umma.cu): supported for
-// at most 112 AOs and 128 MOs; launch_mo_mixed takes it when mo_impl is 2.
 // Dense BF16 GEMM on tcgen05 tensor cores with a fused epilogue (csrc/mdet_gemm_umma.cu).
 // Element (r, k) of an operand is p[r * rs + k * ks] (FP32, or BF16 when bf16 != 0), zero for
 // r >= rows or k >= cols; D[m][n] = sum_k A[m][k] B[n][k] over K = A.cols (= B.cols), the
@@ -172,6 +170,8 @@ struct GemmEpilogue {
 cudaError_t launch_gemm_bf16(const GemmOperand& A, const GemmOperand& B, int64_t k_per_cta, const GemmEpilogue& E,
                              cudaStream_t st);
 
+// The mixed orbitals on the tcgen05 tensor cores (mdet_mo_umma.cu): supported for
+// at most 112 AOs and 128 MOs; launch_mo_mixed takes it when mo_impl is 2.
 bool mo_umma_supported(const DevProblem& P);
 size_t mo_umma_smem_bytes(const DevProblem& P);
 cudaError_t launch_mo_umma(const DevProblem& P, const DevScratch& S, int64_t n_walk, const double* R, int n_sm,

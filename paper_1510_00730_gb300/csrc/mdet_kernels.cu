@@ -1030,6 +1030,8 @@ static cudaError_t launch_mo_f64_ec(const DevProblem& P, const DevScratch& S, in
 cudaError_t launch_mo_f64(const DevProblem& P, const DevScratch& S, int64_t n_walk, const double* R,
                           cudaStream_t st) {
   switch (P.mo_ec) {
+    case 1: return launch_mo_f64_ec<1>(P, S, n_walk, R, st);
+    case 2: return launch_mo_f64_ec<2>(P, S, n_walk, R, st);
     case 4: return launch_mo_f64_ec<4>(P, S, n_walk, R, st);
     case 8: return launch_mo_f64_ec<8>(P, S, n_walk, R, st);
     default: return launch_mo_f64_ec<6>(P, S, n_walk, R, st);
