@@ -111,17 +111,44 @@ static __device__ __forceinline__ void small_cof(int k, const F (&m)[4][4], F (&
 }
 
 
+// a d - b c in double-float as a compensated dot product
+static __device__ __forceinline__ df32 df_minor2(df32 a, df32 b, df32 c, df32 d) {
+  df_dot t;
+  t.add(a, d);
+  t.sub(b, c);
+  return t.value();
+}
+
+// Determinant of a k x k double-float matrix (k <= 4), as small_det, with the 2 x 2 minors
+// and the final expansion as compensated dot products (df_dot).
+static __device__ __forceinline__ df32 small_det_dot(int k, const df32 (&m)[4][4]) {
+  if (k == 0) return df32(1.0f, 0.0f);
+  if (k == 1) return m[0][0];
+  if (k == 2) return df_minor2(m[0][0], m[0][1], m[1][0], m[1][1]);
+  df_dot d;
+  if (k == 3) {  // expansion along row 0
+    d.add(m[0][0], df_minor2(m[1][1], m[1][2], m[2][1], m[2][2]));
+    d.sub(m[0][1], df_minor2(m[1][0], m[1][2], m[2][0], m[2][2]));
+    d.add(m[0][2], df_minor2(m[1][0], m[1][1], m[2][0], m[2][1]));
+    return d.value();
+  }
+  // Laplace expansion along rows 0 and 1: 2 x 2 minors of rows (0,1) and (2,3)
+  auto s = [&](int x, int y) { return df_minor2(m[0][x], m[0][y], m[1][x], m[1][y]); };
+  auto c = [&](int x, int y) { return df_minor2(m[2][x], m[2][y], m[3][x], m[3][y]); };
+  d.add(s(0, 1), c(2, 3));
+  d.sub(s(0, 2), c(1, 3));
+  d.add(s(0, 3), c(1, 2));
+  d.add(s(1, 2), c(0, 3));
+  d.sub(s(1, 3), c(0, 2));
+  d.add(s(2, 3), c(0, 1));
+  return d.value();
+}
+
 // Cofactors of a K x K double-float matrix (K <= 4, compile time), as small_cof: the
 // 2 x 2 minors and the expansions of the 3 x 3 ones are compensated dot products
 // (df_dot) instead of double-float products and sums.
 template <int K>
 static __device__ __forceinline__ void small_cof_dot(const df32 (&m)[4][4], df32 (&cof)[4][4]) {
-  auto minor2 = [](df32 a, df32 b, df32 c, df32 d) {  // a d - b c
-    df_dot t;
-    t.add(a, d);
-    t.sub(b, c);
-    return t.value();
-  };
   if constexpr (K == 1) {
     cof[0][0] = df32(1.0f, 0.0f);
   } else if constexpr (K == 2) {
@@ -136,7 +163,7 @@ static __device__ __forceinline__ void small_cof_dot(const df32 (&m)[4][4], df32
       for (int b = 0; b < 3; b++) {
         const int r0 = a == 0 ? 1 : 0, r1 = a == 2 ? 1 : 2;
         const int c0 = b == 0 ? 1 : 0, c1 = b == 2 ? 1 : 2;
-        const df32 d = minor2(m[r0][c0], m[r0][c1], m[r1][c0], m[r1][c1]);
+        const df32 d = df_minor2(m[r0][c0], m[r0][c1], m[r1][c0], m[r1][c1]);
         cof[a][b] = ((a + b) & 1) ? -d : d;
       }
   } else {
@@ -147,8 +174,8 @@ static __device__ __forceinline__ void small_cof_dot(const df32 (&m)[4][4], df32
     for (int x = 0; x < 4; x++)
 #pragma unroll
       for (int y = x + 1; y < 4; y++) {
-        top[x][y] = minor2(m[0][x], m[0][y], m[1][x], m[1][y]);
-        bot[x][y] = minor2(m[2][x], m[2][y], m[3][x], m[3][y]);
+        top[x][y] = df_minor2(m[0][x], m[0][y], m[1][x], m[1][y]);
+        bot[x][y] = df_minor2(m[2][x], m[2][y], m[3][x], m[3][y]);
       }
 #pragma unroll
     for (int a = 0; a < 4; a++) {
