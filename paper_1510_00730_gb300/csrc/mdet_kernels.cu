@@ -788,14 +788,13 @@ __global__ void __launch_bounds__(NT, MIXED ? 5 : 1) k_final(DevProblem P, DevSc
       const int sp = row < nu ? 0 : 1;
       const int n = sp ? nd : nu, e0 = sp ? nu : 0, i = row - e0;
       const float2* A = A2 + (sp ? nu * nu : 0);
-      df_dot acc;
+      df32 acc(0.0f, 0.0f);
       for (int a = 0; a < n; a++) {
         const float2 av = A[a * n + i];
         const int wi = (e0 + a) * M + m;
-        acc.add(df32(av.x, av.y), df32(Whi[wi], Wlo[wi]));
+        acc = acc + df32(av.x, av.y) * df32(Whi[wi], Wlo[wi]);
       }
-      const df32 q = acc.value();
-      Q2[row * Mt + m] = make_float2(q.hi, q.lo);
+      Q2[row * Mt + m] = make_float2(acc.hi, acc.lo);
     }
     __syncthreads();
     // Pm[b][i] = sum_m T[b][m] Q[i][m]
@@ -806,10 +805,9 @@ __global__ void __launch_bounds__(NT, MIXED ? 5 : 1) k_final(DevProblem P, DevSc
       const int b = tt / n, i = tt - b * n;
       const float2* Tr = Tdf + (e0 + b) * Mt;
       const float2* Qr = Q2 + (e0 + i) * Mt;
-      df_dot acc;
-      for (int m = 0; m < M; m++) acc.add(df32(Tr[m].x, Tr[m].y), df32(Qr[m].x, Qr[m].y));
-      const df32 pv = acc.value();
-      P2[t] = make_float2(pv.hi, pv.lo);
+      df32 acc(0.0f, 0.0f);
+      for (int m = 0; m < M; m++) acc = acc + df32(Tr[m].x, Tr[m].y) * df32(Qr[m].x, Qr[m].y);
+      P2[t] = make_float2(acc.hi, acc.lo);
     }
     __syncthreads();
     const df32 psit_df = df_from_bits(__double_as_longlong(psit));
@@ -823,13 +821,12 @@ __global__ void __launch_bounds__(NT, MIXED ? 5 : 1) k_final(DevProblem P, DevSc
       const float2* dphi = phi2 + ((w * 5 + 1 + mu) * N + e) * M;
       const float2* Qr = Q2 + e * Mt;
       const float2 gv = g2[(w * N + e) * 4 + mu];
-      df_dot acc;
-      acc.add(df32(gv.x, gv.y), psit_df);
+      df32 acc = df32(gv.x, gv.y) * psit_df;
       // magnitudes of the terms, for the error estimate (FP32 is plenty for an estimate)
-      float aab = fabsf(acc.s), aa2 = aab * aab;
+      float aab = fabsf(acc.hi), aa2 = aab * aab;
       for (int m = 0; m < M; m++) {
         const float2 dv = dphi[m];
-        acc.add(df32(dv.x, dv.y), df32(Qr[m].x, Qr[m].y));
+        acc = acc + df32(dv.x, dv.y) * df32(Qr[m].x, Qr[m].y);
         const float tm = fabsf(dv.x * Qr[m].x);
         aab += tm;
         aa2 = fmaf(tm, tm, aa2);
@@ -837,12 +834,12 @@ __global__ void __launch_bounds__(NT, MIXED ? 5 : 1) k_final(DevProblem P, DevSc
       const float2* Pb = P2 + (sp ? nu * nu : 0);
       for (int b = 0; b < n; b++) {
         const float2 dv = dphi[occ[b]], pv = Pb[b * n + i];
-        acc.sub(df32(dv.x, dv.y), df32(pv.x, pv.y));
+        acc = acc - df32(dv.x, dv.y) * df32(pv.x, pv.y);
         const float tm = fabsf(dv.x * pv.x);
         aab += tm;
         aa2 = fmaf(tm, tm, aa2);
       }
-      Gs[e][mu] = df_to_double_int(acc.value());
+      Gs[e][mu] = df_to_double_int(acc);
       Ga[e][mu] = aab;
       G2[e][mu] = sqrtf(aa2);
     }
