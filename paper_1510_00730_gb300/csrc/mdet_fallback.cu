@@ -132,6 +132,10 @@ __global__ void __launch_bounds__(64) k_fb_dets(DevProblem P, DevScratch S) {
     }
 }
 
+// threads per flagged walker of k_fb_scale (its exponentials and two block reductions over every
+// distinct determinant)
+constexpr int kFbScaleThreads = 256;
+
 __device__ __forceinline__ double block_max(double v, double* red) {
 #pragma unroll
   for (int off = 16; off; off >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, off));
@@ -147,7 +151,7 @@ __device__ __forceinline__ double block_max(double v, double* red) {
 // determinants), scaled values d = sign exp(log|D| - L) in place and in a
 // contiguous copy for the gathers, and cleared accumulators.
 // acc layout per slot: [0] L_up, [1] L_dn, [2] Psi, [3..3+4N) G[i][mu].
-__global__ void __launch_bounds__(256) k_fb_scale(DevProblem P, DevScratch S) {
+__global__ void __launch_bounds__(kFbScaleThreads) k_fb_scale(DevProblem P, DevScratch S) {
   const int slot = blockIdx.x;
   const int count = min(S.fb_list[0], P.fallback_cap);
   if (slot >= count) return;
@@ -157,7 +161,7 @@ __global__ void __launch_bounds__(256) k_fb_scale(DevProblem P, DevScratch S) {
   double* rec = S.fb + (size_t)slot * ntot * stride;
   double* dv = S.fb + (size_t)P.fallback_cap * ntot * stride + (size_t)slot * ntot;
   double* acc = S.fb_acc + (size_t)slot * (3 + 4 * 2 * kFbMax);
-  __shared__ double red[8];
+  __shared__ double red[kFbScaleThreads / 32];
   double lu = -INFINITY, ld = -INFINITY;
   for (int t = threadIdx.x; t < ntot; t += blockDim.x)
     if (rec[(size_t)t * stride + 1] != 0.0) {
@@ -183,7 +187,9 @@ __global__ void __launch_bounds__(256) k_fb_scale(DevProblem P, DevScratch S) {
 // grid (ceil(ntot / 256), count slots): one thread per up row (v = C d_dn,
 // Psi and the up-electron sums) or down column (u = C^T d_up, the
 // down-electron sums); block sums in shared memory, then one atomic per value.
-constexpr int kFbRowsPerItem = 64;  // distinct determinants per work item of k_fb_rows (8 warps x 8)
+// distinct determinants per work item of k_fb_rows, one per warp: the longest rows of C hold
+// thousands of nonzeros, and a warp that walked eight of them in turn set the kernel's latency
+constexpr int kFbRowsPerItem = 8;
 
 __global__ void __launch_bounds__(256) k_fb_rows(DevProblem P, DevScratch S) {
   const int count = min(S.fb_list[0], P.fallback_cap);
@@ -390,7 +396,7 @@ cudaError_t launch_fallback(const DevProblem& P, const DevScratch& S, int64_t n_
   dim3 g1((ntot + tpb - 1) / tpb, P.fallback_cap);
   k_fb_dets<<<g1, tpb, smem, st>>>(P, S);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  k_fb_scale<<<P.fallback_cap, 256, 0, st>>>(P, S);
+  k_fb_scale<<<P.fallback_cap, kFbScaleThreads, 0, st>>>(P, S);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   static int n_sm = 0;
   if (!n_sm) {
