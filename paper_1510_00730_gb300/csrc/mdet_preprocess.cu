@@ -5,13 +5,13 @@
 // pointers. The work per distinct determinant (excitation records, context
 // order) stays on the host and is shared with the host path.
 //
-// Sorting uses CUB's device radix sort (stable). The order is lexicographic in
-// (key of Eq. 3, last word, ..., first word): an LSD sequence of stable 64-bit
-// sorts, first word first and the key last, reproduces it exactly, including
-// the original product order among identical determinants.
+// Sorting is a stable LSD radix sort of (64-bit key, index) pairs written here
+// (8-bit digits, 8 passes). The order is lexicographic in (key of Eq. 3, last
+// word, ..., first word): an LSD sequence of stable 64-bit sorts, first word
+// first and the key last, reproduces it exactly, including the original product
+// order among identical determinants.
 
-#include <cub/cub.cuh>
-
+#include <algorithm>
 #include <climits>
 #include <cmath>
 
@@ -53,6 +53,152 @@ __global__ void k_key(int64_t n, int n_int, const uint64_t* __restrict__ D, int 
     v = D[k * n_int + word];
   }
   key[q] = v;
+}
+
+// ---- inclusive scan of int32 values ----------------------------------------
+// Tiles of kScanTile values (kThreads threads x 4): each tile is scanned in shared
+// memory and its total written to sums[tile]; the totals are scanned the same way
+// (recursively) and added back to the tiles after the first.
+constexpr int kScanPer = 4;
+constexpr int kScanTile = kThreads * kScanPer;
+
+__global__ void k_scan_tile(const int32_t* __restrict__ in, int32_t* __restrict__ out, int64_t n,
+                            int32_t* __restrict__ sums) {
+  __shared__ int32_t part[kThreads];
+  const int64_t base = (int64_t)blockIdx.x * kScanTile + (int64_t)threadIdx.x * kScanPer;
+  int32_t v[kScanPer];
+  int32_t run = 0;
+#pragma unroll
+  for (int j = 0; j < kScanPer; j++) {
+    run += base + j < n ? in[base + j] : 0;
+    v[j] = run;
+  }
+  part[threadIdx.x] = run;
+  __syncthreads();
+  for (int off = 1; off < kThreads; off <<= 1) {  // Hillis-Steele scan of the thread totals
+    const int32_t add = threadIdx.x >= off ? part[threadIdx.x - off] : 0;
+    __syncthreads();
+    part[threadIdx.x] += add;
+    __syncthreads();
+  }
+  const int32_t before = threadIdx.x ? part[threadIdx.x - 1] : 0;
+#pragma unroll
+  for (int j = 0; j < kScanPer; j++)
+    if (base + j < n) out[base + j] = v[j] + before;
+  if (threadIdx.x == kThreads - 1) sums[blockIdx.x] = part[kThreads - 1];
+}
+
+__global__ void k_scan_add(int32_t* __restrict__ out, int64_t n, const int32_t* __restrict__ sums) {
+  if (blockIdx.x == 0) return;
+  const int32_t add = sums[blockIdx.x - 1];
+  const int64_t base = (int64_t)blockIdx.x * kScanTile;
+  for (int j = threadIdx.x; j < kScanTile; j += kThreads)
+    if (base + j < n) out[base + j] += add;
+}
+
+// int32 scratch that scan_inclusive needs for n values
+int64_t scan_scratch(int64_t n) {
+  int64_t total = 0;
+  while (n > kScanTile) {
+    n = (n + kScanTile - 1) / kScanTile;
+    total += n;
+  }
+  return total + 1;
+}
+
+// out[i] = in[0] + ... + in[i] (in and out may be the same array)
+cudaError_t scan_inclusive(const int32_t* in, int32_t* out, int64_t n, int32_t* scratch, cudaStream_t st) {
+  if (n <= 0) return cudaSuccess;
+  const int64_t tiles = (n + kScanTile - 1) / kScanTile;
+  int32_t* sums = scratch;
+  k_scan_tile<<<(unsigned)tiles, kThreads, 0, st>>>(in, out, n, sums);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess || tiles == 1) return e;
+  if ((e = scan_inclusive(sums, sums, tiles, scratch + tiles, st)) != cudaSuccess) return e;
+  k_scan_add<<<(unsigned)tiles, kThreads, 0, st>>>(out, n, sums);
+  return cudaGetLastError();
+}
+
+// ---- stable LSD radix sort of (uint64 key, int32 value) pairs ----------------
+// One pass per 8-bit digit: every block counts the digits of its tile of kThreads
+// pairs into counts[digit][block] (digit-major, so that the inclusive scan of the
+// flattened array gives each (digit, block) its end offset); then every block moves
+// its pairs to offset + rank, the rank being the number of earlier pairs of the tile
+// with the same digit (lanes with the same digit found by __match_any_sync, the
+// warps before added from shared counts), which keeps equal keys in their order.
+constexpr int kRadixBits = 8;
+constexpr int kRadix = 1 << kRadixBits;
+constexpr int kWarpsPerBlock = kThreads / 32;
+
+__global__ void k_radix_count(const uint64_t* __restrict__ key, int64_t n, int shift, int32_t* __restrict__ counts) {
+  __shared__ int32_t c[kRadix];
+  for (int d = threadIdx.x; d < kRadix; d += kThreads) c[d] = 0;
+  __syncthreads();
+  const int64_t i = (int64_t)blockIdx.x * kThreads + threadIdx.x;
+  if (i < n) atomicAdd(&c[(int)((key[i] >> shift) & (kRadix - 1))], 1);
+  __syncthreads();
+  for (int d = threadIdx.x; d < kRadix; d += kThreads) counts[(int64_t)d * gridDim.x + blockIdx.x] = c[d];
+}
+
+__global__ void k_radix_move(const uint64_t* __restrict__ kin, const int32_t* __restrict__ vin, int64_t n, int shift,
+                             const int32_t* __restrict__ ends, const int32_t* __restrict__ counts,
+                             uint64_t* __restrict__ kout, int32_t* __restrict__ vout) {
+  __shared__ int32_t wc[kWarpsPerBlock][kRadix];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int t = threadIdx.x; t < kWarpsPerBlock * kRadix; t += kThreads) wc[t / kRadix][t % kRadix] = 0;
+  __syncthreads();
+  const int64_t i = (int64_t)blockIdx.x * kThreads + threadIdx.x;
+  const bool live = i < n;
+  const uint64_t k = live ? kin[i] : 0;
+  const int d = live ? (int)((k >> shift) & (kRadix - 1)) : kRadix;  // kRadix: no pair
+  const unsigned same = __match_any_sync(0xffffffffu, d);
+  const int rank_w = __popc(same & ((1u << lane) - 1u));
+  if (live && rank_w == 0) wc[warp][d] = __popc(same);
+  __syncthreads();
+  if (!live) return;
+  int rank = rank_w;
+  for (int q = 0; q < warp; q++) rank += wc[q][d];
+  const int64_t cell = (int64_t)d * gridDim.x + blockIdx.x;
+  const int64_t pos = (int64_t)ends[cell] - counts[cell] + rank;
+  kout[pos] = k;
+  vout[pos] = vin[i];
+}
+
+// A pair of buffers of which one holds the current data (the role of a double buffer).
+template <class T>
+struct Buffers {
+  T* b[2];
+  int sel = 0;
+  T* cur() const { return b[sel]; }
+  T* alt() const { return b[sel ^ 1]; }
+};
+
+// int32 scratch of radix_sort_pairs for n pairs: the counts and their scan, and the scan's own
+int64_t sort_scratch(int64_t n) {
+  const int64_t cells = (int64_t)kRadix * ((std::max<int64_t>(n, 1) + kThreads - 1) / kThreads);
+  return 2 * cells + scan_scratch(cells);
+}
+
+// Stable sort of keys.cur() with the values alongside; the result is in keys.cur() and vals.cur()
+cudaError_t radix_sort_pairs(Buffers<uint64_t>& keys, Buffers<int32_t>& vals, int64_t n, int32_t* scratch,
+                             cudaStream_t st) {
+  if (n <= 1) return cudaSuccess;
+  const int64_t blocks_n = (n + kThreads - 1) / kThreads;
+  const int64_t cells = (int64_t)kRadix * blocks_n;
+  int32_t* counts = scratch;
+  int32_t* ends = scratch + cells;
+  for (int shift = 0; shift < 64; shift += kRadixBits) {
+    k_radix_count<<<(unsigned)blocks_n, kThreads, 0, st>>>(keys.cur(), n, shift, counts);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    if ((e = scan_inclusive(counts, ends, cells, scratch + 2 * cells, st)) != cudaSuccess) return e;
+    k_radix_move<<<(unsigned)blocks_n, kThreads, 0, st>>>(keys.cur(), vals.cur(), n, shift, ends, counts, keys.alt(),
+                                                          vals.alt());
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    keys.sel ^= 1;
+    vals.sel ^= 1;
+  }
+  return cudaSuccess;
 }
 
 __global__ void k_iota(int64_t n, int32_t* __restrict__ v) {
@@ -169,11 +315,9 @@ cudaError_t get(T* host, const T* dev, size_t count, cudaStream_t st) {
 }
 
 // Stable sort of the permutation in vals by keys that k_key / k_pair_key wrote
-// into keys.Current(); the sorted permutation is vals.Current() afterwards.
-cudaError_t sort_pairs(PreDevice* d, cub::DoubleBuffer<uint64_t>& keys, cub::DoubleBuffer<int32_t>& vals,
-                       int64_t n, cudaStream_t st) {
-  size_t bytes = d->tmp_bytes;
-  return cub::DeviceRadixSort::SortPairs(d->tmp, bytes, keys, vals, (int)n, 0, 64, st);
+// into keys.cur(); the sorted permutation is vals.cur() afterwards.
+cudaError_t sort_pairs(PreDevice* d, Buffers<uint64_t>& keys, Buffers<int32_t>& vals, int64_t n, cudaStream_t st) {
+  return radix_sort_pairs(keys, vals, n, static_cast<int32_t*>(d->tmp), st);
 }
 
 }  // namespace
@@ -199,15 +343,9 @@ mdet_status pre_distinct(PreDevice** h, int64_t n, int n_int, const uint64_t* de
   PRE_TRY(cudaMalloc(&d->pos[0], N * 4));
   PRE_TRY(cudaMalloc(&d->pos[1], N * 4));
   PRE_TRY(cudaMalloc(&d->small, 4 * sizeof(unsigned long long)));
-  {
-    size_t b1 = 0, b2 = 0;
-    cub::DoubleBuffer<uint64_t> k(d->key0, d->key1);
-    cub::DoubleBuffer<int32_t> v(d->v0, d->v1);
-    PRE_TRY(cub::DeviceRadixSort::SortPairs(nullptr, b1, k, v, (int)N, 0, 64, st));
-    PRE_TRY(cub::DeviceScan::InclusiveSum(nullptr, b2, d->flag, d->id, (int)N + 1, st));
-    d->tmp_bytes = std::max(b1, b2);
-    PRE_TRY(cudaMalloc(&d->tmp, d->tmp_bytes));
-  }
+  // int32 scratch of the sorts and scans
+  d->tmp_bytes = sizeof(int32_t) * (size_t)std::max(sort_scratch((int64_t)N), scan_scratch((int64_t)N + 1));
+  PRE_TRY(cudaMalloc(&d->tmp, d->tmp_bytes));
   // validation: both spin lists, and the coefficients once
   unsigned long long bad[2];
   PRE_TRY(cudaMemsetAsync(d->small, 0xff, 2 * sizeof(unsigned long long), st));
@@ -228,23 +366,22 @@ mdet_status pre_distinct(PreDevice** h, int64_t n, int n_int, const uint64_t* de
     }
   for (int sp = 0; sp < 2; sp++) {
     const uint64_t* D = d->det[sp];
-    cub::DoubleBuffer<uint64_t> keys(d->key0, d->key1);
-    cub::DoubleBuffer<int32_t> vals(d->v0, d->v1);
-    k_iota<<<blocks(n), kThreads, 0, st>>>(n, vals.Current());
+    Buffers<uint64_t> keys{{d->key0, d->key1}};
+    Buffers<int32_t> vals{{d->v0, d->v1}};
+    k_iota<<<blocks(n), kThreads, 0, st>>>(n, vals.cur());
     // LSD: first word first, ..., last word, then the key of Eq. 3 (one pass when n_int == 1,
     // where the key is the word)
     const int n_pass = n_int > 1 ? n_int + 1 : 1;
     for (int p = 0; p < n_pass; p++) {
       const int word = p == n_pass - 1 ? -1 : p;
-      k_key<<<blocks(n), kThreads, 0, st>>>(n, n_int, D, word, vals.Current(), keys.Current());
+      k_key<<<blocks(n), kThreads, 0, st>>>(n, n_int, D, word, vals.cur(), keys.cur());
       PRE_TRY(cudaGetLastError());
       PRE_TRY(sort_pairs(d, keys, vals, n, st));
     }
-    const int32_t* ord = vals.Current();
+    const int32_t* ord = vals.cur();
     k_new_det<<<blocks(n), kThreads, 0, st>>>(n, n_int, D, ord, d->flag);
     PRE_TRY(cudaGetLastError());
-    size_t bytes = d->tmp_bytes;
-    PRE_TRY(cub::DeviceScan::InclusiveSum(d->tmp, bytes, d->flag, d->id, (int)n, st));
+    PRE_TRY(scan_inclusive(d->flag, d->id, n, static_cast<int32_t*>(d->tmp), st));
     k_positions<<<blocks(n), kThreads, 0, st>>>(n, ord, d->flag, d->id, d->pos[sp], d->first);
     PRE_TRY(cudaGetLastError());
     int32_t nu = 0;
@@ -293,33 +430,32 @@ mdet_status pre_build_c(PreDevice* d, const std::vector<int32_t> ctx_of[2], int6
     for (int pass = 0; pass < 2; pass++) {
       const int major = pass == 0 ? 1 : 0, minor = 1 - major;
       const int64_t n_major = pass == 0 ? ndn : nup, n_minor = pass == 0 ? nup : ndn;
-      cub::DoubleBuffer<uint64_t> keys(d->key0, d->key1);
-      cub::DoubleBuffer<int32_t> vals(d->v0, d->v1);
-      k_iota<<<blocks(n), kThreads, 0, st>>>(n, vals.Current());
+      Buffers<uint64_t> keys{{d->key0, d->key1}};
+      Buffers<int32_t> vals{{d->v0, d->v1}};
+      k_iota<<<blocks(n), kThreads, 0, st>>>(n, vals.cur());
       k_pair_key<<<blocks(n), kThreads, 0, st>>>(n, d->pos[major], ctx[major], d->pos[minor], ctx[minor], n_minor,
-                                                 keys.Current());
+                                                 keys.cur());
       PRE_TRY(cudaGetLastError());
       PRE_TRY(sort_pairs(d, keys, vals, n, st));
       PRE_TRY(cudaMemsetAsync(cnt, 0, (size_t)(n_major + 1) * 4, st));
       PRE_TRY(cudaMemsetAsync(d->small, 0xff, sizeof(unsigned long long), st));
-      k_dup_and_count<<<blocks(n), kThreads, 0, st>>>(n, keys.Current(), n_minor, d->small, cnt);
+      k_dup_and_count<<<blocks(n), kThreads, 0, st>>>(n, keys.cur(), n_minor, d->small, cnt);
       PRE_TRY(cudaGetLastError());
       if (pass == 0) {
         unsigned long long dup = 0;
         PRE_TRY(get(&dup, d->small, 1, st));
         if (dup != ULLONG_MAX) {
           int32_t pair[2];
-          PRE_TRY(get(pair, vals.Current() + (dup - 1), 2, st));
+          PRE_TRY(get(pair, vals.cur() + (dup - 1), 2, st));
           char buf[160];
           snprintf(buf, sizeof buf, "products %d and %d repeat the same (up, down) pair", pair[0], pair[1]);
           *msg = buf;
           return MDET_E_INPUT;
         }
       }
-      size_t bytes = d->tmp_bytes;
       // counts -> segment starts (cnt[0] = 0): an inclusive scan into id
-      PRE_TRY(cub::DeviceScan::InclusiveSum(d->tmp, bytes, cnt, d->id, (int)(n_major + 1), st));
-      k_scatter_c<<<blocks(n), kThreads, 0, st>>>(n, vals.Current(), d->pos[0], ctx[0], d->pos[1], ctx[1], d->coef,
+      PRE_TRY(scan_inclusive(cnt, d->id, n_major + 1, static_cast<int32_t*>(d->tmp), st));
+      k_scatter_c<<<blocks(n), kThreads, 0, st>>>(n, vals.cur(), d->pos[0], ctx[0], d->pos[1], ctx[1], d->coef,
                                                   row, col, val);
       PRE_TRY(cudaGetLastError());
       std::vector<int32_t>& r = pass == 0 ? out->csc_row : out->csr_row;
