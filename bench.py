@@ -604,7 +604,7 @@ def run_sm_chain(args):
     import torch
 
     import paper_1510_00730_gb300 as pkg
-    from paper_1510_00730_gb300 import synth
+    from paper_1510_00730_gb300 import costs, synth
     torch.cuda.set_device(0)
     dev = torch.device("cuda", 0)
     wl = synth.chlorine_like_750k()
@@ -644,6 +644,10 @@ def run_sm_chain(args):
                        "n_det_dn": st["n_det_dn"], "threshold": 1e-3},
             "table_ms": table_ms, "chain_over_table": chain_ms / table_ms,
             "n_inv": float(n_inv.double().mean()), "n_subst": float(n_subst.double().mean()),
+            # per distinct determinant, and what a fixed reference would need (Sec. 5's 1.78 against 3.46)
+            "n_subst_per_det": float(n_subst.double().mean()) / (st["n_det_up"] + st["n_det_dn"]),
+            "n_subst_per_det_fixed_reference": costs.fixed_reference_substitutions(
+                *[np.bincount(ctx.spin_dets(sp)[1]) for sp in (0, 1)]),
             "ratio_difference": {"p50": float(np.median(diff)), "p99": float(np.percentile(diff, 99)),
                                  "max": float(diff.max())},
             "clocks": clk.summary()}

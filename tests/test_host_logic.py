@@ -36,16 +36,27 @@ def test_library_exports_every_declared_symbol():
         assert hasattr(L, n), n
 
 
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _golden(name):
+    """Rows of a fixture under tests/golden (the paper's printed values), comments skipped."""
+    with open(os.path.join(GOLDEN, name)) as f:
+        return [line.split() for line in f if line.strip() and not line.startswith("#")]
+
+
 def test_paper_encoding_examples():
     """Sec. 2.1: the Hartree-Fock determinant of Cl is (511, 255), and the
-    up+down excitation 7 -> 12 is (2495, 2239)."""
+    up+down excitation 7 -> 12 is (2495, 2239) (tests/golden/encoding_sec2_1.txt)."""
+    rows = {r[0]: r[1:] for r in _golden("encoding_sec2_1.txt")}
     hf_up = synth.occ_to_bits(range(9), 1)[0]
     hf_dn = synth.occ_to_bits(range(8), 1)[0]
-    assert (hf_up, hf_dn) == (511, 255)
+    assert [hf_up, hf_dn] == [int(x) for x in rows["hf"][:2]]
+    assert [format(hf_up, "b"), format(hf_dn, "b")] == rows["hf"][2:]
     ex_up = synth.occ_to_bits([0, 1, 2, 3, 4, 5, 7, 8, 11], 1)[0]
     ex_dn = synth.occ_to_bits([0, 1, 2, 3, 4, 5, 7, 11], 1)[0]
-    assert (ex_up, ex_dn) == (2495, 2239)
-    assert format(ex_up, "b") == "100110111111" and format(ex_dn, "b") == "100010111111"
+    assert [ex_up, ex_dn] == [int(x) for x in rows["ex_7_to_12"][:2]]
+    assert [format(ex_up, "b"), format(ex_dn, "b")] == rows["ex_7_to_12"][2:]
     # the library reads the same strings as a degree-1 excitation of the reference
     wl = synth.chlorine_like_100k(n_walk=1)
     wl.mo_coef = wl.mo_coef[:, :19].copy()
@@ -62,14 +73,35 @@ def test_paper_encoding_examples():
 
 
 def test_table1_ordering():
-    """Table 1 / Eq. 3: 4 electrons in 8 orbitals sort as 15, 23, 27, 29, 30, 39, 43, 45, ..."""
+    """Table 1 / Eq. 3: 4 electrons in 8 orbitals sort as 15, 23, 27, 29, 30, 39, 43, 45, ...
+    (tests/golden/table1_omega_order.txt: decimal, binary and occupied orbitals)."""
+    table = _golden("table1_omega_order.txt")
+    for idx, dec, binary, occ in table:
+        assert int(binary, 2) == int(dec) == sum(1 << (int(c) - 1) for c in occ)
     vals = [sum(1 << m for m in s) for s in combinations(range(8), 4)]
     rng = np.random.default_rng(0)
     vals = np.array(vals, np.uint64)[rng.permutation(len(vals))]
     order = pkg.omega_sort(vals[:, None])
     got = [int(v) for v in vals[order]]
-    assert got[:8] == [15, 23, 27, 29, 30, 39, 43, 45]
+    assert got[:len(table)] == [int(r[1]) for r in table]
     assert got == sorted(got)
+
+
+def test_sec5_operation_counts_reproduce_the_paper():
+    """Sec. 5's cost model (tests/golden/sec5_costs.txt): for a 9 x 9 matrix a full inversion
+    costs 1.71 times two Sherman-Morrison substitutions, and with the Hartree-Fock determinants
+    as a fixed reference the up and down determinants of Table 4
+    (tests/golden/table4_excitation_degrees.txt) would need 3.46 substitutions on average."""
+    from paper_1510_00730_gb300 import costs
+    want = {r[0]: float(r[1]) for r in _golden("sec5_costs.txt")}
+    ratio = costs.inversion_flops(9) / (2 * costs.substitution_flops(9))
+    assert round(ratio, 2) == want["inversion_over_two_substitutions_n9"]
+    t4 = np.array([[int(x) for x in r] for r in _golden("table4_excitation_degrees.txt")])
+    assert list(t4[:, 0]) == list(range(9))
+    avg = costs.fixed_reference_substitutions(t4[:, 2], t4[:, 3])
+    assert round(avg, 2) == want["fixed_reference_substitutions"]
+    # the printed total of Table 4's product column is the 10^6-determinant wave function
+    assert abs(int(t4[:, 1].sum()) - 1_000_000) <= 1_000
 
 
 def test_omega_key_is_xor_of_words_unsigned():
