@@ -29,9 +29,9 @@ CPU_SAMPLE_WALKERS = 96     # bounded oracle sample for the CPU baseline (~10-30
 CPU_SINGLE_CORE_WALKERS = 8  # the same oracle on one core, for the per-core figure
 # dram__bytes_read.sum + dram__bytes_write.sum of the average k_spmm_seg launch on the 750k workload
 # with 8,192 walkers, from one ncu capture of the current kernel per (precision, walker chunks):
-# mixed in three chunks (the v and u launches of chunks 0 and 1; chunk 2 has chunk 0's size and is
-# counted with its figures), FP64 in one; null for a configuration that was not captured
-SPMM_TRAFFIC_750K = {("mixed", 3): 176.3e6, ("fp64", 1): 602.1e6}
+# mixed in three chunks of 6, 21 and 5 tiles (the six launches of one evaluation), FP64 in one; null
+# for a configuration that was not captured
+SPMM_TRAFFIC_750K = {("mixed", 3): 182.7e6, ("fp64", 1): 602.1e6}
 
 
 def _env_int(k, d):
@@ -476,17 +476,29 @@ def measure_batched(precision, steps, warmup, streams=8, tune_ms=60.0, fallback_
         torch.cuda.synchronize()
     ms = statistics.mean(a.elapsed_time(b) for a, b in ev)
     W = sum(wl.n_walk for wl in wls)
-    # time of each expansion alone (no batching), for the gain of sharing the GPU
+    # time of each expansion alone (no batching), for the gain of sharing the GPU, and the roofline
+    # of its FP64 contraction (4 FLOP per product and walker; launch times from the kernels' own
+    # timer stamps, profiling mode 2, which adds no event to the streams)
     solo = 0.0
-    for c, R in zip(ctxs, Rs):
+    contract_tf = []
+    for c, R, wl in zip(ctxs, Rs, wls):
         out = c.alloc_outputs(R.shape[0])
         c.evaluate(R, out=out)
+        c.set_profiling(2)
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         a.record(stream)
         c.evaluate(R, out=out)
         b.record(stream)
         torch.cuda.synchronize()
         solo += a.elapsed_time(b)
+        cms = c.profile()["contract"]
+        c.set_profiling(False)
+        contract_tf.append((4.0 * wl.n_det * wl.n_walk / (cms * 1e-3) / 1e12 if cms > 0 else float("nan"),
+                            4.0 * wl.n_det * wl.n_walk, cms))
+    peak, _, _ = fp64_peak(dev.index, _gpu_index(dev.index))
+    tf = np.array([t[0] for t in contract_tf])
+    flops = np.array([t[1] for t in contract_tf])
+    weighted = float(flops.sum() / (sum(t[2] for t in contract_tf) * 1e-3) / 1e12)
     line = {"metric": "walker-steps/s, 64 uneven expansions in one graph launch", "value": W / (ms / 1e3),
             "unit": UNIT, "n_gpus": 1, "steps": steps, "warmup": warmup, "ms_per_step": ms,
             "higher_is_better": True, "dtype": "f64" if prec == pkg.PRECISION_FP64 else "f64+f32x2",
@@ -496,6 +508,14 @@ def measure_batched(precision, steps, warmup, streams=8, tune_ms=60.0, fallback_
                        "fallback_tol": ctxs[0].fallback[0],
                        "autotune_s": tune_s, "l2": "flushed between timed steps"},
             "sum_of_solo_ms": solo, "batch_gain": solo / ms,
+            "roofline_per_expansion": {
+                "kernel": "k_spmm_seg", "bound": "alu", "unit": "TFLOP/s", "peak": peak,
+                "peak_source": "measured FP64 FMA probe (mdet_measure_fp64_rate), this run",
+                "achieved": {"min": float(np.nanmin(tf)), "median": float(np.nanmedian(tf)),
+                             "max": float(np.nanmax(tf)), "all_expansions": weighted},
+                "frac_median": float(np.nanmedian(tf)) / peak, "frac_all_expansions": weighted / peak,
+                "note": "each expansion evaluated alone; all_expansions = total contraction FLOPs over total "
+                        "contraction time"},
             "tuning_histogram": {k: dict(zip(*np.unique([t[k] for t in tunes], return_counts=True)))
                                  for k in ("spmm_chunk", "mo_ec", "walker_chunks")},
             "clocks": clk.summary(),
