@@ -626,6 +626,8 @@ mdet_status ensure_scratch(mdet_ctx* c, int64_t n_walk) {
     const int64_t N = P.n_elec;
     if ((s = dalloc(c, &S.fb_list, (size_t)cap + 1))) return s;
     DevScratch& E = c->E;
+    // FP64 arrays only; with its live count set, E always takes the narrow FP64 contraction, which
+    // keeps the magnitude sums gathered from the flagging evaluation
     if ((s = alloc_eval_arrays(c, E, cap, false, false)) || (s = alloc_fallback(c, E))) return s;
     if ((s = dalloc(c, &c->e_R, (size_t)cap * N * 3)) || (s = dalloc(c, &c->e_live, 1)) ||
         (s = dalloc(c, &c->eo.log_abs_psi, (size_t)cap)) || (s = dalloc(c, &c->eo.sign, (size_t)cap)) ||

@@ -1056,9 +1056,9 @@ cudaError_t launch_ratios_f64(const DevProblem& P, const DevScratch& S, int64_t 
 // device): 4 walkers per lane and no magnitude sum, because the walkers keep the
 // sum of the evaluation that flagged them (gathered into psia). Decided in one
 // place for the zeroing and the launch, which must agree on whether psia is summed.
-static bool narrow_contraction(const DevProblem& P, const DevScratch& S) {
-  return S.live != nullptr && !(P.contract_impl == 1 && S.rdf && P.csr_val_df);
-}
+// An escalated re-evaluation (live count set) always takes the narrow FP64 kernel, which leaves
+// the gathered magnitude sums psia alone (k_ref does not clear them there either).
+static bool narrow_contraction(const DevProblem&, const DevScratch& S) { return S.live != nullptr; }
 
 cudaError_t launch_zero_f64(const DevProblem&, const DevScratch&, int64_t, cudaStream_t) {
   // nothing left to clear here: the contraction stores whole segments, the ratio kernels clear
@@ -1093,7 +1093,7 @@ cudaError_t launch_contract_f64(const DevProblem& P, const DevScratch& S, int64_
   const int64_t ndt = (int64_t)P.n_det_sp[0] + P.n_det_sp[1];
   const double* r_up = S.r;
   const double* r_dn = S.r + (size_t)P.n_det_sp[0] * S.wp;
-  if (P.contract_impl == 1 && S.rdf && P.csr_val_df) {  // double-float option of the mixed path
+  if (!narrow && P.contract_impl == 1 && S.rdf && P.csr_val_df) {  // double-float option of the mixed path
     const float2* x_up = S.rdf;
     const float2* x_dn = S.rdf + (size_t)P.n_det_sp[0] * S.wp;
     auto gdf = [&](int o) -> unsigned {
