@@ -18,6 +18,21 @@ static __device__ __forceinline__ float abs_f32_of(double x) {
   return __int_as_float(t << 3);
 }
 
+// 1/sqrt(x) for the Coulomb sums of the local energy: an FP32 estimate refined by two
+// Newton-Raphson steps for the reciprocal square root, y <- y + y (1 - x y^2) / 2, in
+// FP64. A step turns a relative error e into about 3 e^2 / 2, so from the FP32
+// estimate (e below 2^-21) two steps leave only the roundings of the last one, a few
+// ulp. Arguments outside the estimate's range (zero, subnormal, huge, Inf, NaN) take
+// 1 / sqrt(x).
+static __device__ __forceinline__ double coulomb_inv_r(double x) {
+  if (!(x > 0x1p-100 && x < 0x1p100)) return 1.0 / sqrt(x);
+  double y = (double)rsqrtf((float)x);
+  double e = fma(-x * y, y, 1.0);
+  y = fma(0.5 * y, e, y);
+  e = fma(-x * y, y, 1.0);
+  return fma(0.5 * y, e, y);
+}
+
 static __device__ __forceinline__ double ipow_d(double x, int n) {
   double r = 1.0;
   for (int i = 0; i < n; i++) r *= x;

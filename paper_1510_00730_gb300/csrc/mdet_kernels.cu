@@ -899,28 +899,52 @@ __global__ void __launch_bounds__(NT, MIXED ? 5 : 1) k_final(DevProblem P, DevSc
     }
   }
   __syncthreads();
-  // potential energy: electron-nucleus, electron-electron, nucleus-nucleus
+  // potential energy: the electron-electron, electron-nucleus and nucleus-nucleus pairs
+  // as one list spread evenly over the block's threads, so that no lane idles on a
+  // skipped pair; electron pairs in circulant order, (i, i + d mod N) for d = 1 ..
+  // (N - 1) / 2 and then, for even N, (i, i + N / 2) with i < N / 2: each unordered
+  // pair once
   double v = 0.0;
-  const double* r = R + w * N * 3;
-  for (int t = threadIdx.x; t < N * P.n_nuc; t += blockDim.x) {
-    const int i = t / P.n_nuc, A = t - i * P.n_nuc;
-    const double dx = r[3 * i] - P.nuc_xyz[3 * A], dy = r[3 * i + 1] - P.nuc_xyz[3 * A + 1],
-                 dz = r[3 * i + 2] - P.nuc_xyz[3 * A + 2];
-    v -= P.Z[A] / sqrt(dx * dx + dy * dy + dz * dz);
-  }
-  for (int t = threadIdx.x; t < N * N; t += blockDim.x) {
-    const int i = t / N, j = t - i * N;
-    if (j <= i) continue;
-    const double dx = r[3 * i] - r[3 * j], dy = r[3 * i + 1] - r[3 * j + 1], dz = r[3 * i + 2] - r[3 * j + 2];
-    v += 1.0 / sqrt(dx * dx + dy * dy + dz * dz);
-  }
-  if (threadIdx.x == 0)
-    for (int A = 0; A < P.n_nuc; A++)
-      for (int B = A + 1; B < P.n_nuc; B++) {
-        const double dx = P.nuc_xyz[3 * A] - P.nuc_xyz[3 * B], dy = P.nuc_xyz[3 * A + 1] - P.nuc_xyz[3 * B + 1],
-                     dz = P.nuc_xyz[3 * A + 2] - P.nuc_xyz[3 * B + 2];
-        v += P.Z[A] * P.Z[B] / sqrt(dx * dx + dy * dy + dz * dz);
+  {
+    const double* r = R + w * N * 3;
+    const int nn = P.n_nuc, H = (N - 1) / 2;
+    const int n_ee = N * (N - 1) / 2, n_en = N * nn, n_nn = nn * (nn - 1) / 2;
+    for (int t = threadIdx.x; t < n_ee + n_en + n_nn; t += blockDim.x) {
+      const double *a, *b;
+      double q;
+      if (t < n_ee) {
+        int i, j;
+        if (t < N * H) {
+          i = t / H;
+          j = i + t % H + 1;
+          if (j >= N) j -= N;
+        } else {
+          i = t - N * H;
+          j = i + N / 2;
+        }
+        a = r + 3 * i;
+        b = r + 3 * j;
+        q = 1.0;
+      } else if (t < n_ee + n_en) {
+        const int u = t - n_ee, i = u / nn, A = u - i * nn;
+        a = r + 3 * i;
+        b = P.nuc_xyz + 3 * A;
+        q = -P.Z[A];
+      } else {
+        int u = t - n_ee - n_en, A = 0;
+        while (u >= nn - 1 - A) {
+          u -= nn - 1 - A;
+          A++;
+        }
+        const int B = A + 1 + u;
+        a = P.nuc_xyz + 3 * A;
+        b = P.nuc_xyz + 3 * B;
+        q = P.Z[A] * P.Z[B];
       }
+      const double dx = a[0] - b[0], dy = a[1] - b[1], dz = a[2] - b[2];
+      v = fma(q, coulomb_inv_r(fma(dx, dx, fma(dy, dy, dz * dz))), v);
+    }
+  }
 #pragma unroll
   for (int off = 16; off; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
   if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
@@ -948,7 +972,10 @@ __global__ void __launch_bounds__(NT, MIXED ? 5 : 1) k_final(DevProblem P, DevSc
   if (fb_on) {
     if (threadIdx.x < 4) {
       float r = 0.0f;
-      for (int i = 0; i < N; i++) r += (float)Gs[i][threadIdx.x] * (float)Gs[i][threadIdx.x];
+      for (int i = 0; i < N; i++) {  // magnitudes from the FP64 bits: no conversions on the FP64 pipe
+        const float a = abs_f32_of(Gs[i][threadIdx.x]);
+        r = fmaf(a, a, r);
+      }
       rmsG[threadIdx.x] = sqrtf(r / N);
     }
     __syncthreads();
@@ -956,8 +983,8 @@ __global__ void __launch_bounds__(NT, MIXED ? 5 : 1) k_final(DevProblem P, DevSc
     float e1 = 0.0f, e2 = 0.0f;
     for (int t = threadIdx.x; t < N * 4; t += blockDim.x) {
       const int i = t >> 2, mu = t & 3;
-      const float kap = (float)fmin(S.kap[w * 2 + (i < nu ? 0 : 1)], 1e30);
-      const float den = fmaxf(fabsf((float)Gs[i][mu]), rmsG[mu]);
+      const float kap = fminf(abs_f32_of(S.kap[w * 2 + (i < nu ? 0 : 1)]), 1e30f);
+      const float den = fmaxf(abs_f32_of(Gs[i][mu]), rmsG[mu]);
       e1 = fmaxf(e1, u * kap * Ga[i][mu] / den);
       e2 = fmaxf(e2, u * kap * G2[i][mu] / den);
     }
