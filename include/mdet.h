@@ -488,6 +488,16 @@ mdet_status mdet_selftest_df32(int device, int64_t n, const double* x, double* y
                                double* prod_df);
 
 /*
+ * Diagnostic of the reciprocal square root in the local energy's Coulomb sums
+ * (Sec. 4, E_L): for n device values x_i, y_nr[i] = the epilogue's 1/sqrt(x_i)
+ * (an FP32 estimate refined by two Newton-Raphson steps in FP64) and y_ref[i] =
+ * CUDA's FP64 1.0 / sqrt(x_i) (all device pointers, n doubles each). Synchronous.
+ * MDET_E_ARG for n < 1, a null pointer or a negative device; MDET_E_CUDA when the
+ * launch fails.
+ */
+mdet_status mdet_selftest_inv_r(int device, int64_t n, const double* x, double* y_nr, double* y_ref);
+
+/*
  * Diagnostics of the last evaluation (host copies, synchronises its stream):
  * cond1 [n_walk][2], cond_1 of the reference Slater matrix of each spin;
  * est [n_walk][2], the first-order error estimates of the walker's table

@@ -90,6 +90,7 @@ def load_library(build_if_missing: bool = True):
     L.mdet_get_fallback.argtypes = [vp, vp, vp]
     L.mdet_get_error_estimates.argtypes = [vp, i64, vp, vp]
     L.mdet_selftest_df32.argtypes = [i32, i64, vp, vp, vp, vp]
+    L.mdet_selftest_inv_r.argtypes = [i32, i64, vp, vp, vp]
     L.mdet_get_tuning.argtypes = [vp, C.POINTER(_Tuning)]
     L.mdet_set_tuning.argtypes = [vp, C.POINTER(_Tuning)]
     L.mdet_autotune.argtypes = [vp, i64, vp, C.c_double, C.POINTER(_Tuning)]
@@ -105,7 +106,7 @@ def load_library(build_if_missing: bool = True):
     for name in ("mdet_create", "mdet_set_system", "mdet_set_orbitals", "mdet_set_ci_expansion", "mdet_evaluate",
                  "mdet_evaluate_host", "mdet_get_ratios", "mdet_get_stats", "mdet_get_spin_dets",
                  "mdet_get_ci_matrix", "mdet_omega_sort", "mdet_truncate_norm", "mdet_sm_chain", "mdet_set_ci_expansion_device", "mdet_set_profiling", "mdet_get_profile",
-                 "mdet_psi_tilde_noalloc", "mdet_set_walker_chunks", "mdet_get_last_launches", "mdet_set_escalation", "mdet_selftest_df32", "mdet_get_tuning",
+                 "mdet_psi_tilde_noalloc", "mdet_set_walker_chunks", "mdet_get_last_launches", "mdet_set_escalation", "mdet_selftest_df32", "mdet_selftest_inv_r", "mdet_get_tuning",
                  "mdet_set_tuning", "mdet_autotune", "mdet_batch_evaluate", "mdet_batch_create", "mdet_batch_launch", "mdet_set_fallback", "mdet_get_fallback",
                  "mdet_get_error_estimates", "mdet_measure_fp64_rate", "mdet_get_timeline"):
         getattr(L, name).restype = i32
@@ -212,6 +213,18 @@ def omega_sort(dets) -> np.ndarray:
     if st:
         raise MdetError(st, "mdet_omega_sort failed")
     return order
+
+
+def selftest_inv_r(x):
+    """The Coulomb sums' Newton-refined 1/sqrt against CUDA's FP64 1.0 / sqrt on the
+    device (x: CUDA float64)."""
+    import torch
+    L = load_library()
+    y_nr, y_ref = torch.empty_like(x), torch.empty_like(x)
+    st = L.mdet_selftest_inv_r(x.device.index or 0, x.numel(), x.data_ptr(), y_nr.data_ptr(), y_ref.data_ptr())
+    if st:
+        raise MdetError(st, "mdet_selftest_inv_r failed")
+    return y_nr, y_ref
 
 
 def selftest_df32(x):

@@ -1411,6 +1411,14 @@ mdet_status mdet_selftest_df32(int device, int64_t n, const double* x, double* y
   return MDET_OK;
 }
 
+mdet_status mdet_selftest_inv_r(int device, int64_t n, const double* x, double* y_nr, double* y_ref) {
+  if (n < 1 || !x || !y_nr || !y_ref || device < 0) return MDET_E_ARG;
+  if (cudaSetDevice(device) != cudaSuccess) return MDET_E_CUDA;
+  if (launch_selftest_inv_r(n, x, y_nr, y_ref, nullptr) != cudaSuccess) return MDET_E_CUDA;
+  if (cudaDeviceSynchronize() != cudaSuccess) return MDET_E_CUDA;
+  return MDET_OK;
+}
+
 mdet_status mdet_get_tuning(const mdet_ctx* c, mdet_tuning* out) {
   if (!c || !out) return MDET_E_ARG;
   *out = c->last_tune;

@@ -228,6 +228,7 @@ const DevProblem* ctx_problem(const mdet_ctx* ctx, int* device);
 void ctx_set_error(mdet_ctx* ctx, const char* msg);
 cudaError_t launch_selftest_df(int64_t n, const double* x, double* y_df, double* y_ref, double* prod_df,
                                cudaStream_t st);
+cudaError_t launch_selftest_inv_r(int64_t n, const double* x, double* y_nr, double* y_ref, cudaStream_t st);
 size_t final_smem_bytes(const DevProblem& P, bool mixed);
 // wide: 512 threads per walker instead of 128 (FP64 only; lower latency for a few walkers)
 cudaError_t launch_final(const DevProblem& P, const DevScratch& S, int64_t n_walk, const double* R,

@@ -305,6 +305,16 @@ __global__ void k_selftest_df(int64_t n, const double* __restrict__ x, double* _
   prod_df[i] = df_to_double(a * b + a);
 }
 
+// The Coulomb sums' reciprocal square root against CUDA's FP64 1 / sqrt on the device:
+// y_nr[i] = coulomb_inv_r(x_i), y_ref[i] = 1.0 / sqrt(x_i).
+__global__ void k_selftest_inv_r(int64_t n, const double* __restrict__ x, double* __restrict__ y_nr,
+                                 double* __restrict__ y_ref) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  y_nr[i] = coulomb_inv_r(x[i]);
+  y_ref[i] = 1.0 / sqrt(x[i]);
+}
+
 }  // namespace
 
 template <int EC>
@@ -359,6 +369,11 @@ cudaError_t launch_mo_mixed(const DevProblem& P, const DevScratch& S, int64_t n_
 cudaError_t launch_selftest_df(int64_t n, const double* x, double* y_df, double* y_ref, double* prod_df,
                                cudaStream_t st) {
   k_selftest_df<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(n, x, y_df, y_ref, prod_df);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_selftest_inv_r(int64_t n, const double* x, double* y_nr, double* y_ref, cudaStream_t st) {
+  k_selftest_inv_r<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(n, x, y_nr, y_ref);
   return cudaGetLastError();
 }
 

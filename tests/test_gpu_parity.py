@@ -49,6 +49,25 @@ def test_double_float_exp_and_product():
     assert np.max(np.abs(got - want) / scale) < 1e-13
 
 
+def test_coulomb_inverse_square_root():
+    """The epilogue's 1/r in the Coulomb sums of E_L (an FP32 estimate refined by two
+    Newton-Raphson steps in FP64) against CUDA's FP64 1.0 / sqrt. A step squares the
+    estimate's relative error (below 2^-21), so what remains are the roundings of the last
+    step, and the reference's own two: within 8 * 2^-53 relative over squared distances
+    from 1e-12 to 1e12. Arguments outside the estimate's range take 1.0 / sqrt itself and
+    must agree exactly."""
+    from paper_1510_00730_gb300.binding import selftest_inv_r
+    x = torch.cat([torch.logspace(-12, 12, 40000, dtype=torch.float64),
+                   torch.rand(40000, dtype=torch.float64) * 100.0 + 1e-3]).to("cuda:0")
+    y, ref = selftest_inv_r(x)
+    rel = ((y - ref).abs() / ref).max().item()
+    assert rel <= 8 * 2.0 ** -53, rel
+    special = torch.tensor([0.0, 1e-300, 2.0 ** -100, 2.0 ** 100, 1e300, math.inf], dtype=torch.float64,
+                           device="cuda:0")
+    ys, refs = selftest_inv_r(special)
+    assert torch.equal(ys, refs)
+
+
 def _gpu_eval(ctx, R):
     Rt = torch.from_numpy(np.ascontiguousarray(R)).to("cuda:0")
     out = ctx.evaluate(Rt)
