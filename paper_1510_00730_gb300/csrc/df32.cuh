@@ -39,6 +39,12 @@ static __device__ __forceinline__ df32 df_from_double(double x) {
   return {h, __double2float_rn(x - (double)h)};
 }
 
+// The rare paths of the bit-level conversions below, out of line so that the compiler
+// cannot if-convert their FP64 conversions into the common path, where they would take
+// the FP64 pipe on every call.
+static __device__ __noinline__ df32 df_from_double_slow(double x) { return df_from_double(x); }
+static __device__ __noinline__ double df_to_double_slow(float hi, float lo) { return (double)hi + (double)lo; }
+
 // The same split from the bits of x with integer and FP32 instructions only:
 // hi keeps the sign, the exponent and the 23 leading mantissa bits (truncated),
 // lo the 29 remaining bits (rounded to FP32, so hi + lo = x (1 + d), |d| <= 2^-47).
@@ -47,7 +53,7 @@ static __device__ __forceinline__ df32 df_from_double(double x) {
 static __device__ __forceinline__ df32 df_from_bits(long long b) {
   const unsigned hw = (unsigned)((unsigned long long)b >> 32), lw = (unsigned)b;
   const int fe = (int)((hw >> 20) & 0x7ff) - 896;  // FP32 biased exponent of x
-  if (fe < 53 || fe > 254) return df_from_double(__longlong_as_double(b));
+  if (fe < 53 || fe > 254) return df_from_double_slow(__longlong_as_double(b));
   const unsigned sign = hw & 0x80000000u;
   const float hi = __uint_as_float(sign | ((unsigned)fe << 23) | ((hw & 0xfffffu) << 3) | (lw >> 29));
   // lo = (lw mod 2^29) 2^(e - 1075), e the FP64 biased exponent: 2^(fe - 179) as an FP32 scale
@@ -66,7 +72,7 @@ static __device__ __forceinline__ double df_to_double(df32 a) { return (double)a
 static __device__ __forceinline__ double df_to_double_int(df32 a) {
   const unsigned uh = __float_as_uint(a.hi), ul = __float_as_uint(a.lo);
   const int eh = (int)((uh >> 23) & 0xffu);
-  if (eh == 0 || eh == 0xff) return df_to_double(a);
+  if (eh == 0 || eh == 0xff) return df_to_double_slow(a.hi, a.lo);
   long long x = (long long)((uh & 0x7fffffu) | 0x800000u) << 29;
   if (uh >> 31) x = -x;
   const int el = (int)((ul >> 23) & 0xffu);

@@ -350,7 +350,8 @@ __global__ void __launch_bounds__(128) k_ratio_f64(DevProblem P, DevScratch S) {
       for (int b = 0; b < 4; b++)
         m[a][b] = (a < e.k && b < e.k) ? T[((size_t)e.h[a] * M + e.p[b]) * wp + w] : 0.0;
     const double d = small_det(e.k, m);
-    S.r[(size_t)t * wp + w] = e.eps < 0 ? -d : d;
+    // the sign by its bit, not by an FP64 instruction
+    S.r[(size_t)t * wp + w] = __longlong_as_double(__double_as_longlong(d) ^ ((long long)(e.eps < 0) << 63));
     if (P.split[t]) S.vu[w * ntot + t] = 0.0;  // the contraction adds the pieces of a cut segment
   }
 }

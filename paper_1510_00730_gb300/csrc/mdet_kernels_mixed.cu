@@ -283,10 +283,10 @@ __global__ void __launch_bounds__(128) k_ratio_df(DevProblem P, DevScratch S) {
         const float2 v = (a < e.k && b < e.k) ? T[((size_t)e.h[a] * M + e.p[b]) * wp + w] : make_float2(0.f, 0.f);
         m[a][b] = df32(v.x, v.y);
       }
-    const df32 dd = small_det_dot(e.k, m);
-    const double d = df_to_double_int(dd);  // the FP64 ratio for the contraction, off the FP64 pipe
-    S.r[(size_t)t * wp + w] = e.eps < 0 ? -d : d;
-    if (S.rdf) S.rdf[(size_t)t * wp + w] = e.eps < 0 ? make_float2(-dd.hi, -dd.lo) : make_float2(dd.hi, dd.lo);
+    const df32 d0 = small_det_dot(e.k, m);
+    const df32 dd = e.eps < 0 ? df32(-d0.hi, -d0.lo) : d0;  // the sign on the FP32 words
+    S.r[(size_t)t * wp + w] = df_to_double_int(dd);  // the FP64 ratio for the contraction, off the FP64 pipe
+    if (S.rdf) S.rdf[(size_t)t * wp + w] = make_float2(dd.hi, dd.lo);
     if (P.split[t]) S.vu[w * ntot + t] = 0.0;  // the contraction adds the pieces of a cut segment
   }
 }
