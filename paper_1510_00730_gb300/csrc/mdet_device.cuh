@@ -18,15 +18,34 @@ static __device__ __forceinline__ float abs_f32_of(double x) {
   return __int_as_float(t << 3);
 }
 
+// FP32 <-> FP64 by the bits, with integer instructions only (no conversion on the FP64
+// pipe). f32_of_f64_bits: x in the FP32 normal range, sign, exponent and the 23 leading
+// mantissa bits (truncated: relative error below 2^-23). f64_of_f32_bits: a normal FP32
+// value, exactly.
+static __device__ __forceinline__ float f32_of_f64_bits(double x) {
+  const unsigned hw = (unsigned)__double2hiint(x), lw = (unsigned)__double2loint(x);
+  return __uint_as_float((hw & 0x80000000u) | ((((hw >> 20) & 0x7ffu) - 896u) << 23) | ((hw & 0xfffffu) << 3) |
+                         (lw >> 29));
+}
+static __device__ __forceinline__ double f64_of_f32_bits(float f) {
+  const unsigned u = __float_as_uint(f);
+  const unsigned hw = (u & 0x80000000u) | ((((u >> 23) & 0xffu) + 896u) << 20) | ((u & 0x7fffffu) >> 3);
+  return __hiloint2double((int)hw, (int)(u << 29));
+}
+
+// Out of line, so that the compiler cannot if-convert it into the common path below.
+static __device__ __noinline__ double inv_sqrt_slow(double x) { return 1.0 / sqrt(x); }
+
 // 1/sqrt(x) for the Coulomb sums of the local energy: an FP32 estimate refined by two
 // Newton-Raphson steps for the reciprocal square root, y <- y + y (1 - x y^2) / 2, in
 // FP64. A step turns a relative error e into about 3 e^2 / 2, so from the FP32
 // estimate (e below 2^-21) two steps leave only the roundings of the last one, a few
-// ulp. Arguments outside the estimate's range (zero, subnormal, huge, Inf, NaN) take
-// 1 / sqrt(x).
+// ulp. The range test is on the bits; arguments outside [2^-99, 2^100) (zero,
+// negative, subnormal, huge, Inf, NaN) take 1 / sqrt(x).
 static __device__ __forceinline__ double coulomb_inv_r(double x) {
-  if (!(x > 0x1p-100 && x < 0x1p100)) return 1.0 / sqrt(x);
-  double y = (double)rsqrtf((float)x);
+  const unsigned se = (unsigned)__double2hiint(x) >> 20;  // sign and biased exponent
+  if (se <= 1023u - 100u || se >= 1023u + 100u) return inv_sqrt_slow(x);
+  double y = f64_of_f32_bits(rsqrtf(f32_of_f64_bits(x)));
   double e = fma(-x * y, y, 1.0);
   y = fma(0.5 * y, e, y);
   e = fma(-x * y, y, 1.0);
