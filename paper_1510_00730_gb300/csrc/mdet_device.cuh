@@ -33,6 +33,45 @@ static __device__ __forceinline__ double f64_of_f32_bits(float f) {
   return __hiloint2double((int)hw, (int)(u << 29));
 }
 
+// x added into a three-word FP32 accumulator (w1, w2, w3 in shared memory), the FP64
+// epilogue's W. x is split exactly by its bits into 24 + 24 + 5 significand bits (hi, mid,
+// lo); hi and then the carried error plus mid are added with atomics whose returned old
+// values give, by TwoSum, the exact rounding errors of those additions, which go to the
+// next word. Only the additions into w3 round, at about 2^-72 of the accumulated value, so
+// the sum is more accurate than FP64 accumulation, and no instruction runs on the FP64
+// pipe (FP64 shared-memory atomics do). |x| outside [2^-74, 2^128), zero, Inf and NaN
+// take the out-of-line path.
+static __device__ __noinline__ void acc3_add_slow(float* w1, float* w2, float* w3, double x) {
+  const float hi = __double2float_rn(x);
+  const double r = x - (double)hi;
+  const float mid = __double2float_rn(r);
+  const float lo = __double2float_rn(r - (double)mid);
+  atomicAdd(w1, hi);
+  atomicAdd(w2, mid);
+  atomicAdd(w3, lo);
+}
+static __device__ __forceinline__ void acc3_add(float* w1, float* w2, float* w3, double x) {
+  const unsigned hw = (unsigned)__double2hiint(x), lw = (unsigned)__double2loint(x);
+  const int fe = (int)((hw >> 20) & 0x7ffu) - 896;  // FP32 biased exponent of hi
+  if (fe < 53 || fe > 254) {
+    acc3_add_slow(w1, w2, w3, x);
+    return;
+  }
+  const unsigned sign = hw & 0x80000000u;
+  const float hi = __uint_as_float(sign | ((unsigned)fe << 23) | ((hw & 0xfffffu) << 3) | (lw >> 29));
+  // mid = bits 28..5 of the low word times 2^(e - 1070), lo = bits 4..0 times 2^(e - 1075)
+  // (e the FP64 biased exponent): both exact
+  const float mid = __uint_as_float(
+      __float_as_uint(__uint2float_rn((lw >> 5) & 0xffffffu) * __uint_as_float((unsigned)(fe - 47) << 23)) | sign);
+  const float lo =
+      __uint_as_float(__float_as_uint(__uint2float_rn(lw & 0x1fu) * __uint_as_float((unsigned)(fe - 52) << 23)) | sign);
+  float s, e1, t, e2, e3;
+  two_sum(atomicAdd(w1, hi), hi, s, e1);
+  two_sum(e1, mid, t, e2);
+  two_sum(atomicAdd(w2, t), t, s, e3);
+  atomicAdd(w3, __fadd_rn(__fadd_rn(e2, e3), lo));
+}
+
 // Out of line, so that the compiler cannot if-convert it into the common path below.
 static __device__ __noinline__ double inv_sqrt_slow(double x) { return 1.0 / sqrt(x); }
 

@@ -649,14 +649,16 @@ __device__ __forceinline__ void scatter_cof_df(const Exc& e, long long wb, const
 // K6: per walker: W scatter over every determinant, Q = A^T W, Pm = T Q^T,
 // G_{i mu} = g Psi~ + sum_m d_mu phi[i][m] Q[i][m] - sum_b d_mu phi[i][o_b] Pm[b][i],
 // then grad, Laplacian, log|Psi|, sign and E_L. grid n_walk, block 128.
-// FP64 variant: cofactors in FP64, W accumulated with FP64 shared atomics.
+// FP64 variant: cofactors in FP64, W accumulated in three FP32 words with compensated shared
+// atomics (acc3_add: more accurate than FP64 accumulation, and off the FP64 pipe, which FP64
+// shared-memory atomics occupy), summed into FP64 before Q.
 // MIXED variant: cofactors in double-float on the FP32 pipe; W accumulated as
 // a compensated pair of FP32 shared atomics: the atomic returns the old value,
 // so TwoSum(old, x) recovers the rounding error of the addition it performed,
 // which goes into the low word. Q, Pm and G are double-float too (orbitals,
 // A and g arrive as pairs), so the FP64 pipe is left to the contraction; the
 // sums G are converted to FP64 with integer instructions.
-// smem, FP64: T[N][M], W[N][M], Q[N][M], A blocks, Pm.
+// smem, FP64: T[N][M], W[3][N][M] (FP32), Q[N][M], A blocks, Pm.
 // smem, MIXED: W[N][M] as hi/lo FP32 arrays, Q[N][M], A blocks, Pm (all pairs),
 //       Tdf[N][M].
 template <bool MIXED, int NT>
@@ -673,13 +675,14 @@ __global__ void __launch_bounds__(NT, MIXED ? 5 : 1) k_final(DevProblem P, DevSc
   // threads reading the same column of different rows hit different banks
   const int Mt = MIXED ? M + 1 : M;
   double* Ts = MIXED ? nullptr : sm;    // [N][M] (FP64 only)
-  double* Ws = MIXED ? sm : sm + NM;    // [N][M] (MIXED: hi words, then lo words)
-  double* Qs = Ws + NM;                 // [N][Mt]
+  double* Ws = MIXED ? sm : sm + NM;    // [N][M] (MIXED: hi words, then lo words; FP64: three FP32 words)
+  double* Qs = Ws + (MIXED ? NM : (3 * NM + 1) / 2);  // [N][Mt]
   double* As = Qs + N * Mt;             // [nu*nu + nd*nd]
   double* Pm = As + nu * nu + nd * nd;  // [nu*nu + nd*nd]  Pm[b][i] per spin
   float2* Tdf = reinterpret_cast<float2*>(Pm + nu * nu + nd * nd);  // [N][Mt] (MIXED)
   float* Whi = reinterpret_cast<float*>(Ws);                          // MIXED: [N][M] hi words
   float* Wlo = Whi + NM;                                              //        [N][M] lo words
+  float* W3 = Wlo + NM;  // FP64: the third word of W (the first two are Whi, Wlo)
   constexpr int NW = NT / 32;  // warps per block
   __shared__ double red[NW];
   __shared__ double Gs[kMaxSpin * 2][4];
@@ -693,7 +696,9 @@ __global__ void __launch_bounds__(NT, MIXED ? 5 : 1) k_final(DevProblem P, DevSc
       Wlo[t] = 0.0f;
     } else {
       Ts[t] = S.T[(size_t)t * wp + w];
-      Ws[t] = 0.0;
+      Whi[t] = 0.0f;
+      Wlo[t] = 0.0f;
+      W3[t] = 0.0f;
     }
   }
   for (int t = threadIdx.x; t < nu * nu + nd * nd; t += blockDim.x) {
@@ -764,7 +769,10 @@ __global__ void __launch_bounds__(NT, MIXED ? 5 : 1) k_final(DevProblem P, DevSc
       for (int a = 0; a < 4; a++)
 #pragma unroll
         for (int b = 0; b < 4; b++)
-          if (a < e.k && b < e.k) atomicAdd(Ws + off + e.h[a] * M + e.p[b], wgt * cof[a][b]);
+          if (a < e.k && b < e.k) {
+            const int slot = off + e.h[a] * M + e.p[b];
+            acc3_add(Whi + slot, Wlo + slot, W3 + slot, wgt * cof[a][b]);
+          }
     }
   }
   __syncthreads();
@@ -845,7 +853,13 @@ __global__ void __launch_bounds__(NT, MIXED ? 5 : 1) k_final(DevProblem P, DevSc
       G2[e][mu] = sqrtf(aa2);
     }
   } else {
+    // W's three words summed into FP64, through Q's space (free until Q is formed), then back
+    // over the words
+    for (int t = threadIdx.x; t < NM; t += blockDim.x) Qs[t] = ((double)Whi[t] + (double)Wlo[t]) + (double)W3[t];
+    __syncthreads();
     double* Wd = Ws;
+    for (int t = threadIdx.x; t < NM; t += blockDim.x) Wd[t] = Qs[t];
+    __syncthreads();
     // Q[i][m] = sum_a A[a][i] W[a][m] (per spin block)
     for (int t = threadIdx.x; t < NM; t += blockDim.x) {
       const int row = t / M, m = t - row * M;
@@ -1186,8 +1200,9 @@ size_t final_smem_bytes(const DevProblem& P, bool mixed) {
   const size_t NM = (size_t)P.n_elec * P.n_mo;
   const size_t NMt = (size_t)P.n_elec * (P.n_mo + 1);  // rows padded by one pair (MIXED)
   const size_t AB = 2 * (size_t)(P.n_up * P.n_up + P.n_dn * P.n_dn);
-  // FP64: T, W, Q, A blocks and Pm; MIXED: W (hi and lo words), Q and T pairs, A blocks and Pm
-  return mixed ? 8 * (NM + 2 * NMt + AB) : 8 * (3 * NM + AB);
+  // FP64: T, W (three FP32 words), Q, A blocks and Pm; MIXED: W (hi and lo words), Q and T
+  // pairs, A blocks and Pm
+  return mixed ? 8 * (NM + 2 * NMt + AB) : 8 * (2 * NM + (3 * NM + 1) / 2 + AB);
 }
 
 cudaError_t launch_final(const DevProblem& P, const DevScratch& S, int64_t n_walk, const double* R,
