@@ -46,6 +46,9 @@ __global__ void k_fb_list(const DevProblem P, uint32_t* __restrict__ wstat, uint
   }
 }
 
+// log|d| of a subnormal pivot, out of line so that the common path issues no log
+static __device__ __noinline__ double fb_log_abs(double d) { return log(fabs(d)); }
+
 __global__ void __launch_bounds__(64) k_fb_dets(DevProblem P, DevScratch S) {
   const int slot = blockIdx.y;
   const int count = min(S.fb_list[0], P.fallback_cap);
@@ -69,23 +72,29 @@ __global__ void __launch_bounds__(64) k_fb_dets(DevProblem P, DevScratch S) {
   for (int i = 0; i < n; i++)
     for (int a = 0; a < n; a++) A[i * n + a] = ph[(size_t)(e0 + i) * M + cols[a]];
   int piv[kFbMax];
-  double logabs = 0.0, sgn = e.eps < 0 ? -1.0 : 1.0;
+  // |prod of pivots| = pm 2^pe with pm in [0.5, 1), one log at the end; pivots compared by the
+  // integer order of their magnitude bits (the order of the magnitudes), the sign kept as a bit,
+  // so that the FP64 pipe runs the elimination and not the bookkeeping
+  double pm = 1.0, log_sub = 0.0;
+  int pe = 0, neg = e.eps < 0;
   bool singular = false;
   for (int k = 0; k < n; k++) {
     int p = k;
-    double best = fabs(A[k * n + k]);
-    for (int i = k + 1; i < n; i++)
-      if (fabs(A[i * n + k]) > best) {
-        best = fabs(A[i * n + k]);
+    unsigned long long best = (unsigned long long)__double_as_longlong(A[k * n + k]) & 0x7fffffffffffffffULL;
+    for (int i = k + 1; i < n; i++) {
+      const unsigned long long v = (unsigned long long)__double_as_longlong(A[i * n + k]) & 0x7fffffffffffffffULL;
+      if (v > best) {
+        best = v;
         p = i;
       }
+    }
     piv[k] = p;
-    if (!(best > 0.0)) {
+    if (best == 0ULL || best >= 0x7ff0000000000000ULL) {  // no nonzero pivot, or Inf / NaN: singular
       singular = true;
       break;
     }
     if (p != k) {
-      sgn = -sgn;
+      neg ^= 1;
       for (int j = 0; j < n; j++) {
         const double tmp = A[k * n + j];
         A[k * n + j] = A[p * n + j];
@@ -93,8 +102,20 @@ __global__ void __launch_bounds__(64) k_fb_dets(DevProblem P, DevScratch S) {
       }
     }
     const double d = A[k * n + k];
-    logabs += log(fabs(d));
-    if (d < 0) sgn = -sgn;
+    {
+      const long long b = __double_as_longlong(d);
+      neg ^= (int)((unsigned long long)b >> 63);
+      const int ex = (int)((b >> 52) & 0x7ff);
+      if (ex == 0) {
+        log_sub += fb_log_abs(d);  // a subnormal pivot (rare, out of line)
+      } else {
+        pm *= __longlong_as_double((b & 0x000fffffffffffffLL) | 0x3fe0000000000000LL);
+        pe += ex - 1022;
+        const long long bm = __double_as_longlong(pm);  // back into [0.5, 1)
+        pe += (int)((bm >> 52) & 0x7ff) - 1022;
+        pm = __longlong_as_double((bm & 0x000fffffffffffffLL) | 0x3fe0000000000000LL);
+      }
+    }
     const double inv = 1.0 / d;
     A[k * n + k] = 1.0;
     for (int j = 0; j < n; j++) A[k * n + j] *= inv;
@@ -102,10 +123,12 @@ __global__ void __launch_bounds__(64) k_fb_dets(DevProblem P, DevScratch S) {
       if (i == k) continue;
       const double f = A[i * n + k];
       A[i * n + k] = 0.0;
-      if (f != 0.0)
+      if ((__double_as_longlong(f) << 1) != 0)
         for (int j = 0; j < n; j++) A[i * n + j] = fma(-f, A[k * n + j], A[i * n + j]);
     }
   }
+  const double logabs = singular ? 0.0 : log(pm) + pe * 0.69314718055994530942 + log_sub;
+  const double sgn = neg ? -1.0 : 1.0;
   double* rec = S.fb + ((size_t)slot * ntot + t) * stride;
   if (singular) {
     rec[0] = -INFINITY;
