@@ -7,8 +7,8 @@
 //   k_fb_list    compacts the flagged walkers into a device list (no host sync)
 //   k_fb_dets    one thread per (determinant, flagged walker): in-place
 //                Gauss-Jordan inversion with partial pivoting of the Slater
-//                matrix, log|D|, sign and (d_{i mu} D)/D = sum_a d_mu phi_{o_a}(r_i) (S^-1)_{a i}
-//   k_fb_scale   per flagged walker: common scale of its determinant values
+//                matrix, D as a signed mantissa times 2^e, and (d_{i mu} D)/D = sum_a d_mu phi_{o_a}(r_i) (S^-1)_{a i}
+//   k_fb_scale   per flagged walker: common power-of-two scale of its determinant values
 //   k_fb_rows    fixed grid over (walker, 64 rows) items, a warp per row: v = C d_dn, u = C^T d_up, Psi, gradient
 //                and Laplacian sums, reduced per block then with atomics
 //   k_fb_out     per flagged walker: potential energy and outputs
@@ -19,6 +19,7 @@
 // tolerance go through the full-LU path above; k_esc_scatter writes the results
 // back to the walkers' slots.
 #include <algorithm>
+#include <climits>
 #include <cfloat>
 #include <cmath>
 
@@ -46,9 +47,6 @@ __global__ void k_fb_list(const DevProblem P, uint32_t* __restrict__ wstat, uint
   }
 }
 
-// log|d| of a subnormal pivot, out of line so that the common path issues no log
-static __device__ __noinline__ double fb_log_abs(double d) { return log(fabs(d)); }
-
 __global__ void __launch_bounds__(64) k_fb_dets(DevProblem P, DevScratch S) {
   const int slot = blockIdx.y;
   const int count = min(S.fb_list[0], P.fallback_cap);
@@ -72,10 +70,10 @@ __global__ void __launch_bounds__(64) k_fb_dets(DevProblem P, DevScratch S) {
   for (int i = 0; i < n; i++)
     for (int a = 0; a < n; a++) A[i * n + a] = ph[(size_t)(e0 + i) * M + cols[a]];
   int piv[kFbMax];
-  // |prod of pivots| = pm 2^pe with pm in [0.5, 1), one log at the end; pivots compared by the
-  // integer order of their magnitude bits (the order of the magnitudes), the sign kept as a bit,
-  // so that the FP64 pipe runs the elimination and not the bookkeeping
-  double pm = 1.0, log_sub = 0.0;
+  // |D| = pm 2^pe with pm in [0.5, 1), no logarithm; pivots compared by the integer order of
+  // their magnitude bits (the order of the magnitudes), the sign kept as a bit, so that the
+  // FP64 pipe runs the elimination and not the bookkeeping
+  double pm = 1.0;
   int pe = 0, neg = e.eps < 0;
   bool singular = false;
   for (int k = 0; k < n; k++) {
@@ -105,16 +103,17 @@ __global__ void __launch_bounds__(64) k_fb_dets(DevProblem P, DevScratch S) {
     {
       const long long b = __double_as_longlong(d);
       neg ^= (int)((unsigned long long)b >> 63);
-      const int ex = (int)((b >> 52) & 0x7ff);
-      if (ex == 0) {
-        log_sub += fb_log_abs(d);  // a subnormal pivot (rare, out of line)
-      } else {
-        pm *= __longlong_as_double((b & 0x000fffffffffffffLL) | 0x3fe0000000000000LL);
-        pe += ex - 1022;
-        const long long bm = __double_as_longlong(pm);  // back into [0.5, 1)
-        pe += (int)((bm >> 52) & 0x7ff) - 1022;
-        pm = __longlong_as_double((bm & 0x000fffffffffffffLL) | 0x3fe0000000000000LL);
+      int ex = (int)((b >> 52) & 0x7ff);
+      long long bn = b;
+      if (ex == 0) {  // a subnormal pivot: scaled by 2^64 into the normal range (exact)
+        bn = __double_as_longlong(d * 0x1p64);
+        ex = (int)((bn >> 52) & 0x7ff) - 64;
       }
+      pm *= __longlong_as_double((bn & 0x000fffffffffffffLL) | 0x3fe0000000000000LL);
+      pe += ex - 1022;
+      const long long bm = __double_as_longlong(pm);  // back into [0.5, 1)
+      pe += (int)((bm >> 52) & 0x7ff) - 1022;
+      pm = __longlong_as_double((bm & 0x000fffffffffffffLL) | 0x3fe0000000000000LL);
     }
     const double inv = 1.0 / d;
     A[k * n + k] = 1.0;
@@ -127,8 +126,6 @@ __global__ void __launch_bounds__(64) k_fb_dets(DevProblem P, DevScratch S) {
         for (int j = 0; j < n; j++) A[i * n + j] = fma(-f, A[k * n + j], A[i * n + j]);
     }
   }
-  const double logabs = singular ? 0.0 : log(pm) + pe * 0.69314718055994530942 + log_sub;
-  const double sgn = neg ? -1.0 : 1.0;
   double* rec = S.fb + ((size_t)slot * ntot + t) * stride;
   if (singular) {
     rec[0] = -INFINITY;
@@ -144,8 +141,8 @@ __global__ void __launch_bounds__(64) k_fb_dets(DevProblem P, DevScratch S) {
         A[i * n + k] = A[i * n + piv[k]];
         A[i * n + piv[k]] = tmp;
       }
-  rec[0] = logabs;
-  rec[1] = sgn;
+  rec[0] = __longlong_as_double((long long)pe);  // the exponent, an integer in the bits
+  rec[1] = __longlong_as_double(__double_as_longlong(pm) | ((long long)neg << 63));  // D / 2^pe
   for (int i = 0; i < n; i++)
     for (int mu = 0; mu < 4; mu++) {
       const double* dph = ph + ((size_t)(1 + mu) * N + e0 + i) * M;
@@ -159,21 +156,22 @@ __global__ void __launch_bounds__(64) k_fb_dets(DevProblem P, DevScratch S) {
 // distinct determinant)
 constexpr int kFbScaleThreads = 256;
 
-__device__ __forceinline__ double block_max(double v, double* red) {
+__device__ __forceinline__ long long block_max_ll(long long v, long long* red) {
 #pragma unroll
-  for (int off = 16; off; off >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, off));
+  for (int off = 16; off; off >>= 1) v = max(v, __shfl_xor_sync(0xffffffffu, v, off));
   __syncthreads();
   if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
   __syncthreads();
-  double r = -INFINITY;
-  for (int q = 0; q < (int)(blockDim.x >> 5); q++) r = fmax(r, red[q]);
+  long long r = LLONG_MIN;
+  for (int q = 0; q < (int)(blockDim.x >> 5); q++) r = max(r, red[q]);
   return r;
 }
 
-// Per flagged walker: common scale per spin (the largest log|D| of its nonzero
-// determinants), scaled values d = sign exp(log|D| - L) in place and in a
-// contiguous copy for the gathers, and cleared accumulators.
-// acc layout per slot: [0] L_up, [1] L_dn, [2] Psi, [3..3+4N) G[i][mu].
+// Per flagged walker: common scale per spin, 2^L with L the largest exponent of its nonzero
+// determinants (each stored as a signed mantissa in [0.5, 1) times 2^e), the scaled values
+// d = mantissa 2^(e - L) in place and in a contiguous copy for the gathers (exact, by the
+// exponent bits; below 2^-1022 of the largest they are zero), and cleared accumulators.
+// acc layout per slot: [0] L_up ln 2, [1] L_dn ln 2, [2] Psi, [3..3+4N) G[i][mu].
 __global__ void __launch_bounds__(kFbScaleThreads) k_fb_scale(DevProblem P, DevScratch S) {
   const int slot = blockIdx.x;
   const int count = min(S.fb_list[0], P.fallback_cap);
@@ -184,26 +182,33 @@ __global__ void __launch_bounds__(kFbScaleThreads) k_fb_scale(DevProblem P, DevS
   double* rec = S.fb + (size_t)slot * ntot * stride;
   double* dv = S.fb + (size_t)P.fallback_cap * ntot * stride + (size_t)slot * ntot;
   double* acc = S.fb_acc + (size_t)slot * (3 + 4 * 2 * kFbMax);
-  __shared__ double red[kFbScaleThreads / 32];
-  double lu = -INFINITY, ld = -INFINITY;
+  __shared__ long long red[kFbScaleThreads / 32];
+  long long lu = LLONG_MIN, ld = LLONG_MIN;
   for (int t = threadIdx.x; t < ntot; t += blockDim.x)
-    if (rec[(size_t)t * stride + 1] != 0.0) {
-      if (t < nu_det) lu = fmax(lu, rec[(size_t)t * stride]);
-      else ld = fmax(ld, rec[(size_t)t * stride]);
+    if ((__double_as_longlong(rec[(size_t)t * stride + 1]) << 1) != 0) {  // a nonzero determinant
+      const long long e = __double_as_longlong(rec[(size_t)t * stride]);
+      if (t < nu_det) lu = max(lu, e);
+      else ld = max(ld, e);
     }
-  double Lu = block_max(lu, red);
-  double Ld = block_max(ld, red);
-  if (!(Lu > -INFINITY)) Lu = 0.0;
-  if (!(Ld > -INFINITY)) Ld = 0.0;
+  long long Lu = block_max_ll(lu, red);
+  long long Ld = block_max_ll(ld, red);
+  if (Lu == LLONG_MIN) Lu = 0;
+  if (Ld == LLONG_MIN) Ld = 0;
   for (int t = threadIdx.x; t < ntot; t += blockDim.x) {
     double* r = rec + (size_t)t * stride;
-    r[0] = r[1] == 0.0 ? 0.0 : r[1] * exp(r[0] - (t < nu_det ? Lu : Ld));
-    dv[t] = r[0];
+    const long long m = __double_as_longlong(r[1]);
+    double d = 0.0;
+    if ((m << 1) != 0) {
+      const long long ex = 1022 + __double_as_longlong(r[0]) - (t < nu_det ? Lu : Ld);  // <= 1022
+      if (ex >= 1) d = __longlong_as_double((m & ~(0x7ffLL << 52)) | (ex << 52));
+    }
+    r[0] = d;
+    dv[t] = d;
   }
   for (int q = threadIdx.x; q < 1 + 4 * N; q += blockDim.x) acc[2 + q] = 0.0;
   if (threadIdx.x == 0) {
-    acc[0] = Lu;
-    acc[1] = Ld;
+    acc[0] = (double)Lu * 0.69314718055994530942;
+    acc[1] = (double)Ld * 0.69314718055994530942;
   }
 }
 
